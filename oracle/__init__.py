@@ -1,0 +1,278 @@
+"""CPU oracle for constrained multilinear sieving of temporal path motifs.
+
+TEST INFRASTRUCTURE ONLY: the plain C reference in ``tmotif_oracle.c`` that the
+GPU library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package.  The product
+library never calls it, and the two share no code.
+
+Every function cites the passage of the paper it follows (Thejaswi, Gionis,
+Lauri, arXiv 2001.07158); see ``tmotif_oracle.c`` for the arithmetic.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+ANY = 0xFFFFFFFF
+KMAX = 20
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tmotif_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+u64 = C.c_uint64
+u32 = C.c_uint32
+i64 = C.c_int64
+P = C.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP over sieve points)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        sig = {
+            "or_gf_mul": (u64, [u64, u64]),
+            "or_gf_pow": (u64, [u64, u64]),
+            "or_gf_inv": (u64, [u64]),
+            "or_fmix64": (u64, [u64]),
+            "or_query_seed": (u64, [u64, u32]),
+            "or_probe_seed": (u64, [u64, u32]),
+            "or_coef_v": (u64, [u64, u32, u32]),
+            "or_coef_w": (u64, [u64, u32, u32]),
+            "or_coef_y": (u64, [u64, u32, u32, u32, u32]),
+            "or_slots": (C.c_int, [u32, P, u32, P, P]),
+            "or_vertex_x": (u64, [u64, u32, P, P, u32, u32, u64]),
+            "or_canon": (i64, [u32, u64, P, P, P, C.c_int, P, P, P]),
+            "or_sieve_points": (C.c_int, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32,
+                                          u64, u64, u64, P, C.c_int]),
+            "or_literal_table": (C.c_int, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32,
+                                           u64, u64, u32, P, P]),
+            "or_brute_points": (i64, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32,
+                                      u64, u64, u64, P]),
+            "or_brute_det": (i64, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32, u64, P]),
+            "or_count_paths": (i64, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32, u64,
+                                     P, P]),
+            "or_decide": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u32, u32,
+                                    u64, u32, u64, u64, P, P, P, C.c_int]),
+            "or_extract": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, u32, P, u32, u32, u32, u32,
+                                     u64, u32, P, P, P, P, C.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _u32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(P)
+
+
+# --------------------------------------------------------------------------
+# GF(2^64) and coefficients (Sec. 5.5 / Lemma 5.5; readings in the design doc)
+# --------------------------------------------------------------------------
+def gf_mul(a: int, b: int) -> int:
+    """Product in GF(2^64) = GF(2)[x]/(x^64 + x^4 + x^3 + x + 1)."""
+    return _load().or_gf_mul(a, b)
+
+
+def gf_pow(a: int, e: int) -> int:
+    return _load().or_gf_pow(a, e)
+
+
+def gf_inv(a: int) -> int:
+    return _load().or_gf_inv(a)
+
+
+def fmix64(z: int) -> int:
+    """splitmix64 output finaliser (Steele, Lea, Flood 2014)."""
+    return _load().or_fmix64(z)
+
+
+def query_seed(seed: int, r: int = 0) -> int:
+    return _load().or_query_seed(seed, r)
+
+
+def probe_seed(seed: int, i: int) -> int:
+    return _load().or_probe_seed(seed, i)
+
+
+def coef_v(qs: int, u: int, d: int) -> int:
+    return _load().or_coef_v(qs, u, d)
+
+
+def coef_w(qs: int, d: int, j: int) -> int:
+    return _load().or_coef_w(qs, d, j)
+
+
+def coef_y(qs: int, a: int, b: int, t: int, p: int) -> int:
+    """y for arc a->b at time t used at walk position p (Sec. 5.3)."""
+    return _load().or_coef_y(qs, a, b, t, p)
+
+
+def slots(k, multiset, num_colors):
+    ms = _u32(multiset)
+    sb = np.zeros(num_colors, np.uint32)
+    sc = np.zeros(num_colors, np.uint32)
+    rc = _load().or_slots(k, _ptr(ms), num_colors, _ptr(sb), _ptr(sc))
+    if rc != 0:
+        raise ValueError("bad multiset")
+    return sb, sc
+
+
+def vertex_x(qs, k, multiset, num_colors, color_u, u, point):
+    sb, sc = slots(k, multiset, num_colors)
+    return _load().or_vertex_x(qs, k, _ptr(sb), _ptr(sc), color_u, u, point)
+
+
+# --------------------------------------------------------------------------
+# Graphs
+# --------------------------------------------------------------------------
+def canon(n, src, dst, time, undirected=False):
+    """Canonical arc set (Sec. 3: E^tau is a set; undirected = two arcs;
+    self-loops dropped), sorted by (time, src, dst)."""
+    src, dst, time = _u32(src), _u32(dst), _u32(time)
+    m = len(src)
+    cap = (2 * m if undirected else m) + 1
+    os_, od, ot = (np.zeros(cap, np.uint32) for _ in range(3))
+    mc = _load().or_canon(n, m, _ptr(src), _ptr(dst), _ptr(time), int(bool(undirected)),
+                          _ptr(os_), _ptr(od), _ptr(ot))
+    if mc < 0:
+        raise ValueError("invalid graph")
+    return os_[:mc].copy(), od[:mc].copy(), ot[:mc].copy()
+
+
+class Problem:
+    """A query on canonical arcs (already passed through :func:`canon`)."""
+
+    def __init__(self, n, src, dst, time, color, num_colors, k, multiset, start=ANY, end=ANY,
+                 t_min=0, t_max=0, alive=None):
+        self.n = int(n)
+        self.src, self.dst, self.time = _u32(src), _u32(dst), _u32(time)
+        self.m = len(self.src)
+        self.color = _u32(color)
+        self.num_colors = int(num_colors)
+        self.k = int(k)
+        self.multiset = _u32(multiset)
+        self.start, self.end = int(start), int(end)
+        self.t_min, self.t_max = int(t_min), int(t_max)
+        self.alive = None if alive is None else np.ascontiguousarray(np.asarray(alive, np.uint8))
+
+    def _args(self):
+        return (self.n, self.m, _ptr(self.src), _ptr(self.dst), _ptr(self.time), _ptr(self.color),
+                self.num_colors, _ptr(self.alive), self.k, _ptr(self.multiset), self.start, self.end,
+                self.t_min, self.t_max)
+
+
+def sieve_points(pb: Problem, qs: int, p_begin=0, p_end=None, nthreads=0):
+    """Q^A for points [p_begin, p_end): eq. gen-polynomial:3 with the time index
+    rolled, sieve substitution of Lemma 5.5."""
+    if p_end is None:
+        p_end = 1 << pb.k
+    out = np.zeros(p_end - p_begin, np.uint64)
+    rc = _load().or_sieve_points(*pb._args(), qs, p_begin, p_end, _ptr(out), nthreads)
+    if rc != 0:
+        raise ValueError("oracle sieve failed")
+    return out
+
+
+def literal_table(pb: Problem, qs: int, point: int, T: int):
+    """Full table P_{u,l,i}, l in [0,k], i in [0,T] (eq. gen-polynomial:3 as printed)."""
+    table = np.zeros(pb.n * (pb.k + 1) * (T + 1), np.uint64)
+    q = np.zeros(1, np.uint64)
+    rc = _load().or_literal_table(*pb._args(), qs, point, T, _ptr(table), _ptr(q))
+    if rc != 0:
+        raise ValueError("oracle literal table failed")
+    return table.reshape(pb.n, pb.k + 1, T + 1), int(q[0])
+
+
+def brute_points(pb: Problem, qs: int, p_begin=0, p_end=None):
+    """Per-point sums of walk monomials (walk enumeration, Sec. 5.3)."""
+    if p_end is None:
+        p_end = 1 << pb.k
+    out = np.zeros(p_end - p_begin, np.uint64)
+    nw = _load().or_brute_points(*pb._args(), qs, p_begin, p_end, _ptr(out))
+    if nw < 0:
+        raise ValueError("oracle brute force failed")
+    return out, nw
+
+
+def brute_det(pb: Problem, qs: int):
+    """Whole-sieve value from sum_walks prod(y) det(Z_walk)."""
+    q = np.zeros(1, np.uint64)
+    nw = _load().or_brute_det(*pb._args(), qs, _ptr(q))
+    if nw < 0:
+        raise ValueError("oracle det failed")
+    return int(q[0]), nw
+
+
+def count_paths(pb: Problem, limit=0):
+    """Exhaustive temporal DFS (Sec. 8.1 baseline): number of matching temporal
+    paths (stops at `limit` if > 0) and the first one found."""
+    fv = np.zeros(KMAX, np.uint32)
+    ft = np.zeros(KMAX, np.uint32)
+    c = _load().or_count_paths(*pb._args(), limit, _ptr(fv), _ptr(ft))
+    if c < 0:
+        raise ValueError("oracle dfs failed")
+    return int(c), fv[:pb.k].copy(), ft[:pb.k - 1].copy()
+
+
+def decide(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
+           t_min=0, t_max=0, seed=1, repeats=1, point_begin=0, point_end=0, alive=None, nthreads=0):
+    """Decision (Lemma 5.5): returns (found, sieve_sum, per_point) from the raw
+    edge list.  per_point covers [point_begin, point_end) (0,0 = all 2^k)."""
+    src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
+    npts = (1 << k) if point_end == 0 else point_end - point_begin
+    pp = np.zeros(max(npts, 1), np.uint64)
+    found = C.c_int(0)
+    q = u64(0)
+    al = None if alive is None else np.ascontiguousarray(np.asarray(alive, np.uint8))
+    rc = _load().or_decide(n, len(src), _ptr(src), _ptr(dst), _ptr(time), int(bool(undirected)), _ptr(color),
+                           num_colors, _ptr(al), k, _ptr(ms), start, end, t_min, t_max, seed, repeats,
+                           point_begin, point_end, C.byref(found), C.byref(q), _ptr(pp), nthreads)
+    if rc != 0:
+        raise ValueError("oracle decide: invalid input")
+    return bool(found.value), int(q.value), pp[:npts]
+
+
+def extract(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
+            t_min=0, t_max=0, seed=1, repeats=1, nthreads=0):
+    """Extraction by self-reducibility + temporal DFS (Sec. 5.9).  Returns
+    (found, verts[k], times[k-1], probes)."""
+    src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
+    verts = np.zeros(KMAX, np.uint32)
+    times = np.zeros(KMAX, np.uint32)
+    found = C.c_int(0)
+    probes = u32(0)
+    rc = _load().or_extract(n, len(src), _ptr(src), _ptr(dst), _ptr(time), int(bool(undirected)), _ptr(color),
+                            num_colors, k, _ptr(ms), start, end, t_min, t_max, seed, repeats, _ptr(verts),
+                            _ptr(times), C.byref(found), C.byref(probes), nthreads)
+    if rc != 0:
+        raise ValueError("oracle extract: invalid input")
+    return bool(found.value), verts[:k].copy(), times[:k - 1].copy(), int(probes.value)
