@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Benchmark of the temporal path-motif sieve on one GB300 (or N replicas).
+
+Workload: the mid-size decision of the benchmark suite -- a power-law
+out-degree temporal graph (exponent 2.1, n = 10^6, m = 10^7 edges, timestamps
+uniform in [1, 1000], 16 colours Zipf(1.0)) with a k = 6 multiset query (one
+colour twice), 2^6 = 64 sieve points, exact GF(2^64) arithmetic.  A step is one
+full decision on the resident graph: per-query arc filter and checkpoint
+build, sieve coefficients, the k-1 generating-function layers, the sieve sum.
+
+Metric: edge-steps/s = m * k * 2^k / (time of one decision).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 it runs under torchrun, one rank per GPU; every rank decides its own
+query (another seed) on its own replica of the graph -- the sieve points of
+different queries are independent, so there is no data-path collective
+("weak" scaling); ranks meet only at the timing barrier.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sieve edge-steps/s (m*k*2^k per s) at k=5..10; served query p50/p99 latency"
+UNIT = "edge-steps/s"
+WORKLOAD = ("power-law out-degree 2.1, n=1e6, m=1e7 (+50 planted arcs), t in [1,1000], 16 colours Zipf(1.0); "
+            "PathMotif k=6 with one colour twice, 64 sieve points, GF(2^64)")
+
+# GB300 integer issue limit: 152 SMs x 4 sub-partitions x 32 lanes (one warp
+# instruction per sub-partition per clock) x 2070 MHz maximum SM clock.  A
+# single integer pipe (ALU: LOP3/SHF/IADD, or FMA-heavy: IMAD) sustains half of
+# it; a throughput probe measured 58-60 lanes/SM/clk for each alone.
+INT_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
+
+# 32-bit integer instructions per GF(2^64) product of the register multiply
+# (Karatsuba over three 32x32 carry-less products with holes, plus the
+# reduction): ncu smsp__inst_executed of an isolated multiply loop / products
+# (99 ALU-pipe + 102 FMA-pipe instructions).
+OPS_PER_GF_MUL = 201.0
+
+# DRAM traffic of one layer launch from an ncu capture, valid only for the
+# layer-kernel source it was taken on (sha256 of csrc/sieve.cu, first 16 hex).
+LAYER_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="scale n and m of the workload (profiling captures of a smaller case)")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def source_sha():
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2001_07158_gb300", "csrc", "sieve.cu"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        self.out = tempfile.NamedTemporaryFile("w+", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait()
+        self.out.flush()
+        self.out.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        for line in self.out.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, flag in zip(self.NAMES, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.out.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def workload(scale=1.0):
+    import synth
+
+    if scale == 1.0:
+        return synth.config2_mid()
+    return synth.config2_mid(n=int(1_000_000 * scale), m=int(10_000_000 * scale))
+
+
+def cpu_baseline(g, q, points=None):
+    """The oracle as it stands (plain C, OpenMP over sieve points) on the host
+    cores, on a bounded sample of the same decision: `points` of the 64 sieve
+    points (one point per thread)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    P = points or max(1, min(cores, 16))
+    t0 = time.perf_counter()
+    oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed, point_begin=0,
+                  point_end=P, nthreads=min(P, cores))
+    dt = time.perf_counter() - t0
+    return {"value": g.m * q.k * P / dt, "unit": UNIT, "cores": min(P, cores), "kind": "oracle",
+            "sample": f"{P} of the {1 << q.k} sieve points of the same decision ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    g, q = workload(args.scale)
+    cores = os.cpu_count() or 1
+    P = max(1, min(cores, 8))
+    for _ in range(args.warmup):
+        cpu_baseline(g, q, P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = cpu_baseline(g, q, P)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = g.m * q.k * P / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": r["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2001_07158_gb300 as tm
+
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    g, q = workload(args.scale)
+    seed = q.seed + 7919 * rank
+    work_units = g.m * q.k * (1 << q.k)
+
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
+    for i in range(args.warmup):
+        tm.tmotif_decide(G, q.k, q.multiset, seed=seed + i)
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    sampler = ClockSampler(uuid)
+    tm.tmotif_set_profiling(G, True)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    found = []
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            starts[i].record(stream)
+        d = tm.tmotif_decide(G, q.k, q.multiset, seed=seed + 1000 + i, per_point=False)
+        ends[i].record(stream)
+        found.append(d.found)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    stats = tm.tmotif_get_stats(G)
+    tm.tmotif_set_profiling(G, False)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * work_units * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the layer kernel), from the library's
+    # CUDA events around every layer launch during the timed region
+    nl = max(stats["layer_launches"], 1)
+    layer_ms = stats["layer_ms"] / nl
+    muls = stats["layer_gf_muls"] / nl
+    achieved = muls * OPS_PER_GF_MUL / (layer_ms / 1e3) / 1e12
+    sha = source_sha()
+    traffic = LAYER_TRAFFIC["bytes_per_launch"] if LAYER_TRAFFIC["source_sha"] == sha else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": INT_PEAK_TOPS, "unit": "Tops/s",
+                "frac": achieved / INT_PEAK_TOPS, "traffic": traffic,
+                "kernel": "k_layer (eq. gen-polynomial:3 layer)", "layer_ms_per_launch": layer_ms,
+                "gf_muls_per_launch": muls, "ops_per_gf_mul": OPS_PER_GF_MUL,
+                "algorithmic_bytes_per_launch": stats["layer_bytes"] / nl,
+                "achieved_gbs": stats["layer_bytes"] / nl / (layer_ms / 1e3) / 1e9,
+                "layer_share_of_step": stats["layer_ms"] / total_ms if total_ms else None}
+
+    # end to end through the C ABI with host buffers: upload + build the graph,
+    # decide, read the result back, release
+    pin = {}
+    for name in ("src", "dst", "time"):
+        a = getattr(g, name)
+        tpin = torch.empty(len(a), dtype=torch.int32, pin_memory=True)
+        tpin.numpy().view(np.uint32)[:] = a
+        pin[name] = tpin
+    cpin = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+    cpin.numpy().view(np.uint32)[:] = g.color
+    e2e_times = []
+    for i in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = tm.tmotif_create_graph(g.n, pin["src"].numpy().view(np.uint32), pin["dst"].numpy().view(np.uint32),
+                                    pin["time"].numpy().view(np.uint32), cpin.numpy().view(np.uint32),
+                                    g.num_colors, stream=stream)
+        d2 = tm.tmotif_decide(G2, q.k, q.multiset, seed=seed + 5000 + i)
+        G2.close()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_t = torch.tensor([statistics.mean(e2e_times) if e2e_times else float("nan")], dtype=torch.float64,
+                         device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e = {"value": world * work_units / float(e2e_t.item()), "unit": UNIT,
+           "h2d_bytes_per_step": 12 * g.m + 4 * g.n + 4 * q.k,
+           "d2h_bytes_per_step": 8 * (1 << q.k) + 16, "ms_per_step": float(e2e_t.item()) * 1e3}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "k": int(q.k), "points": 1 << q.k,
+                       "multiset": [int(c) for c in q.multiset], "found_all": all(found),
+                       "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                       "parallelism": f"replicas x{world} (independent queries)"},
+            "clocks": clocks, "roofline": roofline, "e2e": e2e,
+            "gpu_launches": int(stats["launches"])}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, q)
+    if rank == 0:
+        print(json.dumps(line))
+    G.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * tmotif.h -- C ABI of the GB300 temporal path-motif sieve.
+ *
+ * The library decides PathMotif (Sec. 4.3 of Thejaswi, Gionis, Lauri, "Finding
+ * path motifs in large temporal graphs using algebraic fingerprints"): given a
+ * vertex-coloured temporal graph and a multiset M of k colours, is there a
+ * temporal path (k distinct vertices, arcs with strictly increasing
+ * timestamps, Sec. 3) whose vertex colours are exactly M?  It evaluates the
+ * constrained multilinear sieve of Lemma 5.5 over GF(2^64): the temporal-walk
+ * generating function of eq. (gen-polynomial:3) at 2^k sieve points, summed;
+ * a nonzero sum certifies a matching path.  Extraction follows Sec. 5.9 (self-
+ * reducibility with halving, then temporal DFS).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns TMOTIF_OK (0) or a TMOTIF_ERR_* code and never aborts
+ *     the process; tmotif_last_error() gives a message for the calling thread.
+ *   - Pointers in descriptors are HOST pointers owned by the caller; the
+ *     library copies what it keeps.  Outputs go to caller-owned host buffers.
+ *   - Handles are owned by the library and released by the matching destroy.
+ *   - Vertex ids are in [0, n).  Timestamps are >= 1 (Z_+, Sec. 3).
+ *   - 2 <= k <= TMOTIF_KMAX.  Colours are in [0, num_colors).
+ *   - A YES answer (found = 1) is always right: the sieve's error is one-sided
+ *     (Lemma 5.3/5.5).  A NO is wrong with probability at most
+ *     (2k-1)/2^64 per independent repeat (Sec. 5.5).
+ *   - Work runs on the CUDA stream given at graph creation (NULL = the legacy
+ *     default stream); calls return after their results are on the host.
+ *   - A graph handle is used by one thread at a time.
+ */
+#ifndef TMOTIF_H
+#define TMOTIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TMOTIF_ANY 0xFFFFFFFFu
+#define TMOTIF_KMAX 20
+
+enum {
+    TMOTIF_OK = 0,
+    TMOTIF_ERR_INVALID = 1,     /* malformed argument or graph              */
+    TMOTIF_ERR_OOM = 2,         /* device or host allocation failed         */
+    TMOTIF_ERR_CUDA = 3,        /* a CUDA call failed                       */
+    TMOTIF_ERR_TIMEOUT = 4,     /* a bounded device or host wait gave up    */
+    TMOTIF_ERR_UNSUPPORTED = 5, /* outside the supported range (e.g. k = 1) */
+    TMOTIF_ERR_NOT_FOUND = 6,   /* unknown ticket                           */
+    TMOTIF_ERR_BUSY = 7         /* over the admission budget; retry later   */
+};
+
+typedef struct tmotif_graph *tmotif_graph_t;   /* opaque, library-owned */
+typedef struct tmotif_server *tmotif_server_t; /* opaque, library-owned */
+
+/* A vertex-coloured temporal graph G^tau = (V, E^tau), Sec. 3.  Edge e is the
+ * triple (src[e], dst[e], time[e]); with undirected = 0 it is the arc
+ * src -> dst (moving from src to dst at that time); with undirected = 1 it
+ * stands for both arcs.  E^tau is a set: identical arcs are kept once and
+ * self-loops are dropped (tmotif_graph_info reports both counts).  Arrays are
+ * caller-owned host memory of m (edges) and n (colours) entries. */
+typedef struct {
+    uint32_t n;
+    uint64_t m;
+    const uint32_t *src, *dst, *time;
+    const uint32_t *color;
+    uint32_t num_colors;
+    uint32_t undirected;
+    void *cuda_stream; /* cudaStream_t used for every call on this graph */
+} tmotif_graph_desc;
+
+/* A PathMotif query (Sec. 4.3), with the (s,d) variant of Sec. 6.1 as start/
+ * end vertices and the latest-time restriction of Sec. 5.8 as a window.
+ *   multiset      k colours in any order (caller-owned host array);
+ *   start, end    TMOTIF_ANY or the required first / last vertex; M must count
+ *                 their colours;
+ *   t_min, t_max  only arcs with t_min <= time <= t_max are used (t_max = 0:
+ *                 no upper bound);
+ *   seed          selects the random evaluation point; repeats >= 1
+ *                 independent evaluations, found = OR over them;
+ *   point_begin, point_end  0,0 = all 2^k sieve points; otherwise only the
+ *                 points [point_begin, point_end) are evaluated (sharding a
+ *                 query across devices; combine the per-point sums by XOR). */
+typedef struct {
+    uint32_t k;
+    const uint32_t *multiset;
+    uint32_t start, end;
+    uint32_t t_min, t_max;
+    uint64_t seed;
+    uint32_t repeats;
+    uint32_t point_begin, point_end;
+} tmotif_query;
+
+/* Result of tmotif_decide.  per_point is caller-owned and optional (NULL or
+ * room for point_end - point_begin values, 2^k when both are 0); it receives
+ * the sieve sums Q^A of the first repeat, point p <-> A = {j : bit j of p}.
+ * sieve_sum is their XOR; ms is the device time of the call. */
+typedef struct {
+    int found;
+    uint64_t sieve_sum;
+    uint64_t *per_point;
+    double ms;
+} tmotif_decision;
+
+typedef struct {
+    uint32_t n;
+    uint64_t m_input;     /* edges passed in                               */
+    uint64_t m_arcs;      /* canonical arcs kept on the device              */
+    uint64_t self_loops;  /* dropped                                        */
+    uint64_t duplicates;  /* identical arcs merged                          */
+    uint32_t max_time;
+    uint64_t device_bytes;/* resident graph plus current workspace         */
+} tmotif_graph_info;
+
+/* Cumulative device time per kernel family (CUDA events on the graph's
+ * stream), recorded only while profiling is on.  bytes_* count the
+ * algorithmic traffic the layer kernels were asked to move. */
+typedef struct {
+    uint64_t launches;         /* every kernel this library launched        */
+    uint64_t layer_launches;
+    double layer_ms;           /* generating-function layers (eq. 3)        */
+    double prep_ms;            /* per-query filter, segments, checkpoints   */
+    double coef_ms;            /* sieve coefficients x_u^A (eq. motif:1)    */
+    double other_ms;
+    uint64_t layer_arc_lanes;  /* arcs x lanes processed by layer kernels   */
+    uint64_t layer_cp_lanes;   /* checkpoints x lanes written               */
+    uint64_t layer_bytes;      /* algorithmic bytes of the layer kernels    */
+    uint64_t layer_gf_muls;    /* GF(2^64) products in the layer kernels    */
+} tmotif_stats;
+
+/* Build the resident graph: validate, orient, drop self-loops, merge
+ * duplicates, sort arcs by (dst, time, src) and upload.  Errors: INVALID for
+ * an id >= n, time 0 or colour >= num_colors; OOM; CUDA. */
+int tmotif_create_graph(const tmotif_graph_desc *desc, tmotif_graph_t *out);
+void tmotif_destroy_graph(tmotif_graph_t g);
+int tmotif_graph_get_info(tmotif_graph_t g, tmotif_graph_info *info);
+
+/* Decide PathMotif (Lemma 5.5 on eq. gen-polynomial:3, Lemma 5.4 time and
+ * O(m L) space per lane batch of L points).  Errors: INVALID (bad multiset
+ * colour, start/end out of range, repeats 0, bad point range), UNSUPPORTED
+ * (k outside [2, TMOTIF_KMAX]), OOM, CUDA. */
+int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out);
+
+/* Extract one matching temporal path by self-reducibility (Sec. 5.9): verts
+ * receives k vertex ids in path order and times the k-1 arc timestamps
+ * (caller-owned).  found = 0 when no path exists.  The probe order is fixed:
+ * candidates (vertices whose colour is in M) in ascending id; a block of
+ * candidates is removed when the query stays YES without it, otherwise it is
+ * halved; probe i uses seed mix(seed ^ i * 0xD1B54A32D192ED03); the survivors
+ * go to a temporal DFS over start vertices in ascending id and arcs in
+ * (time, dst) order.  Errors as tmotif_decide. */
+int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uint32_t *times, int *found);
+
+/* Decide many (graph, query) pairs in one pass: every query runs its sieve
+ * and the per-query phases of all of them share persistent launches (the
+ * batched form for many small graphs).  out has count entries.  Graphs must
+ * share one CUDA stream.  Errors as tmotif_decide; on error no result is
+ * valid. */
+int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_query *queries, uint32_t count,
+                        tmotif_decision *out);
+
+/* Serving: a request loop that admits decide/extract requests against
+ * resident graphs while the device memory they need fits hbm_budget_bytes,
+ * runs admitted requests concurrently on the device and completes them
+ * asynchronously.  tmotif_submit copies the query and returns a ticket at
+ * once (BUSY if the request alone exceeds the budget); tmotif_poll reports
+ * done = 1 with the result once finished (verts/times may be NULL for
+ * decide requests; they need room for k and k-1 entries otherwise).  A
+ * finished ticket is forgotten after it is polled. */
+int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *out);
+int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_query *q, int is_extract, uint64_t *ticket);
+int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *out, uint32_t *verts, uint32_t *times,
+                int *done);
+void tmotif_server_destroy(tmotif_server_t s);
+
+/* Profiling counters for a graph (see tmotif_stats).  set_profiling(g, 1)
+ * enables per-kernel events and clears the counters. */
+int tmotif_set_profiling(tmotif_graph_t g, int on);
+int tmotif_get_stats(tmotif_graph_t g, tmotif_stats *out);
+
+/* Diagnostic: out[i] = a[i] * b[i] in GF(2^64) computed by the device
+ * multiply of the sieve kernels (host arrays of n entries). */
+int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n);
+
+/* Message for the last error on the calling thread (never NULL). */
+const char *tmotif_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMOTIF_H */

@@ -54,6 +54,7 @@ def _load():
         sig = {
             "or_gf_mul": (u64, [u64, u64]),
             "or_gf_pow": (u64, [u64, u64]),
+            "or_gf_mul_batch": (None, [P, P, P, u64]),
             "or_gf_inv": (u64, [u64]),
             "or_fmix64": (u64, [u64]),
             "or_query_seed": (u64, [u64, u32]),
@@ -100,6 +101,15 @@ def _ptr(a):
 def gf_mul(a: int, b: int) -> int:
     """Product in GF(2^64) = GF(2)[x]/(x^64 + x^4 + x^3 + x + 1)."""
     return _load().or_gf_mul(a, b)
+
+
+def gf_mul_batch(a, b):
+    """Element-wise products of two uint64 arrays."""
+    a = np.ascontiguousarray(np.asarray(a, np.uint64))
+    b = np.ascontiguousarray(np.asarray(b, np.uint64))
+    out = np.zeros_like(a)
+    _load().or_gf_mul_batch(_ptr(a), _ptr(b), _ptr(out), len(a))
+    return out
 
 
 def gf_pow(a: int, e: int) -> int:

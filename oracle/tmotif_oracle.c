@@ -70,6 +70,12 @@ u64 or_gf_mul(u64 a, u64 b)
     return r;
 }
 
+/* out[i] = a[i] * b[i] for i < n (the product above, in a loop). */
+void or_gf_mul_batch(const u64 *a, const u64 *b, u64 *out, u64 n)
+{
+    for (u64 i = 0; i < n; i++) out[i] = or_gf_mul(a[i], b[i]);
+}
+
 u64 or_gf_pow(u64 a, u64 e)
 {
     u64 r = 1;

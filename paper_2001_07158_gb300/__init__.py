@@ -1,0 +1,283 @@
+"""Python binding of the GB300 temporal path-motif sieve (libtmotif.so).
+
+Argument marshalling only: every step of the sieve runs in the CUDA library
+behind ``include/tmotif.h``.  Functions carry the C names.  Importing the
+package loads the in-tree library and raises if it has not been built; there
+is no CPU fallback.
+
+Method: Thejaswi, Gionis, Lauri, "Finding path motifs in large temporal graphs
+using algebraic fingerprints" -- the constrained multilinear sieve (Lemma 5.5)
+over the temporal-walk generating function (eq. gen-polynomial:3) in GF(2^64),
+and extraction by self-reducibility (Sec. 5.9).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+TMOTIF_ANY = 0xFFFFFFFF
+TMOTIF_KMAX = 20
+ERRORS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "NOT_FOUND", 7: "BUSY"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtmotif.so")
+
+
+class TmotifError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tmotif error {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _GraphDesc(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("m", C.c_uint64), ("src", C.c_void_p), ("dst", C.c_void_p),
+                ("time", C.c_void_p), ("color", C.c_void_p), ("num_colors", C.c_uint32),
+                ("undirected", C.c_uint32), ("cuda_stream", C.c_void_p)]
+
+
+class _Query(C.Structure):
+    _fields_ = [("k", C.c_uint32), ("multiset", C.c_void_p), ("start", C.c_uint32), ("end", C.c_uint32),
+                ("t_min", C.c_uint32), ("t_max", C.c_uint32), ("seed", C.c_uint64), ("repeats", C.c_uint32),
+                ("point_begin", C.c_uint32), ("point_end", C.c_uint32)]
+
+
+class _Decision(C.Structure):
+    _fields_ = [("found", C.c_int), ("sieve_sum", C.c_uint64), ("per_point", C.c_void_p), ("ms", C.c_double)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("m_input", C.c_uint64), ("m_arcs", C.c_uint64), ("self_loops", C.c_uint64),
+                ("duplicates", C.c_uint64), ("max_time", C.c_uint32), ("device_bytes", C.c_uint64)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("layer_launches", C.c_uint64), ("layer_ms", C.c_double),
+                ("prep_ms", C.c_double), ("coef_ms", C.c_double), ("other_ms", C.c_double),
+                ("layer_arc_lanes", C.c_uint64), ("layer_cp_lanes", C.c_uint64), ("layer_bytes", C.c_uint64),
+                ("layer_gf_muls", C.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtmotif.so is not built ({LIB_PATH}); run paper_2001_07158_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "tmotif_create_graph": (C.c_int, [C.POINTER(_GraphDesc), C.POINTER(P)]),
+        "tmotif_destroy_graph": (None, [P]),
+        "tmotif_graph_get_info": (C.c_int, [P, C.POINTER(_Info)]),
+        "tmotif_decide": (C.c_int, [P, C.POINTER(_Query), C.POINTER(_Decision)]),
+        "tmotif_extract": (C.c_int, [P, C.POINTER(_Query), P, P, C.POINTER(C.c_int)]),
+        "tmotif_decide_batch": (C.c_int, [P, P, C.c_uint32, P]),
+        "tmotif_server_create": (C.c_int, [C.c_size_t, C.POINTER(P)]),
+        "tmotif_submit": (C.c_int, [P, P, C.POINTER(_Query), C.c_int, C.POINTER(C.c_uint64)]),
+        "tmotif_poll": (C.c_int, [P, C.c_uint64, C.POINTER(_Decision), P, P, C.POINTER(C.c_int)]),
+        "tmotif_server_destroy": (None, [P]),
+        "tmotif_set_profiling": (C.c_int, [P, C.c_int]),
+        "tmotif_get_stats": (C.c_int, [P, C.POINTER(_Stats)]),
+        "tmotif_gf_mul_batch": (C.c_int, [P, P, P, C.c_uint64]),
+        "tmotif_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc):
+    if rc != 0:
+        raise TmotifError(rc, _lib.tmotif_last_error().decode())
+
+
+def _u32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+@dataclass
+class Decision:
+    found: bool
+    sieve_sum: int
+    per_point: np.ndarray | None
+    ms: float
+
+
+class Graph:
+    """A resident graph handle (tmotif_graph_t)."""
+
+    def __init__(self, handle, n, num_colors, keep):
+        self._h = handle
+        self.n = n
+        self.num_colors = num_colors
+        self._keep = keep
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.tmotif_destroy_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tmotif_create_graph(n, src, dst, time, color, num_colors, undirected=False, stream=None) -> Graph:
+    src, dst, time, color = _u32(src), _u32(dst), _u32(time), _u32(color)
+    d = _GraphDesc(n, len(src), src.ctypes.data, dst.ctypes.data, time.ctypes.data, color.ctypes.data,
+                   num_colors, int(bool(undirected)), _stream_handle(stream))
+    h = C.c_void_p()
+    _check(_lib.tmotif_create_graph(C.byref(d), C.byref(h)))
+    return Graph(h.value, n, num_colors, None)
+
+
+def tmotif_destroy_graph(g: Graph):
+    g.close()
+
+
+def tmotif_graph_get_info(g: Graph) -> dict:
+    info = _Info()
+    _check(_lib.tmotif_graph_get_info(g.handle, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in _Info._fields_}
+
+
+def _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end):
+    ms = _u32(multiset)
+    q = _Query(k, ms.ctypes.data, start, end, t_min, t_max, seed & (2**64 - 1), repeats, point_begin, point_end)
+    return q, ms
+
+
+def tmotif_decide(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
+                  repeats=1, point_begin=0, point_end=0, per_point=True) -> Decision:
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end)
+    npts = (1 << k) if point_end == 0 else max(point_end - point_begin, 0)
+    pp = np.zeros(max(npts, 1), np.uint64) if per_point else None
+    d = _Decision(0, 0, pp.ctypes.data if per_point else None, 0.0)
+    _check(_lib.tmotif_decide(g.handle, C.byref(q), C.byref(d)))
+    return Decision(bool(d.found), int(d.sieve_sum), pp[:npts] if per_point else None, float(d.ms))
+
+
+def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
+                   repeats=1):
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0)
+    verts = np.zeros(k, np.uint32)
+    times = np.zeros(max(k - 1, 1), np.uint32)
+    found = C.c_int(0)
+    _check(_lib.tmotif_extract(g.handle, C.byref(q), verts.ctypes.data, times.ctypes.data, C.byref(found)))
+    return bool(found.value), verts, times[:k - 1]
+
+
+def tmotif_decide_batch(graphs, queries):
+    """queries: list of dicts with the keyword arguments of tmotif_decide."""
+    n = len(graphs)
+    hs = (C.c_void_p * n)(*[g.handle for g in graphs])
+    qarr = (_Query * n)()
+    keep = []
+    pps = []
+    darr = (_Decision * n)()
+    for i, qd in enumerate(queries):
+        qd = dict(qd)
+        k = qd.pop("k")
+        ms = qd.pop("multiset")
+        q, kp = _query(k, ms, qd.get("start", TMOTIF_ANY), qd.get("end", TMOTIF_ANY), qd.get("t_min", 0),
+                       qd.get("t_max", 0), qd.get("seed", 1), qd.get("repeats", 1), 0, 0)
+        qarr[i] = q
+        keep.append(kp)
+        pp = np.zeros(1 << k, np.uint64)
+        pps.append(pp)
+        darr[i] = _Decision(0, 0, pp.ctypes.data, 0.0)
+    _check(_lib.tmotif_decide_batch(hs, qarr, n, darr))
+    return [Decision(bool(darr[i].found), int(darr[i].sieve_sum), pps[i], float(darr[i].ms)) for i in range(n)]
+
+
+def tmotif_set_profiling(g: Graph, on=True):
+    _check(_lib.tmotif_set_profiling(g.handle, int(bool(on))))
+
+
+def tmotif_get_stats(g: Graph) -> dict:
+    s = _Stats()
+    _check(_lib.tmotif_get_stats(g.handle, C.byref(s)))
+    return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+def tmotif_gf_mul_batch(a, b) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, np.uint64))
+    b = np.ascontiguousarray(np.asarray(b, np.uint64))
+    out = np.zeros_like(a)
+    _check(_lib.tmotif_gf_mul_batch(a.ctypes.data, b.ctypes.data, out.ctypes.data, len(a)))
+    return out
+
+
+def tmotif_last_error() -> str:
+    return _lib.tmotif_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# Serving (tmotif_server_*)
+# ---------------------------------------------------------------------------
+class Server:
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.tmotif_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tmotif_server_create(hbm_budget_bytes: int) -> Server:
+    h = C.c_void_p()
+    _check(_lib.tmotif_server_create(hbm_budget_bytes, C.byref(h)))
+    return Server(h.value)
+
+
+def tmotif_submit(s: Server, g: Graph, k, multiset, *, is_extract=False, start=TMOTIF_ANY, end=TMOTIF_ANY,
+                  t_min=0, t_max=0, seed=1, repeats=1) -> int:
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0)
+    t = C.c_uint64(0)
+    _check(_lib.tmotif_submit(s.handle, g.handle, C.byref(q), int(bool(is_extract)), C.byref(t)))
+    return int(t.value)
+
+
+def tmotif_poll(s: Server, ticket: int, k: int):
+    d = _Decision(0, 0, None, 0.0)
+    verts = np.zeros(max(k, 1), np.uint32)
+    times = np.zeros(max(k, 1), np.uint32)
+    done = C.c_int(0)
+    _check(_lib.tmotif_poll(s.handle, ticket, C.byref(d), verts.ctypes.data, times.ctypes.data, C.byref(done)))
+    if not done.value:
+        return None
+    return Decision(bool(d.found), int(d.sieve_sum), None, float(d.ms)), verts[:k], times[:k - 1]
+
+
+def tmotif_server_destroy(s: Server):
+    s.close()

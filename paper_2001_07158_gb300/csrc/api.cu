@@ -1,0 +1,356 @@
+// api.cu -- the extern "C" entry points of include/tmotif.h, error handling,
+// device buffers, profiling and graph residency.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gf64.cuh"
+#include "internal.h"
+
+namespace tmo {
+
+static thread_local std::string g_last_error = "no error";
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+Status fail(int code, const std::string &msg)
+{
+    set_error(msg);
+    Status s;
+    s.code = code;
+    return s;
+}
+
+Status cuda_fail(cudaError_t e, const char *what)
+{
+    std::string msg = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    int code = (e == cudaErrorMemoryAllocation) ? TMOTIF_ERR_OOM : TMOTIF_ERR_CUDA;
+    cudaGetLastError();  // clear sticky-free errors so later calls can proceed
+    return fail(code, msg);
+}
+
+Status DevBuf::reserve(size_t need)
+{
+    if (need <= bytes && p) return Status();
+    release();
+    size_t want = std::max<size_t>(need, 256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    bytes = want;
+    return Status();
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+void Workspace::release()
+{
+    DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &keep, &pos,
+                     &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive};
+    for (DevBuf *b : all) b->release();
+    if (host_pinned) cudaFreeHost(host_pinned);
+    host_pinned = nullptr;
+    host_pinned_bytes = 0;
+}
+
+size_t Workspace::bytes() const
+{
+    const DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &keep, &pos,
+                           &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive};
+    size_t s = 0;
+    for (const DevBuf *b : all) s += b->bytes;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Profiler
+// ---------------------------------------------------------------------------
+Status Profiler::begin(cudaStream_t s, cudaEvent_t *a)
+{
+    *a = nullptr;
+    if (!on) return Status();
+    if (used + 2 > pool.size()) {
+        for (int i = 0; i < 16; i++) {
+            cudaEvent_t e;
+            TM_CUDA(cudaEventCreate(&e));
+            pool.push_back(e);
+        }
+    }
+    *a = pool[used++];
+    TM_CUDA(cudaEventRecord(*a, s));
+    return Status();
+}
+
+Status Profiler::end(cudaStream_t s, cudaEvent_t a, int family)
+{
+    if (!on || !a) return Status();
+    cudaEvent_t b = pool[used++];
+    TM_CUDA(cudaEventRecord(b, s));
+    pending.push_back({a, b, family});
+    return Status();
+}
+
+Status Profiler::collect()
+{
+    if (!on) return Status();
+    for (const Pending &p : pending) {
+        TM_CUDA(cudaEventSynchronize(p.b));
+        float ms = 0;
+        TM_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+        if (p.family == FAM_LAYER) stats.layer_ms += ms;
+        else if (p.family == FAM_PREP) stats.prep_ms += ms;
+        else if (p.family == FAM_COEF) stats.coef_ms += ms;
+        else stats.other_ms += ms;
+    }
+    pending.clear();
+    used = 0;
+    return Status();
+}
+
+void Profiler::destroy()
+{
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+    pending.clear();
+    used = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Graph residency: validate, orient, drop self-loops, merge duplicates, sort
+// arcs by (dst, time, src), upload.  E^tau is a set of triples (Sec. 3).
+// ---------------------------------------------------------------------------
+struct HArc {
+    u32 dst, time, src;
+};
+
+Status build_graph(const tmotif_graph_desc *d, Graph *g)
+{
+    if (!d) return fail(TMOTIF_ERR_INVALID, "null graph descriptor");
+    if (d->num_colors == 0) return fail(TMOTIF_ERR_INVALID, "num_colors must be >= 1");
+    if (d->n > 0 && !d->color) return fail(TMOTIF_ERR_INVALID, "null color array");
+    if (d->m > 0 && (!d->src || !d->dst || !d->time)) return fail(TMOTIF_ERR_INVALID, "null edge array");
+    const u64 cap = d->undirected ? 2 * d->m : d->m;
+    if (cap >= 0xFFFFFFFFull) return fail(TMOTIF_ERR_UNSUPPORTED, "more than 2^32-2 arcs");
+    for (u32 u = 0; u < d->n; u++)
+        if (d->color[u] >= d->num_colors) return fail(TMOTIF_ERR_INVALID, "color out of range");
+    std::vector<HArc> arcs;
+    try {
+        arcs.reserve(cap);
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed");
+    }
+    u64 loops = 0;
+    u32 tmax = 0;
+    for (u64 e = 0; e < d->m; e++) {
+        const u32 a = d->src[e], b = d->dst[e], t = d->time[e];
+        if (a >= d->n || b >= d->n) return fail(TMOTIF_ERR_INVALID, "vertex id out of range");
+        if (t == 0) return fail(TMOTIF_ERR_INVALID, "timestamp 0 (timestamps are >= 1)");
+        if (a == b) { loops++; continue; }
+        tmax = std::max(tmax, t);
+        arcs.push_back({b, t, a});
+        if (d->undirected) arcs.push_back({a, t, b});
+    }
+    std::sort(arcs.begin(), arcs.end(), [](const HArc &x, const HArc &y) {
+        if (x.dst != y.dst) return x.dst < y.dst;
+        if (x.time != y.time) return x.time < y.time;
+        return x.src < y.src;
+    });
+    u64 w = 0;
+    for (u64 e = 0; e < arcs.size(); e++) {
+        if (w > 0 && arcs[w - 1].dst == arcs[e].dst && arcs[w - 1].time == arcs[e].time &&
+            arcs[w - 1].src == arcs[e].src)
+            continue;
+        arcs[w++] = arcs[e];
+    }
+    g->n = d->n;
+    g->m_input = d->m;
+    g->m = w;
+    g->self_loops = loops;
+    g->duplicates = arcs.size() - w;
+    g->num_colors = d->num_colors;
+    g->max_time = tmax;
+    g->stream = (cudaStream_t)d->cuda_stream;
+    g->h_color.assign(d->color, d->color + d->n);
+    std::vector<u32> hs(w), hd(w), ht(w);
+    for (u64 e = 0; e < w; e++) { hs[e] = arcs[e].src; hd[e] = arcs[e].dst; ht[e] = arcs[e].time; }
+    arcs.clear();
+    arcs.shrink_to_fit();
+    const u64 mb = std::max<u64>(w, 1) * 4;
+    TM_CUDA(cudaMalloc(&g->d_src, mb));
+    TM_CUDA(cudaMalloc(&g->d_dst, mb));
+    TM_CUDA(cudaMalloc(&g->d_time, mb));
+    TM_CUDA(cudaMalloc(&g->d_color, std::max<u64>(d->n, 1) * 4));
+    g->resident_bytes = 3 * mb + std::max<u64>(d->n, 1) * 4;
+    TM_CUDA(cudaMemcpyAsync(g->d_src, hs.data(), w * 4, cudaMemcpyHostToDevice, g->stream));
+    TM_CUDA(cudaMemcpyAsync(g->d_dst, hd.data(), w * 4, cudaMemcpyHostToDevice, g->stream));
+    TM_CUDA(cudaMemcpyAsync(g->d_time, ht.data(), w * 4, cudaMemcpyHostToDevice, g->stream));
+    TM_CUDA(cudaMemcpyAsync(g->d_color, d->color, (u64)d->n * 4, cudaMemcpyHostToDevice, g->stream));
+    TM_CUDA(cudaStreamSynchronize(g->stream));
+    return Status();
+}
+
+static void free_graph(Graph *g)
+{
+    if (!g) return;
+    if (g->d_src) cudaFree(g->d_src);
+    if (g->d_dst) cudaFree(g->d_dst);
+    if (g->d_time) cudaFree(g->d_time);
+    if (g->d_color) cudaFree(g->d_color);
+    g->ws.release();
+    g->prof.destroy();
+    delete static_cast<tmotif_graph *>(g);
+}
+
+Status parse_query(const Graph &g, const tmotif_query *q, QuerySpec *out)
+{
+    if (!q) return fail(TMOTIF_ERR_INVALID, "null query");
+    if (q->k < 2 || q->k > TMOTIF_KMAX)
+        return fail(TMOTIF_ERR_UNSUPPORTED, "k must be in [2, " + std::to_string(TMOTIF_KMAX) + "]");
+    if (!q->multiset) return fail(TMOTIF_ERR_INVALID, "null multiset");
+    if (q->repeats < 1) return fail(TMOTIF_ERR_INVALID, "repeats must be >= 1");
+    if (q->start != TMOTIF_ANY && q->start >= g.n) return fail(TMOTIF_ERR_INVALID, "start vertex out of range");
+    if (q->end != TMOTIF_ANY && q->end >= g.n) return fail(TMOTIF_ERR_INVALID, "end vertex out of range");
+    out->k = q->k;
+    out->multiset.assign(q->multiset, q->multiset + q->k);
+    for (u32 c : out->multiset)
+        if (c >= g.num_colors) return fail(TMOTIF_ERR_INVALID, "multiset colour out of range");
+    out->start = q->start;
+    out->end = q->end;
+    out->t_min = q->t_min;
+    out->t_max = q->t_max;
+    out->seed = q->seed;
+    out->repeats = q->repeats;
+    const u64 full = 1ull << q->k;
+    if (q->point_begin == 0 && q->point_end == 0) {
+        out->p_begin = 0;
+        out->p_end = full;
+    } else {
+        if (q->point_begin >= q->point_end || q->point_end > full)
+            return fail(TMOTIF_ERR_INVALID, "bad point range");
+        out->p_begin = q->point_begin;
+        out->p_end = q->point_end;
+    }
+    return Status();
+}
+
+}  // namespace tmo
+
+using namespace tmo;
+
+
+extern "C" {
+
+int tmotif_create_graph(const tmotif_graph_desc *desc, tmotif_graph_t *out)
+{
+    if (!out) return fail(TMOTIF_ERR_INVALID, "null output handle").code;
+    *out = nullptr;
+    tmotif_graph *g = nullptr;
+    try {
+        g = new tmotif_graph();
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
+    Status s;
+    try {
+        s = build_graph(desc, g);
+    } catch (const std::bad_alloc &) {
+        s = fail(TMOTIF_ERR_OOM, "host allocation failed");
+    }
+    if (!s.ok()) {
+        free_graph(g);
+        return s.code;
+    }
+    *out = g;
+    return TMOTIF_OK;
+}
+
+void tmotif_destroy_graph(tmotif_graph_t g) { free_graph(g); }
+
+int tmotif_graph_get_info(tmotif_graph_t g, tmotif_graph_info *info)
+{
+    if (!g || !info) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    info->n = g->n;
+    info->m_input = g->m_input;
+    info->m_arcs = g->m;
+    info->self_loops = g->self_loops;
+    info->duplicates = g->duplicates;
+    info->max_time = g->max_time;
+    info->device_bytes = g->resident_bytes + g->ws.bytes();
+    return TMOTIF_OK;
+}
+
+int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out)
+{
+    if (!g || !out) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    try {
+        QuerySpec qs;
+        Status s = parse_query(*g, q, &qs);
+        if (!s.ok()) return s.code;
+        int found = 0;
+        u64 sum = 0;
+        double ms = 0;
+        s = sieve_decide(*g, qs, nullptr, &found, &sum, (u64 *)out->per_point, &ms);
+        if (!s.ok()) return s.code;
+        out->found = found;
+        out->sieve_sum = sum;
+        out->ms = ms;
+        return TMOTIF_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
+}
+
+int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uint32_t *times, int *found)
+{
+    if (!g || !verts || !times || !found) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    try {
+        QuerySpec qs;
+        Status s = parse_query(*g, q, &qs);
+        if (!s.ok()) return s.code;
+        if (qs.p_begin != 0 || qs.p_end != (1ull << qs.k))
+            return fail(TMOTIF_ERR_INVALID, "extraction needs the full point range").code;
+        u32 probes = 0;
+        s = extract_path(*g, qs, verts, times, found, &probes);
+        return s.code;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
+}
+
+int tmotif_set_profiling(tmotif_graph_t g, int on)
+{
+    if (!g) return fail(TMOTIF_ERR_INVALID, "null graph").code;
+    g->prof.on = on != 0;
+    std::memset(&g->prof.stats, 0, sizeof(g->prof.stats));
+    g->prof.pending.clear();
+    g->prof.used = 0;
+    return TMOTIF_OK;
+}
+
+int tmotif_get_stats(tmotif_graph_t g, tmotif_stats *out)
+{
+    if (!g || !out) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    *out = g->prof.stats;
+    return TMOTIF_OK;
+}
+
+int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n)
+{
+    if (n && (!a || !b || !out)) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    return gf_mul_batch((const u64 *)a, (const u64 *)b, (u64 *)out, n).code;
+}
+
+const char *tmotif_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

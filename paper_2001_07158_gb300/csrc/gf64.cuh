@@ -1,0 +1,162 @@
+// gf64.cuh -- GF(2^64) arithmetic and counter-based coefficients on sm_103a.
+//
+// Field: GF(2)[x] / (x^64 + x^4 + x^3 + x + 1), polynomial basis, bit i of a
+// 64-bit word is the coefficient of x^i.  Addition is XOR.  The paper fixes
+// only the field size (b = 64, Sec. 5.5 and Sec. 7); the modulus is the
+// standard pentanomial for this size.
+//
+// Multiplication (carry-less product then reduction) is built from 32-bit
+// integer multiplies: GB300 has no carry-less multiply instruction, so each
+// 32x32 carry-less product spreads both operands over four residue classes
+// (bits 0 mod 4, 1 mod 4, ...) with three-bit holes between set bits; an
+// ordinary integer product of two such spread words counts at most 8 partial
+// products per output bit, which stays inside its 4-bit slot, so the parity
+// of each slot is the carry-less bit ("multiplication with holes").  Three
+// such products form the 64x64 product by Karatsuba.  The table form in
+// gf_mul_table() serves multipliers shared by many sieve lanes.
+#pragma once
+#include <stdint.h>
+
+namespace tmo {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// 32 x 32 -> 64 carry-less product.
+__device__ __forceinline__ u64 clmul32(u32 a, u32 b)
+{
+    const u32 m0 = 0x11111111u, m1 = 0x22222222u, m2 = 0x44444444u, m3 = 0x88888888u;
+    u32 a0 = a & m0, a1 = a & m1, a2 = a & m2, a3 = a & m3;
+    u32 b0 = b & m0, b1 = b & m1, b2 = b & m2, b3 = b & m3;
+    u64 c0 = ((u64)a0 * b0) ^ ((u64)a1 * b3) ^ ((u64)a2 * b2) ^ ((u64)a3 * b1);
+    u64 c1 = ((u64)a0 * b1) ^ ((u64)a1 * b0) ^ ((u64)a2 * b3) ^ ((u64)a3 * b2);
+    u64 c2 = ((u64)a0 * b2) ^ ((u64)a1 * b1) ^ ((u64)a2 * b0) ^ ((u64)a3 * b3);
+    u64 c3 = ((u64)a0 * b3) ^ ((u64)a1 * b2) ^ ((u64)a2 * b1) ^ ((u64)a3 * b0);
+    return (c0 & 0x1111111111111111ull) | (c1 & 0x2222222222222222ull) |
+           (c2 & 0x4444444444444444ull) | (c3 & 0x8888888888888888ull);
+}
+
+// Reduce hi * x^64 + lo modulo f.  x^64 = x^4 + x^3 + x + 1, so hi * x^64
+// folds to hi ^ hi<<1 ^ hi<<3 ^ hi<<4 plus the <= 4 bits pushed past x^63,
+// which fold once more without overflowing.
+__device__ __forceinline__ u64 gf_reduce(u64 lo, u64 hi)
+{
+    u64 over = (hi >> 63) ^ (hi >> 61) ^ (hi >> 60);
+    return lo ^ hi ^ (hi << 1) ^ (hi << 3) ^ (hi << 4) ^ over ^ (over << 1) ^ (over << 3) ^ (over << 4);
+}
+
+__device__ __forceinline__ u64 gf_mul(u64 a, u64 b)
+{
+    u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
+    u64 lo = clmul32(al, bl);
+    u64 hi = clmul32(ah, bh);
+    u64 mid = clmul32(al ^ ah, bl ^ bh) ^ lo ^ hi;
+    return gf_reduce(lo ^ (mid << 32), hi ^ (mid >> 32));
+}
+
+// a * x^s mod f for 0 <= s < 61 (the bits shifted out are < 2^s, and
+// hi * (x^4 + x^3 + x + 1) < 2^(s+4) <= 2^64, so one fold suffices).
+__device__ __forceinline__ u64 gf_mul_xpow(u64 a, int s)
+{
+    if (s == 0) return a;
+    u64 hi = a >> (64 - s);
+    return (a << s) ^ hi ^ (hi << 1) ^ (hi << 3) ^ (hi << 4);
+}
+
+// a * x mod f.
+__device__ __forceinline__ u64 gf_mul_x(u64 a)
+{
+    return (a << 1) ^ ((u64)((long long)a >> 63) & 0x1Bull);
+}
+
+// ---------------------------------------------------------------------------
+// Products by a multiplier y shared by many lanes: a 16 x 16 table
+// tab[i][b] = y * b * x^(4i) mod f (i = nibble position, b = nibble value),
+// so y * s = XOR_i tab[i][nibble_i(s)] -- 16 shared-memory loads instead of a
+// full carry-less product.  A team of `nthreads` threads builds the 256
+// entries together (each thread 256/nthreads of them, nthreads in {8,16,32}).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthreads)
+{
+    const int per = 256 / nthreads;           // 8, 16 or 32 entries
+    const int first = tt * per;               // first entry index i*16 + b
+    for (int e0 = first; e0 < first + per; e0 += 8) {
+        const int i = e0 >> 4, h = (e0 >> 3) & 1;
+        const u64 b0 = gf_mul_xpow(y, 4 * i);
+        const u64 b1 = gf_mul_x(b0), b2 = gf_mul_x(b1);
+        const u64 base = h ? gf_mul_x(b2) : 0ull;
+        ulonglong2 *t = (ulonglong2 *)(tab + e0);
+        t[0] = make_ulonglong2(base, base ^ b0);
+        t[1] = make_ulonglong2(base ^ b1, base ^ b1 ^ b0);
+        t[2] = make_ulonglong2(base ^ b2, base ^ b2 ^ b0);
+        t[3] = make_ulonglong2(base ^ b2 ^ b1, base ^ b2 ^ b1 ^ b0);
+    }
+}
+
+__device__ __forceinline__ u64 gf_table_mul(const u64 *tab, u64 s)
+{
+    const u32 lo = (u32)s, hi = (u32)(s >> 32);
+    u64 r = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r ^= tab[i * 16 + ((lo >> (4 * i)) & 15u)];
+#pragma unroll
+    for (int i = 0; i < 8; i++) r ^= tab[(i + 8) * 16 + ((hi >> (4 * i)) & 15u)];
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Counter-based coefficients (splitmix64 output function, Steele/Lea/Flood
+// 2014): every sieve variable is a pure function of (query seed, its indices),
+// so any arc order, sort or subgraph gives the same values.
+// ---------------------------------------------------------------------------
+#define TM_GOLDEN 0x9E3779B97F4A7C15ull
+#define TM_TAG_V 0x1111111111111111ull
+#define TM_TAG_W 0x2222222222222222ull
+#define TM_TAG_Y 0x3333333333333333ull
+#define TM_PROBE 0xD1B54A32D192ED03ull
+
+__host__ __device__ __forceinline__ u64 mix64(u64 z)
+{
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Per-query keys, one per variable family.
+struct QueryKeys {
+    u64 kv, kw, ky;
+};
+
+__host__ __device__ __forceinline__ QueryKeys make_keys(u64 qseed)
+{
+    QueryKeys k;
+    k.kv = mix64(qseed ^ TM_TAG_V);
+    k.kw = mix64(qseed ^ TM_TAG_W);
+    k.ky = mix64(qseed ^ TM_TAG_Y);
+    return k;
+}
+
+// v_{u,d} (vertex u, slot d)
+__host__ __device__ __forceinline__ u64 coef_v(const QueryKeys &k, u32 u, u32 d)
+{
+    return mix64(k.kv ^ (((u64)u << 8) | d));
+}
+// w_{d,j} (slot d, label j)
+__host__ __device__ __forceinline__ u64 coef_w(const QueryKeys &k, u32 d, u32 j)
+{
+    return mix64(k.kw ^ (((u64)d << 8) | j));
+}
+// Arc part of y: shared by every walk position of arc a -> b.
+__host__ __device__ __forceinline__ u64 coef_y_arc(const QueryKeys &k, u32 a, u32 b)
+{
+    return mix64(k.ky ^ (((u64)a << 32) | b));
+}
+// y for arc a -> b at time t, walk position p.
+__host__ __device__ __forceinline__ u64 coef_y(u64 arc_key, u32 t, u32 p)
+{
+    return mix64(arc_key ^ (((u64)t << 8) | p));
+}
+
+}  // namespace tmo

@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+GF(2^64) arithmetic is exact, so every comparison is bit-exact: each per-point
+sieve sum Q^A, each decision and each extracted path (Lemma 5.5 sieve over
+eq. gen-polynomial:3; extraction of Sec. 5.9).
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+ANY = oracle.ANY
+
+
+@pytest.fixture(scope="module")
+def tm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2001_07158_gb300 as tm
+
+    return tm
+
+
+def gpu_graph(tm, g, undirected=None):
+    und = g.undirected if undirected is None else undirected
+    return tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, undirected=und)
+
+
+def both(tm, G, g, k, ms, und=False, **kw):
+    d = tm.tmotif_decide(G, k, ms, **kw)
+    f, s, pp = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, undirected=und, **kw)
+    return d, (f, s, pp)
+
+
+def assert_same(d, o):
+    f, s, pp = o
+    assert np.array_equal(d.per_point, pp), (d.per_point[:8], pp[:8])
+    assert d.sieve_sum == s
+    assert d.found == f
+
+
+def test_device_multiply_bit_exact(tm):
+    rng = np.random.default_rng(101)
+    n = 1 << 20
+    a = rng.integers(0, 2**64, n, dtype=np.uint64)
+    b = rng.integers(0, 2**64, n, dtype=np.uint64)
+    sp = np.array([0, 1, 2, 1 << 63, 2**64 - 1, 0x1B, 0x8000000000000001, 0xFFFFFFFF, 0xFFFFFFFF00000000],
+                  dtype=np.uint64)
+    a[:81] = np.repeat(sp, 9)
+    b[:81] = np.tile(sp, 9)
+    assert np.array_equal(tm.tmotif_gf_mul_batch(a, b), oracle.gf_mul_batch(a, b))
+
+
+def test_config1_tiny_per_point(tm):
+    g, q = synth.config1_tiny()
+    G = gpu_graph(tm, g)
+    for seed in (q.seed, 2, 3, 12345):
+        assert_same(*both(tm, G, g, q.k, q.multiset, seed=seed))
+
+
+def test_config1_brute_instance_many_seeds(tm):
+    g, q = synth.config1_brute()
+    G = gpu_graph(tm, g)
+    for seed in range(1, 60):
+        assert_same(*both(tm, G, g, q.k, q.multiset, seed=seed))
+
+
+def test_paper_example(tm):
+    g = synth.paper_example()
+    G = gpu_graph(tm, g)
+    for seed in range(1, 10):
+        d, o = both(tm, G, g, 3, [0, 0, 0], und=True, seed=seed)
+        assert_same(d, o)
+        assert d.found
+        d, o = both(tm, G, g, 3, [0, 0, 0], und=True, seed=seed, t_max=1)
+        assert_same(d, o)
+        assert not d.found
+
+
+def _random_case(rng):
+    n = rng.randint(2, 60)
+    m = rng.randint(0, 6 * n)
+    t_hi = rng.randint(1, 12)
+    ncol = rng.randint(1, 5)
+    src = np.array([rng.randrange(n) for _ in range(m)], np.uint32)
+    dst = np.array([rng.randrange(n) for _ in range(m)], np.uint32)
+    time = np.array([rng.randint(1, t_hi) for _ in range(m)], np.uint32)
+    color = np.array([rng.randrange(ncol) for _ in range(n)], np.uint32)
+    und = rng.random() < 0.3
+    g = synth.Graph(n, src, dst, time, color, ncol, und)
+    k = rng.randint(2, 7)
+    ms = [rng.randrange(ncol) for _ in range(k)]
+    kw = {"seed": rng.getrandbits(63)}
+    r = rng.random()
+    if r < 0.15:
+        kw["start"] = rng.randrange(n)
+    elif r < 0.3:
+        kw["end"] = rng.randrange(n)
+    if rng.random() < 0.25:
+        kw["t_min"] = rng.randint(0, min(4, t_hi))
+        kw["t_max"] = rng.randint(kw["t_min"], t_hi + 1)
+    if rng.random() < 0.2:
+        kw["repeats"] = rng.randint(2, 3)
+    return g, k, ms, kw
+
+
+def test_random_graphs_and_constraints(tm):
+    rng = random.Random(2024)
+    for _ in range(120):
+        g, k, ms, kw = _random_case(rng)
+        G = gpu_graph(tm, g)
+        assert_same(*both(tm, G, g, k, ms, und=g.undirected, **kw))
+        G.close()
+
+
+def test_lane_batches_and_point_ranges(tm):
+    # k = 7, 8, 9: 128..512 points run as several lane batches; partial ranges
+    # (sharding) must equal the matching slice of the full evaluation.
+    g = synth.uniform_graph(400, 5000, 60, 6, seed=77)
+    G = gpu_graph(tm, g)
+    for k in (7, 8, 9):
+        ms = [i % 6 for i in range(k)]
+        d, o = both(tm, G, g, k, ms, seed=k)
+        assert_same(d, o)
+        hi = (1 << k) - 3
+        sub = tm.tmotif_decide(G, k, ms, seed=k, point_begin=37, point_end=hi)
+        assert np.array_equal(sub.per_point, o[2][37:hi])
+
+
+def test_edge_cases(tm):
+    # empty edge set, only self-loops, duplicated input edges, absent colours,
+    # k larger than the vertex count
+    n = 5
+    color = np.array([0, 1, 2, 0, 1], np.uint32)
+    cases = [
+        (np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.uint32)),
+        (np.array([1, 2, 3], np.uint32), np.array([1, 2, 3], np.uint32), np.array([1, 2, 3], np.uint32)),
+        (np.array([0, 0, 1, 1, 1], np.uint32), np.array([1, 1, 2, 2, 2], np.uint32), np.array([1, 1, 2, 2, 2], np.uint32)),
+    ]
+    for src, dst, time in cases:
+        g = synth.Graph(n, src, dst, time, color, 4, False)
+        G = gpu_graph(tm, g)
+        for k, ms in ((2, [0, 1]), (3, [0, 1, 2]), (3, [3, 3, 3]), (6, [0, 0, 1, 1, 2, 2])):
+            assert_same(*both(tm, G, g, k, ms, seed=5))
+        info = tm.tmotif_graph_get_info(G)
+        assert info["m_arcs"] == len(oracle.canon(n, src, dst, time)[0])
+        G.close()
+
+
+def test_errors_are_reported(tm):
+    g, q = synth.config1_brute()
+    G = gpu_graph(tm, g)
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide(G, 1, [0])
+    assert e.value.code == 5
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide(G, 3, [0, 1, 99])
+    assert e.value.code == 1
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide(G, 3, [0, 1, 2], repeats=0)
+    assert e.value.code == 1
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide(G, 3, [0, 1, 2], start=10**6)
+    assert e.value.code == 1
+    # the handle stays usable after an error
+    assert_same(*both(tm, G, g, q.k, q.multiset, seed=3))
+
+
+# ---------------------------------------------------------------------------
+# Extraction (Sec. 5.9): same deterministic procedure -> the same path
+# ---------------------------------------------------------------------------
+def test_extraction_matches_oracle(tm):
+    g, q = synth.config1_tiny()
+    G = gpu_graph(tm, g)
+    for seed in (1, 2, 3):
+        f, v, t = tm.tmotif_extract(G, q.k, q.multiset, seed=seed)
+        fo, vo, to, _ = oracle.extract(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=seed)
+        assert f == fo and np.array_equal(v, vo) and np.array_equal(t, to)
+    rng = random.Random(99)
+    for _ in range(30):
+        g, k, ms, kw = _random_case(rng)
+        kw.pop("repeats", None)
+        G = gpu_graph(tm, g)
+        f, v, t = tm.tmotif_extract(G, k, ms, **kw)
+        fo, vo, to, _ = oracle.extract(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms,
+                                       undirected=g.undirected, **kw)
+        assert f == fo
+        if f:
+            assert np.array_equal(v, vo) and np.array_equal(t, to)
+        G.close()
+
+
+# ---------------------------------------------------------------------------
+# Full size (the benchmark workload): sampled points against the oracle
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg2(tm):
+    g, q = synth.config2_mid()
+    return g, q, gpu_graph(tm, g)
+
+
+def test_config2_full_size_sampled_points(tm, cfg2):
+    g, q, G = cfg2
+    d = tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed)
+    assert d.found  # planted paths
+    # a ragged sample of the 64 points, each computed by the oracle on its own
+    # (oracle calls run concurrently in threads; ctypes releases the GIL)
+    import concurrent.futures as cf
+
+    ranges = ((5, 6), (33, 35), (62, 64))
+
+    def run(r):
+        lo, hi = r
+        return oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed,
+                             point_begin=lo, point_end=hi, nthreads=hi - lo)[2]
+
+    with cf.ThreadPoolExecutor(len(ranges)) as ex:
+        for (lo, hi), pp in zip(ranges, ex.map(run, ranges)):
+            assert np.array_equal(d.per_point[lo:hi], pp)
+
+
+def test_config2_full_size_extraction_is_valid(tm, cfg2):
+    g, q, G = cfg2
+    f, v, t = tm.tmotif_extract(G, q.k, q.multiset, seed=q.seed)
+    assert f
+    arcs = set(zip(g.src.tolist(), g.dst.tolist(), g.time.tolist()))
+    assert len(set(v.tolist())) == q.k
+    assert sorted(g.color[v].tolist()) == sorted(q.multiset.tolist())
+    for r in range(q.k - 1):
+        assert (int(v[r]), int(v[r + 1]), int(t[r])) in arcs
+        if r:
+            assert t[r] > t[r - 1]

@@ -145,3 +145,13 @@ def test_vertex_x_is_sum_over_labels(oracle_mod, k):
                     for d in range(sb[color], sb[color] + sc[color]):
                         want ^= py_gf_mul(oracle.coef_v(qs, u, d), oracle.coef_w(qs, d, j))
             assert oracle.vertex_x(qs, k, ms, 2, color, u, point) == want
+
+
+def test_batch_product_matches_scalar(oracle_mod):
+    import numpy as np
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 2**64, 1000, dtype=np.uint64)
+    b = rng.integers(0, 2**64, 1000, dtype=np.uint64)
+    out = oracle.gf_mul_batch(a, b)
+    for i in range(0, 1000, 37):
+        assert int(out[i]) == py_gf_mul(int(a[i]), int(b[i]))
