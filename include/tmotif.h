@@ -182,6 +182,38 @@ int tmotif_get_stats(tmotif_graph_t g, tmotif_stats *out);
  * multiply of the sieve kernels (host arrays of n entries). */
 int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n);
 
+/* Decision without any memory allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * need an answer -- a host program whose own allocator already holds the whole
+ * device, a latency-bound loop where cudaMalloc/cudaFree would synchronise the
+ * device, or code living under a memory budget fixed elsewhere.  It computes
+ * the same per-point sieve sums as tmotif_decide (first repeat only) and
+ * allocates nothing: every intermediate lives in one fixed device array of
+ * TMOTIF_NOALLOC_SCRATCH_BYTES that each GPU loading the library keeps until
+ * the process exits.
+ *   d_src, d_dst, d_time  caller-owned DEVICE arrays of m canonical arcs
+ *                 (ids < n, time >= 1, no self-loops, no duplicates) sorted
+ *                 strictly by (dst, time, src) -- the resident layout of a
+ *                 graph built by tmotif_create_graph;
+ *   d_color       caller-owned DEVICE array of n colours < num_colors;
+ *   q             as for tmotif_decide, with repeats == 1;
+ *   d_per_point   caller-owned DEVICE output of point_end - point_begin
+ *                 values (2^k when both are 0); XOR them for the sieve sum;
+ *   cuda_stream   stream for all work; the call returns after it finished.
+ * Errors: UNSUPPORTED when the graph needs more scratch than the fixed array
+ * (the message gives both sizes) or k is outside [2, TMOTIF_KMAX]; INVALID for
+ * arcs that are not canonical and sorted, bad colours or query fields; CUDA.
+ * All calls share the array and it keeps the previous call's contents; each
+ * call clears what must start at zero.  Calls whose work overlaps on the GPU
+ * (other streams or host threads on the same device) race on the array and
+ * must be serialised by the caller.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. */
+#define TMOTIF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int tmotif_decide_noalloc(const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_time, uint64_t m,
+                          const uint32_t *d_color, uint32_t n, uint32_t num_colors, const tmotif_query *q,
+                          uint64_t *d_per_point, void *cuda_stream);
+
 /* Message for the last error on the calling thread (never NULL). */
 const char *tmotif_last_error(void);
 

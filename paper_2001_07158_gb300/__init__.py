@@ -79,6 +79,7 @@ def _load():
         "tmotif_set_profiling": (C.c_int, [P, C.c_int]),
         "tmotif_get_stats": (C.c_int, [P, C.POINTER(_Stats)]),
         "tmotif_gf_mul_batch": (C.c_int, [P, P, P, C.c_uint64]),
+        "tmotif_decide_noalloc": (C.c_int, [P, P, P, C.c_uint64, P, C.c_uint32, C.c_uint32, C.POINTER(_Query), P, P]),
         "tmotif_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -225,6 +226,24 @@ def tmotif_gf_mul_batch(a, b) -> np.ndarray:
     out = np.zeros_like(a)
     _check(_lib.tmotif_gf_mul_batch(a.ctypes.data, b.ctypes.data, out.ctypes.data, len(a)))
     return out
+
+
+def tmotif_decide_noalloc(d_src, d_dst, d_time, m, d_color, n, num_colors, k, multiset, d_per_point, *,
+                          start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1, point_begin=0, point_end=0,
+                          stream=None):
+    """Allocation-free decision for callers that cannot allocate device memory
+    (their allocator owns the device, or an allocation would synchronise a
+    latency-bound loop).  d_* are device addresses (ints) of caller-owned
+    arrays in the resident layout (canonical arcs sorted by (dst, time,
+    src)); the per-point sieve sums land in d_per_point.  All intermediates
+    live in the library's fixed scratch array of TMOTIF_NOALLOC_SCRATCH_BYTES,
+    shared by every call: do not overlap calls on the GPU."""
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, 1, point_begin, point_end)
+    _check(_lib.tmotif_decide_noalloc(d_src, d_dst, d_time, m, d_color, n, num_colors, C.byref(q), d_per_point,
+                                      _stream_handle(stream)))
+
+
+TMOTIF_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 def tmotif_last_error() -> str:
