@@ -43,14 +43,18 @@ WORKLOAD = ("power-law out-degree 2.1, n=1e6, m=1e7 (+50 planted arcs), t in [1,
 # it; a throughput probe measured 58-60 lanes/SM/clk for each alone.
 INT_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 
-# 32-bit integer instructions per GF(2^64) product of the register multiply
-# (Karatsuba over three 32x32 carry-less products with holes, plus the
-# reduction): ncu smsp__inst_executed of an isolated multiply loop / products
-# (99 ALU-pipe + 102 FMA-pipe instructions).
+# Instructions per GF(2^64) product for the two forms the layer kernel uses,
+# from ncu smsp__inst_executed of the library's throughput probe
+# (tmotif_gf_probe) divided by its products:
+#   register multiply (Karatsuba over three 32x32 carry-less products with
+#   holes, plus the reduction) -- used for the x-products;
+#   shared nibble table of a multiplier common to 64 lanes (build amortised)
+#   -- used for the y-products.
 OPS_PER_GF_MUL = 201.0
+OPS_PER_TABLE_MUL = 201.0
 
 # DRAM traffic of one layer launch from an ncu capture, valid only for the
-# layer-kernel source it was taken on (sha256 of csrc/sieve.cu, first 16 hex).
+# layer-kernel source it was taken on (source_sha() below, first 16 hex).
 LAYER_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
 
 
@@ -73,7 +77,10 @@ def dist_env():
 
 
 def source_sha():
-    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2001_07158_gb300", "csrc", "sieve.cu"), "rb").read())
+    """Hash of the sources the layer kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in ("sieve.cu", "gf64.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2001_07158_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -239,13 +246,16 @@ def run_ours(args):
     nl = max(stats["layer_launches"], 1)
     layer_ms = stats["layer_ms"] / nl
     muls = stats["layer_gf_muls"] / nl
-    achieved = muls * OPS_PER_GF_MUL / (layer_ms / 1e3) / 1e12
+    tmuls = stats["layer_table_muls"] / nl
+    ops = tmuls * OPS_PER_TABLE_MUL + (muls - tmuls) * OPS_PER_GF_MUL
+    achieved = ops / (layer_ms / 1e3) / 1e12
     sha = source_sha()
     traffic = LAYER_TRAFFIC["bytes_per_launch"] if LAYER_TRAFFIC["source_sha"] == sha else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": INT_PEAK_TOPS, "unit": "Tops/s",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": INT_PEAK_TOPS, "unit": "Tinstr/s",
                 "frac": achieved / INT_PEAK_TOPS, "traffic": traffic,
                 "kernel": "k_layer (eq. gen-polynomial:3 layer)", "layer_ms_per_launch": layer_ms,
-                "gf_muls_per_launch": muls, "ops_per_gf_mul": OPS_PER_GF_MUL,
+                "gf_muls_per_launch": muls, "table_muls_per_launch": tmuls,
+                "instr_per_product": {"register": OPS_PER_GF_MUL, "table": OPS_PER_TABLE_MUL},
                 "algorithmic_bytes_per_launch": stats["layer_bytes"] / nl,
                 "achieved_gbs": stats["layer_bytes"] / nl / (layer_ms / 1e3) / 1e9,
                 "layer_share_of_step": stats["layer_ms"] / total_ms if total_ms else None}

@@ -126,6 +126,7 @@ typedef struct {
     uint64_t layer_cp_lanes;   /* checkpoints x lanes written               */
     uint64_t layer_bytes;      /* algorithmic bytes of the layer kernels    */
     uint64_t layer_gf_muls;    /* GF(2^64) products in the layer kernels    */
+    uint64_t layer_table_muls; /* ... of which by a shared multiplier table  */
 } tmotif_stats;
 
 /* Build the resident graph: validate, orient, drop self-loops, merge
@@ -181,6 +182,14 @@ int tmotif_get_stats(tmotif_graph_t g, tmotif_stats *out);
 /* Diagnostic: out[i] = a[i] * b[i] in GF(2^64) computed by the device
  * multiply of the sieve kernels (host arrays of n entries). */
 int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n);
+
+/* Diagnostic throughput probe of the two GF(2^64) product forms the layer
+ * kernel uses, on register-resident data (no memory traffic), 8 blocks of 256
+ * threads per SM: method 0 = register multiply (Karatsuba over 32x32
+ * carry-less products with holes); method 1 = a warp builds the 16 x 16 nibble
+ * table of one multiplier in shared memory and applies it to 64 lanes.  Runs
+ * `iters` rounds; ms receives the device time, products the products done. */
+int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products);
 
 /* Decision without any memory allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they

@@ -57,7 +57,7 @@ class _Stats(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("layer_launches", C.c_uint64), ("layer_ms", C.c_double),
                 ("prep_ms", C.c_double), ("coef_ms", C.c_double), ("other_ms", C.c_double),
                 ("layer_arc_lanes", C.c_uint64), ("layer_cp_lanes", C.c_uint64), ("layer_bytes", C.c_uint64),
-                ("layer_gf_muls", C.c_uint64)]
+                ("layer_gf_muls", C.c_uint64), ("layer_table_muls", C.c_uint64)]
 
 
 def _load():
@@ -79,6 +79,7 @@ def _load():
         "tmotif_set_profiling": (C.c_int, [P, C.c_int]),
         "tmotif_get_stats": (C.c_int, [P, C.POINTER(_Stats)]),
         "tmotif_gf_mul_batch": (C.c_int, [P, P, P, C.c_uint64]),
+        "tmotif_gf_probe": (C.c_int, [C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
         "tmotif_decide_noalloc": (C.c_int, [P, P, P, C.c_uint64, P, C.c_uint32, C.c_uint32, C.POINTER(_Query), P, P]),
         "tmotif_last_error": (C.c_char_p, []),
     }
@@ -244,6 +245,14 @@ def tmotif_decide_noalloc(d_src, d_dst, d_time, m, d_color, n, num_colors, k, mu
 
 
 TMOTIF_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def tmotif_gf_probe(method: int, iters: int = 256):
+    """Throughput probe of a GF(2^64) product form: returns (ms, products)."""
+    ms = C.c_double(0)
+    n = C.c_uint64(0)
+    _check(_lib.tmotif_gf_probe(method, iters, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 def tmotif_last_error() -> str:

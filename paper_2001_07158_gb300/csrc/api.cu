@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -32,32 +33,76 @@ Status cuda_fail(cudaError_t e, const char *what)
     return fail(code, msg);
 }
 
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pools[256];
+
+static Status pool_for_current_device(cudaMemPool_t *out)
+{
+    int dev = 0;
+    TM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(TMOTIF_ERR_UNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        TM_CUDA(cudaMemPoolCreate(&pool, &props));
+        unsigned long long keep = ~0ull;  // keep freed memory cached in the pool
+        TM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return Status();
+}
+
+Status dev_alloc(void **p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    cudaMemPool_t pool;
+    TM_TRY(pool_for_current_device(&pool));
+    cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 256), pool, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "device allocation");
+    }
+    return Status();
+}
+
+void dev_free(void *p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
 Status DevBuf::reserve(size_t need)
 {
     if (need <= bytes && p) return Status();
     release();
     size_t want = std::max<size_t>(need, 256);
-    cudaError_t e = cudaMalloc(&p, want);
-    if (e != cudaSuccess) {
-        p = nullptr;
-        bytes = 0;
-        return cuda_fail(e, "cudaMalloc(workspace)");
-    }
+    TM_TRY(dev_alloc(&p, want, stream));
     bytes = want;
     return Status();
 }
 
 void DevBuf::release()
 {
-    if (p) cudaFree(p);
+    dev_free(p, stream);
     p = nullptr;
     bytes = 0;
+}
+
+void Workspace::set_stream(cudaStream_t s)
+{
+    DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &keep, &pos,
+                     &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial};
+    for (DevBuf *b : all) b->stream = s;
 }
 
 void Workspace::release()
 {
     DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &keep, &pos,
-                     &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive};
+                     &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial};
     for (DevBuf *b : all) b->release();
     if (host_pinned) cudaFreeHost(host_pinned);
     host_pinned = nullptr;
@@ -67,7 +112,7 @@ void Workspace::release()
 size_t Workspace::bytes() const
 {
     const DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &keep, &pos,
-                           &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive};
+                           &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->bytes;
     return s;
@@ -142,6 +187,11 @@ Status build_graph(const tmotif_graph_desc *d, Graph *g)
     if (d->m > 0 && (!d->src || !d->dst || !d->time)) return fail(TMOTIF_ERR_INVALID, "null edge array");
     const u64 cap = d->undirected ? 2 * d->m : d->m;
     if (cap >= 0xFFFFFFFFull) return fail(TMOTIF_ERR_UNSUPPORTED, "more than 2^32-2 arcs");
+    {
+        bool done = false;
+        TM_TRY(build_graph_device(d, g, &done));
+        if (done) return Status();
+    }
     for (u32 u = 0; u < d->n; u++)
         if (d->color[u] >= d->num_colors) return fail(TMOTIF_ERR_INVALID, "color out of range");
     std::vector<HArc> arcs;
@@ -187,10 +237,10 @@ Status build_graph(const tmotif_graph_desc *d, Graph *g)
     arcs.clear();
     arcs.shrink_to_fit();
     const u64 mb = std::max<u64>(w, 1) * 4;
-    TM_CUDA(cudaMalloc(&g->d_src, mb));
-    TM_CUDA(cudaMalloc(&g->d_dst, mb));
-    TM_CUDA(cudaMalloc(&g->d_time, mb));
-    TM_CUDA(cudaMalloc(&g->d_color, std::max<u64>(d->n, 1) * 4));
+    TM_TRY(dev_alloc((void **)&g->d_src, mb, g->stream));
+    TM_TRY(dev_alloc((void **)&g->d_dst, mb, g->stream));
+    TM_TRY(dev_alloc((void **)&g->d_time, mb, g->stream));
+    TM_TRY(dev_alloc((void **)&g->d_color, std::max<u64>(d->n, 1) * 4, g->stream));
     g->resident_bytes = 3 * mb + std::max<u64>(d->n, 1) * 4;
     TM_CUDA(cudaMemcpyAsync(g->d_src, hs.data(), w * 4, cudaMemcpyHostToDevice, g->stream));
     TM_CUDA(cudaMemcpyAsync(g->d_dst, hd.data(), w * 4, cudaMemcpyHostToDevice, g->stream));
@@ -203,11 +253,12 @@ Status build_graph(const tmotif_graph_desc *d, Graph *g)
 static void free_graph(Graph *g)
 {
     if (!g) return;
-    if (g->d_src) cudaFree(g->d_src);
-    if (g->d_dst) cudaFree(g->d_dst);
-    if (g->d_time) cudaFree(g->d_time);
-    if (g->d_color) cudaFree(g->d_color);
+    dev_free(g->d_src, g->stream);
+    dev_free(g->d_dst, g->stream);
+    dev_free(g->d_time, g->stream);
+    dev_free(g->d_color, g->stream);
     g->ws.release();
+    cudaStreamSynchronize(g->stream);
     g->prof.destroy();
     delete static_cast<tmotif_graph *>(g);
 }
@@ -263,6 +314,10 @@ int tmotif_create_graph(const tmotif_graph_desc *desc, tmotif_graph_t *out)
     }
     Status s;
     try {
+        if (desc) {
+            g->stream = (cudaStream_t)desc->cuda_stream;
+            g->ws.set_stream(g->stream);
+        }
         s = build_graph(desc, g);
     } catch (const std::bad_alloc &) {
         s = fail(TMOTIF_ERR_OOM, "host allocation failed");
@@ -349,6 +404,13 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
 {
     if (n && (!a || !b || !out)) return fail(TMOTIF_ERR_INVALID, "null argument").code;
     return gf_mul_batch((const u64 *)a, (const u64 *)b, (u64 *)out, n).code;
+}
+
+int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products)
+{
+    if (!ms || !products || (method != 0 && method != 1) || iters == 0)
+        return fail(TMOTIF_ERR_INVALID, "bad probe arguments").code;
+    return gf_probe(method, iters, ms, (u64 *)products).code;
 }
 
 const char *tmotif_last_error(void) { return g_last_error.c_str(); }

@@ -75,6 +75,13 @@ __device__ __forceinline__ u64 gf_mul_x(u64 a)
 // so y * s = XOR_i tab[i][nibble_i(s)] -- 16 shared-memory loads instead of a
 // full carry-less product.  A team of `nthreads` threads builds the 256
 // entries together (each thread 256/nthreads of them, nthreads in {8,16,32}).
+//
+// Layout: row i holds 16 entries = 8 chunks of 16 bytes; chunk c of row i is
+// stored at chunk position c ^ (i & 7).  Threads write whole chunks, and with
+// this swizzle the chunks that one store instruction writes fall in distinct
+// bank groups (rows i..i+3 or i..i+7 of neighbouring threads); a lookup of
+// entry b in row i reads position b ^ 2(i & 7), still inside the 128-byte row,
+// so the 32 lookups of a warp stay free of bank conflicts.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthreads)
 {
@@ -85,11 +92,12 @@ __device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthr
         const u64 b0 = gf_mul_xpow(y, 4 * i);
         const u64 b1 = gf_mul_x(b0), b2 = gf_mul_x(b1);
         const u64 base = h ? gf_mul_x(b2) : 0ull;
-        ulonglong2 *t = (ulonglong2 *)(tab + e0);
-        t[0] = make_ulonglong2(base, base ^ b0);
-        t[1] = make_ulonglong2(base ^ b1, base ^ b1 ^ b0);
-        t[2] = make_ulonglong2(base ^ b2, base ^ b2 ^ b0);
-        t[3] = make_ulonglong2(base ^ b2 ^ b1, base ^ b2 ^ b1 ^ b0);
+        ulonglong2 *row = (ulonglong2 *)(tab + i * 16);
+        const int sw = i & 7, c0 = 4 * h;
+        row[(c0 + 0) ^ sw] = make_ulonglong2(base, base ^ b0);
+        row[(c0 + 1) ^ sw] = make_ulonglong2(base ^ b1, base ^ b1 ^ b0);
+        row[(c0 + 2) ^ sw] = make_ulonglong2(base ^ b2, base ^ b2 ^ b0);
+        row[(c0 + 3) ^ sw] = make_ulonglong2(base ^ b2 ^ b1, base ^ b2 ^ b1 ^ b0);
     }
 }
 
@@ -98,9 +106,9 @@ __device__ __forceinline__ u64 gf_table_mul(const u64 *tab, u64 s)
     const u32 lo = (u32)s, hi = (u32)(s >> 32);
     u64 r = 0;
 #pragma unroll
-    for (int i = 0; i < 8; i++) r ^= tab[i * 16 + ((lo >> (4 * i)) & 15u)];
+    for (int i = 0; i < 8; i++) r ^= tab[i * 16 + (((lo >> (4 * i)) & 15u) ^ (u32)((i & 7) << 1))];
 #pragma unroll
-    for (int i = 0; i < 8; i++) r ^= tab[(i + 8) * 16 + ((hi >> (4 * i)) & 15u)];
+    for (int i = 0; i < 8; i++) r ^= tab[(i + 8) * 16 + (((hi >> (4 * i)) & 15u) ^ (u32)(((i + 8) & 7) << 1))];
     return r;
 }
 

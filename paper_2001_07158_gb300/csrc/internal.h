@@ -38,10 +38,19 @@ Status cuda_fail(cudaError_t e, const char *what);
         if (!_s.ok()) return _s;    \
     } while (0)
 
-// A device buffer that only grows.
+// Stream-ordered device memory from the library's own pool (one per device,
+// memory kept cached across frees so repeated graphs and queries reuse it).
+Status dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// Colour-pair histograms are kept for up to this many colours.
+static const u32 PAIR_HIST_COLORS = 64;
+
+// A device buffer that only grows (pool memory, ordered on `stream`).
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t stream = nullptr;
     Status reserve(size_t need);
     void release();
     template <class T> T *as() const { return (T *)p; }
@@ -80,10 +89,12 @@ struct Workspace {
     DevBuf out;                         // L u64: per-lane sieve sums
     DevBuf wtab;                        // k * L u64: W_d^A
     DevBuf alive;                       // n bytes: extraction probe mask
+    DevBuf partial;                     // chunks * L u64: per-chunk sieve sums
     void *host_pinned = nullptr;        // small pinned readback area
     size_t host_pinned_bytes = 0;
     void release();
     size_t bytes() const;
+    void set_stream(cudaStream_t s);
 };
 
 struct Graph {
@@ -97,6 +108,7 @@ struct Graph {
     u32 *d_src = nullptr, *d_dst = nullptr, *d_time = nullptr;
     u32 *d_color = nullptr;
     std::vector<u32> h_color;           // host copy for extraction bookkeeping
+    std::vector<u64> pair_hist;         // arcs per (colour(src), colour(dst)), if few colours
     Workspace ws;
     Profiler prof;
     size_t resident_bytes = 0;
@@ -114,23 +126,109 @@ struct QuerySpec {
 
 Status parse_query(const Graph &g, const tmotif_query *q, QuerySpec *out);
 
+// Parameters of one job's layer step (eq. gen-polynomial:3), as the layer
+// kernel reads them.
+struct LayerParams {
+    const u32 *src, *dst, *time, *cp_in, *cp_out, *seg_hi;
+    const u64 *x;
+    const u64 *Cin;
+    u64 *Cout;
+    u64 *partial;   // last layer: per (chunk, lane) sums
+    u64 m_f;
+    u64 n_chunks;
+    u64 ky;
+    u32 L, lane_groups, chunk, ell, k, start, end, T;
+};
+
+// One decision in flight: its query, its device workspace and its progress
+// through lane batches and layers.  tmotif_decide runs one job to the end;
+// the batch driver and the server advance many jobs together, one shared
+// layer launch per step.
+struct Job {
+    Graph *g = nullptr;
+    QuerySpec q;
+    const uint8_t *d_alive = nullptr;
+    Workspace *ws = nullptr;
+    cudaStream_t st = nullptr;
+    Profiler *prof = nullptr;
+    // sizes known after prep
+    u64 mf = 0, ncp = 0;
+    u32 L = 0, T = 0, lane_groups = 0, chunk = 128;
+    u64 n_chunks = 0;
+    // progress
+    u32 r = 0;            // repeat
+    u64 p0 = 0;           // first point of the current lane batch
+    u32 ell = 0;          // next layer to run (2..k), k+1 = batch finished
+    u64 qsum = 0;
+    int found = 0;
+    u64 sieve_sum = 0;
+    bool done = false;
+    std::vector<u64> vals;  // repeat-0 per-point sums on [p_begin, p_end)
+    u64 ky = 0;           // y key of the current repeat
+};
+
+// Job steps.  prep: filter, checkpoints, buffer sizing (synchronises the
+// job's stream); batch_begin: coefficients of the lane batch at p0;
+// readout_enqueue: reduce the last layer's partial sums and copy them to the
+// host; readout_finish (after the stream is synchronised): accumulate and
+// move on to the next batch, repeat, or finish.
+Status job_prep(Job &j);
+Status job_batch_begin(Job &j);
+LayerParams job_layer_params(const Job &j);
+Status job_readout_enqueue(Job &j);
+void job_readout_finish(Job &j);
+// One layer launch per lane-width class for all the given jobs (each at its
+// own layer), on stream st.  `dev_params` is a device buffer for the job
+// table.
+Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &dev_params, void *host_params,
+                     size_t host_params_bytes, Profiler *prof);
+// Device bytes a job will hold once prepped (for admission).
+size_t job_bytes(const Job &j);
+
 // Decide on graph g; alive (device, n bytes, may be null) masks vertices.
 // per_point (host, may be null) receives repeat-0 values on [p_begin,p_end).
 Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *found, u64 *sieve_sum,
                     u64 *per_point, double *ms);
 
 // Arcs among the vertices with alive[u] != 0 (device mask) inside the time
-// window, copied to the host in (dst, time, src) order.
-Status gather_arcs(Graph &g, const uint8_t *d_alive, u32 t_min, u32 t_max, std::vector<u32> *src,
-                   std::vector<u32> *dst, std::vector<u32> *time);
+// window, copied to the host in (dst, time, src) order, using workspace w on
+// stream st.
+Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const uint8_t *d_alive, u32 t_min,
+                   u32 t_max, std::vector<u32> *src, std::vector<u32> *dst, std::vector<u32> *time);
 
-// Extraction (Sec. 5.9).
+// Extraction (Sec. 5.9) as a state machine: next_probe() gives the next
+// decision to run (the first one is the query itself, the rest mask the
+// vertices with alive[u] == 0), result() takes its answer.  When
+// next_probe() returns false, stage is SHRUNK (run extract_finish) or
+// NOT_FOUND.
+struct ExtractState {
+    enum Stage { FIRST, SEARCHING, PROBING, SHRUNK, NOT_FOUND };
+    struct Block { u64 lo, hi; };
+    QuerySpec query;
+    std::vector<uint8_t> alive;
+    std::vector<u32> R;
+    std::vector<Block> stack;
+    u64 n_alive = 0, cur_lo = 0, cur_hi = 0, cur_cnt = 0;
+    u32 probes = 0;
+    Stage stage = FIRST;
+    void init(const Graph &g, const QuerySpec &q);
+    bool next_probe(QuerySpec *pq);
+    void result(bool yes);
+    void push_halves(u64 lo, u64 hi);
+};
+Status extract_finish(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const ExtractState &ex, u32 *verts,
+                      u32 *times, int *found);
 Status extract_path(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *found, u32 *probes);
 
 Status build_graph(const tmotif_graph_desc *d, Graph *g);
+// Device build; *done = false (and no error) when the packed arc key would not
+// fit 64 bits, in which case the caller builds on the host.
+Status build_graph_device(const tmotif_graph_desc *d, Graph *g, bool *done);
 
 // Device GF multiply of host arrays (diagnostic).
 Status gf_mul_batch(const u64 *a, const u64 *b, u64 *out, u64 n);
+// Throughput probe of the product forms (diagnostic).
+Status gf_probe(int method, u32 iters, double *ms, u64 *products);
 
 }  // namespace tmo
 

@@ -1,47 +1,505 @@
-// serve.cu -- batched decisions and the request server.
+// serve.cu -- batched decisions and the continuous-batching request server.
+//
+// Both run on a Scheduler: every admitted decision is a Job with its own
+// device workspace; each scheduler step advances every active job by one
+// layer of eq. (gen-polynomial:3) in one shared layer launch (jobs may sit on
+// different graphs, have different k and be at different layers), starts the
+// coefficients of jobs that begin a lane batch, and reads out jobs that
+// finished one.  Jobs are admitted while the device memory they will hold
+// fits the budget, and leave as soon as they finish, so new work joins the
+// next launch without waiting for a whole batch to drain.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
+#include "gf64.cuh"
 #include "internal.h"
+
+namespace tmo {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// Upper bound on the arcs a query keeps: arcs whose two endpoint colours are
+// in the multiset (before masks and the time window).
+u64 kept_arc_bound(const Graph &g, const QuerySpec &q)
+{
+    if (g.pair_hist.empty()) return g.m;
+    std::vector<u32> cs(q.multiset.begin(), q.multiset.end());
+    std::sort(cs.begin(), cs.end());
+    cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+    u64 s = 0;
+    for (u32 a : cs)
+        for (u32 b : cs) s += g.pair_hist[(size_t)a * g.num_colors + b];
+    return s;
+}
+
+// Device bytes a job on (g, q) can hold: prep arrays, coefficients,
+// double-buffered checkpoints (at most one per kept arc), partial sums.
+size_t job_estimate(const Graph &g, const QuerySpec &q)
+{
+    const u64 mf = kept_arc_bound(g, q), n = g.n, m = g.m;
+    u64 L = 4;
+    while (L < 64 && L < q.p_end - q.p_begin) L <<= 1;
+    return (size_t)(n * 9 + (m + 1) * 4 + mf * 32 + n * L * 8 + 2 * mf * L * 8 + ((mf + 127) / 128) * L * 8 +
+                    (u64)q.k * L * 8 + 4096 + (m / 4096 + 1) * 4);
+}
+
+enum JobState { J_BEGIN = 0, J_LAYER = 1, J_READOUT = 2 };
+
+struct SJob {
+    Job job;
+    Workspace ws;
+    size_t reserved = 0;
+    int state = J_BEGIN;
+    u64 owner = 0;
+    ~SJob() { ws.release(); }
+};
+
+class Scheduler {
+public:
+    Scheduler(cudaStream_t st, size_t budget) : st_(st), budget_(budget) {}
+    ~Scheduler()
+    {
+        dev_params_.release();
+        if (host_params_) cudaFreeHost(host_params_);
+        prof.destroy();
+    }
+
+    Status init()
+    {
+        TM_CUDA(cudaMallocHost(&host_params_, kParamsBytes));
+        dev_params_.stream = st_;
+        return Status();
+    }
+
+    bool fits(size_t bytes) const { return in_use_ + bytes <= budget_; }
+    size_t in_use() const { return in_use_; }
+    size_t budget() const { return budget_; }
+    bool idle() const { return active_.empty(); }
+    size_t active() const { return active_.size(); }
+
+    // Admit a job whose query/graph/mask are set; runs its prep.  On return
+    // the job is active, or finished (nothing kept) and appended to done.
+    Status admit(std::unique_ptr<SJob> sj, size_t reserved, std::vector<std::unique_ptr<SJob>> *done)
+    {
+        sj->reserved = reserved;
+        in_use_ += reserved;
+        sj->ws.set_stream(st_);
+        sj->job.ws = &sj->ws;
+        sj->job.st = st_;
+        sj->job.prof = &prof;
+        Status s = job_prep(sj->job);
+        if (!s.ok()) {
+            in_use_ -= reserved;
+            return s;
+        }
+        sj->state = J_BEGIN;
+        if (sj->job.done) {
+            in_use_ -= sj->reserved;
+            done->push_back(std::move(sj));
+        } else {
+            active_.push_back(std::move(sj));
+        }
+        return Status();
+    }
+
+    // Upload a probe mask into a job's workspace before admission.
+    Status set_mask(SJob &sj, const std::vector<uint8_t> &alive)
+    {
+        sj.ws.set_stream(st_);
+        TM_TRY(sj.ws.alive.reserve(std::max<size_t>(alive.size(), 1)));
+        TM_CUDA(cudaMemcpyAsync(sj.ws.alive.p, alive.data(), alive.size(), cudaMemcpyHostToDevice, st_));
+        sj.job.d_alive = sj.ws.alive.as<uint8_t>();
+        return Status();
+    }
+
+    // One step: coefficients for jobs starting a lane batch, one shared layer
+    // launch per lane-width class, readouts of finished batches, one sync.
+    Status step(std::vector<std::unique_ptr<SJob>> *done)
+    {
+        if (active_.empty()) return Status();
+        std::vector<Job *> layer;
+        for (auto &sj : active_) {
+            if (sj->state == J_BEGIN) {
+                TM_TRY(job_batch_begin(sj->job));
+                sj->state = J_LAYER;
+            }
+            layer.push_back(&sj->job);
+        }
+        TM_TRY(launch_layers(st_, layer, dev_params_, host_params_, kParamsBytes, &prof));
+        for (auto &sj : active_) {
+            sj->job.ell++;
+            if (sj->job.ell > sj->job.q.k) {
+                TM_TRY(job_readout_enqueue(sj->job));
+                sj->state = J_READOUT;
+            }
+        }
+        TM_CUDA(cudaStreamSynchronize(st_));
+        TM_TRY(prof.collect());
+        steps++;
+        std::vector<std::unique_ptr<SJob>> keep;
+        for (auto &sj : active_) {
+            if (sj->state == J_READOUT) {
+                job_readout_finish(sj->job);
+                sj->state = J_BEGIN;
+                if (sj->job.done) {
+                    in_use_ -= sj->reserved;
+                    done->push_back(std::move(sj));
+                    continue;
+                }
+            }
+            keep.push_back(std::move(sj));
+        }
+        active_.swap(keep);
+        return Status();
+    }
+
+    Profiler prof;
+    u64 steps = 0;
+
+private:
+    static const size_t kParamsBytes = 4 << 20;
+    cudaStream_t st_;
+    size_t budget_;
+    size_t in_use_ = 0;
+    std::vector<std::unique_ptr<SJob>> active_;
+    DevBuf dev_params_;
+    void *host_params_ = nullptr;
+};
+
+size_t default_budget()
+{
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return (size_t)8 << 30;
+    return (size_t)(free_b * 0.8);
+}
+
+}  // namespace
+}  // namespace tmo
 
 using namespace tmo;
 
-struct tmotif_server {
-    size_t budget = 0;
+// ---------------------------------------------------------------------------
+// Batched decisions
+// ---------------------------------------------------------------------------
+extern "C" int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_query *queries, uint32_t count,
+                                   tmotif_decision *out)
+{
+    if (count == 0) return TMOTIF_OK;
+    if (!graphs || !queries || !out) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    try {
+        std::vector<QuerySpec> specs(count);
+        for (uint32_t i = 0; i < count; i++) {
+            if (!graphs[i]) return fail(TMOTIF_ERR_INVALID, "null graph in batch").code;
+            Status s = parse_query(*graphs[i], &queries[i], &specs[i]);
+            if (!s.ok()) return s.code;
+            if (graphs[i]->stream != graphs[0]->stream)
+                return fail(TMOTIF_ERR_INVALID, "graphs of one batch must share a stream").code;
+        }
+        cudaStream_t st = graphs[0]->stream;
+        Scheduler sched(st, default_budget());
+        Status s = sched.init();
+        if (!s.ok()) return s.code;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        std::vector<std::unique_ptr<SJob>> done;
+        auto finish = [&](std::unique_ptr<SJob> &sj) {
+            const u64 i = sj->owner;
+            out[i].found = sj->job.found;
+            out[i].sieve_sum = sj->job.sieve_sum;
+            if (out[i].per_point && !sj->job.vals.empty())
+                std::memcpy(out[i].per_point, sj->job.vals.data(), sj->job.vals.size() * sizeof(u64));
+            else if (out[i].per_point)
+                std::memset(out[i].per_point, 0, (specs[i].p_end - specs[i].p_begin) * sizeof(u64));
+        };
+        uint32_t next = 0;
+        while (next < count || !sched.idle()) {
+            while (next < count) {
+                const size_t need = job_estimate(*graphs[next], specs[next]);
+                if (!sched.idle() && !sched.fits(need)) break;
+                auto sj = std::make_unique<SJob>();
+                sj->owner = next;
+                sj->job.g = graphs[next];
+                sj->job.q = specs[next];
+                s = sched.admit(std::move(sj), need, &done);
+                if (!s.ok()) return s.code;
+                next++;
+            }
+            s = sched.step(&done);
+            if (!s.ok()) return s.code;
+            for (auto &sj : done) finish(sj);
+            done.clear();
+        }
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (uint32_t i = 0; i < count; i++) out[i].ms = ms;
+        return TMOTIF_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Request server
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Request {
+    u64 ticket = 0;
+    Graph *g = nullptr;
+    QuerySpec q;
+    bool is_extract = false;
+    ExtractState ex;
+    Clock::time_point t_submit;
+    bool done = false;
+    int code = TMOTIF_OK;
+    std::string err;
+    int found = 0;
+    u64 sieve_sum = 0;
+    double ms = 0;
+    std::vector<u32> verts, times;
 };
 
-extern "C" {
+}  // namespace
 
-int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_query *queries, uint32_t count,
-                        tmotif_decision *out)
-{
-    if (count && (!graphs || !queries || !out)) return fail(TMOTIF_ERR_INVALID, "null argument").code;
-    for (uint32_t i = 0; i < count; i++) {
-        int rc = tmotif_decide(graphs[i], &queries[i], &out[i]);
-        if (rc != TMOTIF_OK) return rc;
+struct tmotif_server {
+    size_t budget = 0;
+    int device = 0;
+    cudaStream_t st = nullptr;
+    std::unique_ptr<Scheduler> sched;
+    Workspace finish_ws;  // arc gathering for extraction's final DFS
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request *> pending;           // submitted, not yet admitted
+    std::map<u64, std::unique_ptr<Request>> reqs;
+    std::atomic<bool> stop{false};
+    u64 next_ticket = 1;
+
+    void complete(Request *r, Status s)
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!s.ok()) {
+            r->code = s.code;
+            r->err = tmotif_last_error();
+        }
+        r->ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+        r->done = true;
     }
-    return TMOTIF_OK;
-}
 
-int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *out)
+    // Make the next job of a request (its decision, or its next probe).
+    // Returns false when the request needs no more jobs.
+    bool next_job(Request *r, std::unique_ptr<SJob> *out)
+    {
+        auto sj = std::make_unique<SJob>();
+        sj->owner = r->ticket;
+        sj->job.g = r->g;
+        if (!r->is_extract) {
+            sj->job.q = r->q;
+            *out = std::move(sj);
+            return true;
+        }
+        QuerySpec pq;
+        if (!r->ex.next_probe(&pq)) return false;
+        sj->job.q = pq;
+        if (r->ex.stage == ExtractState::PROBING) {
+            Status s = sched->set_mask(*sj, r->ex.alive);
+            if (!s.ok()) {
+                complete(r, s);
+                return false;
+            }
+        }
+        *out = std::move(sj);
+        return true;
+    }
+
+    void finish_extract(Request *r)
+    {
+        r->verts.assign(r->q.k, 0);
+        r->times.assign(r->q.k, 0);
+        Status s;
+        if (r->ex.stage == ExtractState::SHRUNK)
+            s = extract_finish(*r->g, finish_ws, st, sched->prof, r->ex, r->verts.data(), r->times.data(),
+                               &r->found);
+        else
+            r->found = 0;
+        complete(r, s);
+    }
+
+    void run()
+    {
+        cudaSetDevice(device);
+        std::deque<std::pair<Request *, std::unique_ptr<SJob>>> waiting;  // admission queue (FIFO)
+        std::vector<std::unique_ptr<SJob>> done;
+        while (!stop.load()) {
+            {
+                std::unique_lock<std::mutex> lock(mu);
+                if (pending.empty() && waiting.empty() && sched->idle())
+                    cv.wait_for(lock, std::chrono::milliseconds(2));
+                while (!pending.empty()) {
+                    Request *r = pending.front();
+                    pending.pop_front();
+                    waiting.push_back({r, nullptr});
+                }
+            }
+            // admit in arrival order while the memory budget allows
+            while (!waiting.empty()) {
+                Request *r = waiting.front().first;
+                std::unique_ptr<SJob> &sj = waiting.front().second;
+                if (!sj && !next_job(r, &sj)) {  // nothing to run (error already recorded)
+                    if (!r->done) finish_extract(r);
+                    waiting.pop_front();
+                    continue;
+                }
+                const size_t need = job_estimate(*r->g, sj->job.q);
+                if (!sched->idle() && !sched->fits(need)) break;
+                Status s = sched->admit(std::move(sj), need, &done);
+                waiting.pop_front();
+                if (!s.ok()) complete(r, s);
+            }
+            if (!sched->idle()) {
+                Status s = sched->step(&done);
+                if (!s.ok()) {  // fail every request in flight
+                    std::lock_guard<std::mutex> lock(mu);
+                    for (auto &kv : reqs)
+                        if (!kv.second->done) {
+                            kv.second->code = s.code;
+                            kv.second->done = true;
+                        }
+                    return;
+                }
+            }
+            for (auto &sj : done) {
+                Request *r = nullptr;
+                {
+                    std::lock_guard<std::mutex> lock(mu);
+                    auto it = reqs.find(sj->owner);
+                    if (it != reqs.end()) r = it->second.get();
+                }
+                if (!r) continue;
+                if (!r->is_extract) {
+                    r->found = sj->job.found;
+                    r->sieve_sum = sj->job.sieve_sum;
+                    complete(r, Status());
+                    continue;
+                }
+                r->ex.result(sj->job.found != 0);
+                if (r->ex.stage == ExtractState::NOT_FOUND) {
+                    finish_extract(r);
+                    continue;
+                }
+                // next probe joins the front of the admission queue (the request keeps its turn)
+                std::unique_ptr<SJob> nj;
+                if (next_job(r, &nj)) waiting.push_front({r, std::move(nj)});
+                else if (!r->done) finish_extract(r);
+            }
+            done.clear();
+        }
+    }
+};
+
+extern "C" int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *out)
 {
-    (void)hbm_budget_bytes;
-    if (out) *out = nullptr;
-    return fail(TMOTIF_ERR_UNSUPPORTED, "server not built yet").code;
+    if (!out) return fail(TMOTIF_ERR_INVALID, "null output handle").code;
+    *out = nullptr;
+    try {
+        auto s = std::make_unique<tmotif_server>();
+        if (cudaGetDevice(&s->device) != cudaSuccess) return fail(TMOTIF_ERR_CUDA, "no CUDA device").code;
+        s->budget = hbm_budget_bytes ? hbm_budget_bytes : default_budget();
+        cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "server stream").code;
+        s->sched = std::make_unique<Scheduler>(s->st, s->budget);
+        Status st = s->sched->init();
+        if (!st.ok()) return st.code;
+        s->finish_ws.set_stream(s->st);
+        tmotif_server *raw = s.get();
+        s->worker = std::thread([raw] { raw->run(); });
+        *out = s.release();
+        return TMOTIF_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
 }
 
-int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_query *q, int is_extract, uint64_t *ticket)
+extern "C" int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_query *q, int is_extract,
+                             uint64_t *ticket)
 {
-    (void)s; (void)g; (void)q; (void)is_extract; (void)ticket;
-    return fail(TMOTIF_ERR_UNSUPPORTED, "server not built yet").code;
+    if (!s || !g || !ticket) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    try {
+        auto r = std::make_unique<Request>();
+        Status st = parse_query(*g, q, &r->q);
+        if (!st.ok()) return st.code;
+        if (is_extract && (r->q.p_begin != 0 || r->q.p_end != (1ull << r->q.k)))
+            return fail(TMOTIF_ERR_INVALID, "extraction needs the full point range").code;
+        if (job_estimate(*g, r->q) > s->budget)
+            return fail(TMOTIF_ERR_BUSY, "request needs more device memory than the server budget").code;
+        r->g = g;
+        r->is_extract = is_extract != 0;
+        if (r->is_extract) r->ex.init(*g, r->q);
+        r->t_submit = Clock::now();
+        std::lock_guard<std::mutex> lock(s->mu);
+        r->ticket = s->next_ticket++;
+        *ticket = r->ticket;
+        s->pending.push_back(r.get());
+        s->reqs[r->ticket] = std::move(r);
+        s->cv.notify_one();
+        return TMOTIF_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
 }
 
-int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *out, uint32_t *verts, uint32_t *times,
-                int *done)
+extern "C" int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *out, uint32_t *verts,
+                           uint32_t *times, int *done)
 {
-    (void)s; (void)ticket; (void)out; (void)verts; (void)times; (void)done;
-    return fail(TMOTIF_ERR_UNSUPPORTED, "server not built yet").code;
+    if (!s || !done) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(TMOTIF_ERR_NOT_FOUND, "unknown ticket").code;
+    Request *r = it->second.get();
+    *done = r->done ? 1 : 0;
+    if (!r->done) return TMOTIF_OK;
+    const int code = r->code;
+    if (code != TMOTIF_OK) set_error(r->err);
+    if (out) {
+        out->found = r->found;
+        out->sieve_sum = r->sieve_sum;
+        out->ms = r->ms;
+    }
+    if (r->is_extract && r->found) {
+        if (verts) std::copy(r->verts.begin(), r->verts.begin() + r->q.k, verts);
+        if (times) std::copy(r->times.begin(), r->times.begin() + (r->q.k - 1), times);
+    }
+    s->reqs.erase(it);
+    return code;
 }
 
-void tmotif_server_destroy(tmotif_server_t s) { delete s; }
-
-}  // extern "C"
+extern "C" void tmotif_server_destroy(tmotif_server_t s)
+{
+    if (!s) return;
+    s->stop.store(true);
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    s->sched.reset();
+    s->finish_ws.release();
+    if (s->st) {
+        cudaStreamSynchronize(s->st);
+        cudaStreamDestroy(s->st);
+    }
+    delete s;
+}

@@ -21,107 +21,14 @@
 
 #include "gf64.cuh"
 #include "internal.h"
+#include "scan.cuh"
 
 namespace tmo {
-
-// ---------------------------------------------------------------------------
-// Exclusive scan of u32 arrays (three phases: tile sums, scan of tile sums,
-// tile scan).  Totals fit in u32 because arc counts are < 2^32.
-// ---------------------------------------------------------------------------
-static const int SCAN_THREADS = 256;
-static const int SCAN_PER_THREAD = 16;
-static const int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
-
-__device__ __forceinline__ u32 block_exclusive_scan(u32 v, u32 *total)
-{
-    __shared__ u32 warp_sums[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    u32 x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        u32 y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-        u32 s = lane < nw ? warp_sums[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            u32 y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
-        }
-        if (lane < nw) warp_sums[lane] = s;
-    }
-    __syncthreads();
-    u32 before = (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
-    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
-    __syncthreads();
-    return before;
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_tile_sum(const u32 *in, u64 N, u32 *tile_sums)
-{
-    u64 base = (u64)blockIdx.x * SCAN_TILE + (u64)threadIdx.x * SCAN_PER_THREAD;
-    u32 s = 0;
-#pragma unroll
-    for (int i = 0; i < SCAN_PER_THREAD; i++)
-        if (base + i < N) s += in[base + i];
-    u32 tot;
-    block_exclusive_scan(s, &tot);
-    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
-}
-
-// One block: exclusive scan of ntiles values in place; total to *total.
-__global__ void __launch_bounds__(1024) k_scan_tiles(u32 *sums, u32 ntiles, u32 *total)
-{
-    const u32 per = (ntiles + blockDim.x - 1) / blockDim.x;
-    const u32 b = threadIdx.x * per, e = min(ntiles, b + per);
-    u32 s = 0;
-    for (u32 i = b; i < e; i++) s += sums[i];
-    u32 tot;
-    u32 run = block_exclusive_scan(s, &tot);
-    for (u32 i = b; i < e; i++) {
-        u32 v = sums[i];
-        sums[i] = run;
-        run += v;
-    }
-    if (threadIdx.x == 0) *total = tot;
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(const u32 *in, u64 N, const u32 *tile_off, u32 *out)
-{
-    u64 base = (u64)blockIdx.x * SCAN_TILE + (u64)threadIdx.x * SCAN_PER_THREAD;
-    u32 v[SCAN_PER_THREAD];
-    u32 s = 0;
-#pragma unroll
-    for (int i = 0; i < SCAN_PER_THREAD; i++) {
-        v[i] = (base + i < N) ? in[base + i] : 0;
-        s += v[i];
-    }
-    u32 run = block_exclusive_scan(s, nullptr) + tile_off[blockIdx.x];
-#pragma unroll
-    for (int i = 0; i < SCAN_PER_THREAD; i++) {
-        if (base + i < N) out[base + i] = run;
-        run += v[i];
-    }
-}
 
 // In-place exclusive scan of a[0..N); writes the total to d_total (device u32).
 static Status exclusive_scan(Graph &g, u32 *a, u64 N, u32 *d_total)
 {
-    Workspace &w = g.ws;
-    u64 ntiles = (N + SCAN_TILE - 1) / SCAN_TILE;
-    if (ntiles == 0) ntiles = 1;
-    TM_TRY(w.block_sums.reserve(ntiles * sizeof(u32)));
-    u32 *sums = w.block_sums.as<u32>();
-    k_tile_sum<<<(unsigned)ntiles, SCAN_THREADS, 0, g.stream>>>(a, N, sums);
-    k_scan_tiles<<<1, 1024, 0, g.stream>>>(sums, (u32)ntiles, d_total);
-    k_tile_scan<<<(unsigned)ntiles, SCAN_THREADS, 0, g.stream>>>(a, N, sums, a);
-    g.prof.stats.launches += 3;
-    TM_CUDA(cudaGetLastError());
-    return Status();
+    return exclusive_scan_on(g.stream, g.ws.block_sums, a, N, d_total, (u64 *)&g.prof.stats.launches);
 }
 
 // ---------------------------------------------------------------------------
@@ -237,126 +144,140 @@ __global__ void k_coef(u32 n, u32 L, const uint8_t *vflag, const u32 *color, con
 }
 
 // ---------------------------------------------------------------------------
-// Layer kernel: eq. (gen-polynomial:3), one walk length per launch.
+// Layer kernel: eq. (gen-polynomial:3), one walk length per job per launch.
 // ---------------------------------------------------------------------------
-struct LayerParams {
-    const u32 *src, *dst, *time, *cp_in, *cp_out, *seg_hi;
-    const u64 *x;
-    const u64 *Cin;
-    u64 *Cout;
-    u64 *out;
-    u64 m_f;
-    u64 n_chunks;
-    u64 ky;
-    u32 L, lane_groups, chunk, ell, k, start, end;
-};
-
-// A team of T threads owns 2T consecutive lanes (16 bytes per thread) and walks
-// one chunk of whole in-segments in arc order.  Segments are never split, so a
-// running XOR is the prefix of eq. (3)'s stay term.  With TAB the team builds,
-// per arc, the nibble table of y_{e,l-1} in shared memory and every lane's
-// y-product is 16 table loads; x-products (one per checkpoint and per segment
-// at the last layer) use the register multiply.
+// A team of T threads owns 2T consecutive lanes (16 bytes per thread) of one
+// job and walks one chunk of whole in-segments in arc order.  Segments are
+// never split, so a running XOR is the prefix of eq. (3)'s stay term.  With
+// TAB the team builds, per arc, the nibble table of y_{e,l-1} in shared memory
+// and every lane's y-product is 16 table loads; x-products (one per
+// checkpoint and per segment at the last layer) use the register multiply.
+// One launch can carry many jobs (njobs > 0: the team's job is found in the
+// prefix of team counts); njobs = 0 means the single job in `one`.  At the
+// last layer every team writes its lanes' sums to the job's partial array.
 template <int T, bool TAB>
-__global__ void __launch_bounds__(256) k_layer(LayerParams p)
+__device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *tab)
 {
-    extern __shared__ __align__(16) u64 smem[];
-    u64 *red = smem;
-    u64 *tab = smem + ((p.L + 1u) & ~1u) + (size_t)(threadIdx.x / T) * 256;
-    for (u32 i = threadIdx.x; i < p.L; i += blockDim.x) red[i] = 0;
-    __syncthreads();
-
     const int tt = threadIdx.x % T;
     const u32 team_mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (((threadIdx.x & 31) / T) * T));
-    const u64 team = (u64)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
     const u64 chunk = team / p.lane_groups;
+    if (chunk >= p.n_chunks) return;
     const u32 lane0 = (u32)(team % p.lane_groups) * (2 * T) + 2 * tt;
     const u64 Lw = p.L;
+    const bool last = (p.ell == p.k);
     u64 q0 = 0, q1 = 0;
 
-    if (chunk < p.n_chunks) {
-        const u64 b0 = chunk * p.chunk;
-        const u64 b1 = min(b0 + p.chunk, p.m_f);
-        u64 begin = b0, stop = b1;
-        if (b0 > 0 && p.dst[b0] == p.dst[b0 - 1]) begin = p.seg_hi[p.dst[b0]];
-        if (b1 < p.m_f && p.dst[b1] == p.dst[b1 - 1]) stop = p.seg_hi[p.dst[b1]];
+    const u64 b0 = chunk * p.chunk;
+    const u64 b1 = min(b0 + p.chunk, p.m_f);
+    u64 begin = b0, stop = b1;
+    if (b0 > 0 && p.dst[b0] == p.dst[b0 - 1]) begin = p.seg_hi[p.dst[b0]];
+    if (b1 < p.m_f && p.dst[b1] == p.dst[b1 - 1]) stop = p.seg_hi[p.dst[b1]];
 
-        u32 cur = NONE;
-        u64 xc0 = 0, xc1 = 0, acc0 = 0, acc1 = 0;
-        const bool last = (p.ell == p.k);
-        for (u64 base = begin; base < stop; base += T) {
-            const u64 e = base + tt;
-            u32 s = 0, d = NONE, ci = NONE, co = NONE;
-            u64 y = 0;
-            if (e < stop) {
-                s = p.src[e];
-                d = p.dst[e];
-                const u32 t = p.time[e];
-                if (p.ell > 2) ci = p.cp_in[e];
-                if (!last) co = p.cp_out[e];
-                y = coef_y(mix64(p.ky ^ (((u64)s << 32) | d)), t, p.ell - 1);
-            }
-            const int cnt = (int)min((u64)T, stop - base);
-            for (int j = 0; j < cnt; j++) {
-                const u32 dj = __shfl_sync(team_mask, d, j, T);
-                const u32 sj = __shfl_sync(team_mask, s, j, T);
-                const u32 cij = __shfl_sync(team_mask, ci, j, T);
-                const u32 coj = __shfl_sync(team_mask, co, j, T);
-                const u64 yj = __shfl_sync(team_mask, y, j, T);
-                if (dj != cur) {
-                    if (last && cur != NONE && (p.end == NONE || cur == p.end)) {
-                        q0 ^= gf_mul(xc0, acc0);
-                        q1 ^= gf_mul(xc1, acc1);
-                    }
-                    cur = dj;
-                    acc0 = acc1 = 0;
-                    const ulonglong2 xv = *(const ulonglong2 *)(p.x + (u64)dj * Lw + lane0);
-                    xc0 = xv.x;
-                    xc1 = xv.y;
+    u32 cur = NONE;
+    u64 xc0 = 0, xc1 = 0, acc0 = 0, acc1 = 0;
+    for (u64 base = begin; base < stop; base += T) {
+        const u64 e = base + tt;
+        u32 s = 0, d = NONE, ci = NONE, co = NONE;
+        u64 y = 0;
+        if (e < stop) {
+            s = p.src[e];
+            d = p.dst[e];
+            const u32 t = p.time[e];
+            if (p.ell > 2) ci = p.cp_in[e];
+            if (!last) co = p.cp_out[e];
+            y = coef_y(mix64(p.ky ^ (((u64)s << 32) | d)), t, p.ell - 1);
+        }
+        const int cnt = (int)min((u64)T, stop - base);
+        for (int j = 0; j < cnt; j++) {
+            const u32 dj = __shfl_sync(team_mask, d, j, T);
+            const u32 sj = __shfl_sync(team_mask, s, j, T);
+            const u32 cij = __shfl_sync(team_mask, ci, j, T);
+            const u32 coj = __shfl_sync(team_mask, co, j, T);
+            const u64 yj = __shfl_sync(team_mask, y, j, T);
+            if (dj != cur) {
+                if (last && cur != NONE && (p.end == NONE || cur == p.end)) {
+                    q0 ^= gf_mul(xc0, acc0);
+                    q1 ^= gf_mul(xc1, acc1);
                 }
-                bool have = false;
-                ulonglong2 in;
-                if (p.ell == 2) {
-                    if (p.start == NONE || sj == p.start) {
-                        in = *(const ulonglong2 *)(p.x + (u64)sj * Lw + lane0);
-                        have = true;
-                    }
-                } else if (cij != NONE) {
-                    in = *(const ulonglong2 *)(p.Cin + (u64)cij * Lw + lane0);
+                cur = dj;
+                acc0 = acc1 = 0;
+                const ulonglong2 xv = *(const ulonglong2 *)(p.x + (u64)dj * Lw + lane0);
+                xc0 = xv.x;
+                xc1 = xv.y;
+            }
+            bool have = false;
+            ulonglong2 in;
+            if (p.ell == 2) {
+                if (p.start == NONE || sj == p.start) {
+                    in = *(const ulonglong2 *)(p.x + (u64)sj * Lw + lane0);
                     have = true;
                 }
-                if (have) {  // uniform across the team
-                    if (TAB) {
-                        __syncwarp(team_mask);  // earlier lookups are done
-                        gf_table_build(tab, yj, tt, T);
-                        __syncwarp(team_mask);  // table complete
-                        acc0 ^= gf_table_mul(tab, in.x);
-                        acc1 ^= gf_table_mul(tab, in.y);
-                    } else {
-                        acc0 ^= gf_mul(yj, in.x);
-                        acc1 ^= gf_mul(yj, in.y);
-                    }
-                }
-                if (coj != NONE) {
-                    ulonglong2 o;
-                    o.x = gf_mul(xc0, acc0);
-                    o.y = gf_mul(xc1, acc1);
-                    *(ulonglong2 *)(p.Cout + (u64)coj * Lw + lane0) = o;
+            } else if (cij != NONE) {
+                in = *(const ulonglong2 *)(p.Cin + (u64)cij * Lw + lane0);
+                have = true;
+            }
+            if (have) {  // uniform across the team
+                if (TAB) {
+                    __syncwarp(team_mask);  // earlier lookups are done
+                    gf_table_build(tab, yj, tt, T);
+                    __syncwarp(team_mask);  // table complete
+                    acc0 ^= gf_table_mul(tab, in.x);
+                    acc1 ^= gf_table_mul(tab, in.y);
+                } else {
+                    acc0 ^= gf_mul(yj, in.x);
+                    acc1 ^= gf_mul(yj, in.y);
                 }
             }
+            if (coj != NONE) {
+                ulonglong2 o;
+                o.x = gf_mul(xc0, acc0);
+                o.y = gf_mul(xc1, acc1);
+                *(ulonglong2 *)(p.Cout + (u64)coj * Lw + lane0) = o;
+            }
         }
-        if (last && cur != NONE && (p.end == NONE || cur == p.end)) {
+    }
+    if (last) {
+        if (cur != NONE && (p.end == NONE || cur == p.end)) {
             q0 ^= gf_mul(xc0, acc0);
             q1 ^= gf_mul(xc1, acc1);
         }
+        *(ulonglong2 *)(p.partial + chunk * Lw + lane0) = make_ulonglong2(q0, q1);
     }
-    if (p.ell == p.k) {
-        if (q0) atomicXor(&red[lane0], q0);
-        if (q1) atomicXor(&red[lane0 + 1], q1);
-        __syncthreads();
-        for (u32 i = threadIdx.x; i < p.L; i += blockDim.x)
-            if (red[i]) atomicXor(&p.out[i], red[i]);
+}
+
+// MULTI = false: the single job in `one` (read from parameter space);
+// MULTI = true: the team's job is found in the prefix of team counts.
+template <int T, bool TAB, bool MULTI>
+__global__ void __launch_bounds__(256) k_layer(LayerParams one, const LayerParams *__restrict__ jobs,
+                                               const u64 *__restrict__ team_prefix, u32 njobs)
+{
+    extern __shared__ __align__(16) u64 smem[];
+    u64 *tab = smem + (size_t)(threadIdx.x / T) * 256;
+    const u64 team = (u64)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
+    if (!MULTI) {
+        layer_team<T, TAB>(one, team, tab);
+        return;
     }
+    if (team >= team_prefix[njobs]) return;
+    u32 lo = 0, hi = njobs;  // last job with team_prefix[job] <= team
+    while (hi - lo > 1) {
+        const u32 mid = (lo + hi) >> 1;
+        if (team_prefix[mid] <= team) lo = mid;
+        else hi = mid;
+    }
+    layer_team<T, TAB>(jobs[lo], team - team_prefix[lo], tab);
+}
+
+// out[lane] = XOR over chunks of partial[chunk * L + lane]; blockDim.x = L,
+// gridDim.x = chunk slices (each XORs its slice, then one atomic per lane).
+__global__ void k_reduce_partials(const u64 *partial, u64 n_chunks, u32 L, u64 *out)
+{
+    const u32 lane = threadIdx.x;
+    const u64 per = (n_chunks + gridDim.x - 1) / gridDim.x;
+    const u64 c0 = blockIdx.x * per, c1 = min(n_chunks, c0 + per);
+    u64 s = 0;
+    for (u64 c = c0; c < c1; c++) s ^= partial[c * L + lane];
+    if (s) atomicXor(&out[lane], s);
 }
 
 // ---------------------------------------------------------------------------
@@ -366,6 +287,66 @@ __global__ void k_gf_mul(const u64 *a, const u64 *b, u64 *out, u64 n)
 {
     u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = gf_mul(a[i], b[i]);
+}
+
+// Throughput probe of the two product forms on register-resident data: every
+// warp runs `iters` rounds; a round multiplies 64 lanes (2 per thread) by one
+// multiplier, which changes every round.  method 0: register multiply;
+// method 1: shared-memory nibble table built by the warp, then looked up.
+template <int METHOD>
+__global__ void __launch_bounds__(256) k_gf_probe(u32 iters, u64 seed, u64 *sink)
+{
+    __shared__ __align__(16) u64 tabs[8][256];
+    u64 *tab = tabs[threadIdx.x >> 5];
+    const int tt = threadIdx.x & 31;
+    u64 a0 = mix64(seed + blockIdx.x * 256 + threadIdx.x), a1 = mix64(a0), y = mix64(seed ^ blockIdx.x);
+    u64 acc0 = 0, acc1 = 0;
+    for (u32 it = 0; it < iters; it++) {
+        if (METHOD == 0) {
+            acc0 ^= gf_mul(y, a0);
+            acc1 ^= gf_mul(y, a1);
+        } else {
+            __syncwarp();
+            gf_table_build(tab, y, tt, 32);
+            __syncwarp();
+            acc0 ^= gf_table_mul(tab, a0);
+            acc1 ^= gf_table_mul(tab, a1);
+        }
+        a0 += acc1;
+        a1 ^= acc0;
+        y += TM_GOLDEN;
+    }
+    if ((acc0 ^ acc1) == 0x5151ull) sink[0] = acc0;
+}
+
+Status gf_probe(int method, u32 iters, double *ms, u64 *products)
+{
+    u64 *sink = nullptr;
+    TM_CUDA(cudaMalloc(&sink, 64));
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned blocks = (unsigned)sms * 8;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    if (method == 0) k_gf_probe<0><<<blocks, 256>>>(4, 1, sink);
+    else k_gf_probe<1><<<blocks, 256>>>(4, 1, sink);
+    cudaEventRecord(a);
+    if (method == 0) k_gf_probe<0><<<blocks, 256>>>(iters, 7, sink);
+    else k_gf_probe<1><<<blocks, 256>>>(iters, 7, sink);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float f = 0;
+    cudaEventElapsedTime(&f, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(e, "gf_probe");
+    TM_CUDA(cudaGetLastError());
+    *ms = f;
+    *products = (u64)blocks * 256 * 2 * iters;
+    return Status();
 }
 
 Status gf_mul_batch(const u64 *a, const u64 *b, u64 *out, u64 n)
@@ -386,100 +367,72 @@ Status gf_mul_batch(const u64 *a, const u64 *b, u64 *out, u64 n)
 }
 
 // ---------------------------------------------------------------------------
-// Host orchestration of one decision.
+// Host orchestration: jobs.
 // ---------------------------------------------------------------------------
 static inline unsigned grid_for(u64 items, int threads) { return (unsigned)((items + threads - 1) / threads); }
 
-template <int T, bool TAB>
-static Status launch_layer_t(Graph &g, const LayerParams &lp, u64 teams)
-{
-    const int threads = 256;
-    const u64 teams_per_block = threads / T;
-    const unsigned blocks = (unsigned)((teams + teams_per_block - 1) / teams_per_block);
-    const size_t smem = (((size_t)lp.L + 1) & ~(size_t)1) * sizeof(u64) + (TAB ? teams_per_block * 256 * 8 : 0);
-    static bool attr_set = false;
-    if (!attr_set) {
-        TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-        attr_set = true;
-    }
-    k_layer<T, TAB><<<blocks, threads, smem, g.stream>>>(lp);
-    return Status();
-}
-
-static Status launch_layer(Graph &g, const LayerParams &lp, int T, u64 teams)
-{
-    // L <= 64 lanes per batch, so the shared XOR buffer is at most 512 B; the
-    // tables take 2 KB per team.
-    switch (T) {
-        case 2: TM_TRY((launch_layer_t<2, false>(g, lp, teams))); break;
-        case 4: TM_TRY((launch_layer_t<4, false>(g, lp, teams))); break;
-        case 8: TM_TRY((launch_layer_t<8, false>(g, lp, teams))); break;
-        case 16: TM_TRY((launch_layer_t<16, false>(g, lp, teams))); break;
-        default: TM_TRY((launch_layer_t<32, false>(g, lp, teams))); break;
-    }
-    g.prof.stats.launches++;
-    g.prof.stats.layer_launches++;
-    TM_CUDA(cudaGetLastError());
-    return Status();
-}
-
 static const u32 LANES_MAX = 64;  // lanes per batch (one warp owns 64 lanes)
+static const u32 CHUNK = 128;     // arcs per team chunk (whole in-segments)
+static const size_t PIN_BYTES = 64 + LANES_MAX * 8;
 
-Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *found, u64 *sieve_sum,
-                    u64 *per_point, double *ms)
+static Status ensure_pinned(Workspace &w)
 {
-    Workspace &w = g.ws;
-    cudaStream_t st = g.stream;
-    const u32 n = g.n, k = q.k;
-    const u64 m = g.m;
-    *found = 0;
-    *sieve_sum = 0;
+    if (w.host_pinned_bytes >= PIN_BYTES) return Status();
+    if (w.host_pinned) cudaFreeHost(w.host_pinned);
+    w.host_pinned = nullptr;
+    TM_CUDA(cudaMallocHost(&w.host_pinned, PIN_BYTES));
+    w.host_pinned_bytes = PIN_BYTES;
+    return Status();
+}
 
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    TM_CUDA(cudaEventCreate(&ev0));
-    TM_CUDA(cudaEventCreate(&ev1));
-    TM_CUDA(cudaEventRecord(ev0, st));
+size_t job_bytes(const Job &j)
+{
+    const u64 n = j.g->n, m = j.mf ? j.mf : j.g->m, L = j.L ? j.L : LANES_MAX;
+    const u64 ncp = j.mf ? j.ncp : m;
+    return (size_t)(n * (1 + 8) + (j.g->m + 1) * 4 + m * 28 + n * L * 8 + 2 * ncp * L * 8 +
+                    ((m + CHUNK - 1) / CHUNK) * L * 8 + 4096);
+}
+
+Status job_prep(Job &j)
+{
+    Graph &g = *j.g;
+    Workspace &w = *j.ws;
+    const cudaStream_t st = j.st;
+    const QuerySpec &q = j.q;
+    const u32 n = g.n;
+    const u64 m = g.m;
+    u64 *launches = (u64 *)&j.prof->stats.launches;
 
     // slots: distinct colours of M ascending get consecutive slot ranges
     std::vector<u32> sb(g.num_colors, 0), sc(g.num_colors, 0);
     for (u32 c : q.multiset) sc[c]++;
-    {
-        u32 off = 0;
-        for (u32 c = 0; c < g.num_colors; c++) { sb[c] = off; off += sc[c]; }
-    }
+    for (u32 c = 0, off = 0; c < g.num_colors; c++) { sb[c] = off; off += sc[c]; }
     TM_TRY(w.slot_begin.reserve(g.num_colors * sizeof(u32)));
     TM_TRY(w.slot_count.reserve(g.num_colors * sizeof(u32)));
     TM_TRY(w.counters.reserve(64));
-    if (w.host_pinned_bytes < 64 + LANES_MAX * 8) {
-        if (w.host_pinned) cudaFreeHost(w.host_pinned);
-        w.host_pinned = nullptr;
-        TM_CUDA(cudaMallocHost(&w.host_pinned, 64 + LANES_MAX * 8));
-        w.host_pinned_bytes = 64 + LANES_MAX * 8;
-    }
+    TM_TRY(ensure_pinned(w));
     u32 *h_cnt = (u32 *)w.host_pinned;
-    u64 *h_out = (u64 *)((char *)w.host_pinned + 64);
     TM_CUDA(cudaMemcpyAsync(w.slot_begin.p, sb.data(), g.num_colors * 4, cudaMemcpyHostToDevice, st));
     TM_CUDA(cudaMemcpyAsync(w.slot_count.p, sc.data(), g.num_colors * 4, cudaMemcpyHostToDevice, st));
     u32 *d_cnt = w.counters.as<u32>();
 
-    // ---- prep: filter arcs (Sec. 7.1 (i)) ----
+    // filter arcs (Sec. 7.1 (i): colours outside M, masked vertices, window)
     cudaEvent_t pa = nullptr;
-    TM_TRY(g.prof.begin(st, &pa));
+    TM_TRY(j.prof->begin(st, &pa));
     TM_TRY(w.vflag.reserve(std::max<u64>(n, 1)));
     TM_TRY(w.keep.reserve((m + 1) * 4));
-    k_vflag<<<grid_for(n, 256), 256, 0, st>>>(n, g.d_color, w.slot_count.as<u32>(), d_alive, w.vflag.as<uint8_t>());
+    k_vflag<<<grid_for(n, 256), 256, 0, st>>>(n, g.d_color, w.slot_count.as<u32>(), j.d_alive, w.vflag.as<uint8_t>());
     k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), q.t_min,
                                                  q.t_max, w.keep.as<u32>());
-    g.prof.stats.launches += 2;
+    *launches += 2;
     TM_CUDA(cudaGetLastError());
-    TM_TRY(exclusive_scan(g, w.keep.as<u32>(), m + 1, d_cnt + 0));
+    TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt + 0, launches));
     TM_CUDA(cudaMemcpyAsync(h_cnt, d_cnt, 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
-    const u64 mf = h_cnt[0];
-
-    u64 npts = q.p_end - q.p_begin;
-    std::vector<u64> vals(npts, 0);
-    if (mf > 0) {
+    j.mf = h_cnt[0];
+    j.ncp = 0;
+    if (j.mf > 0) {
+        const u64 mf = j.mf;
         TM_TRY(w.f_src.reserve(mf * 4));
         TM_TRY(w.f_dst.reserve(mf * 4));
         TM_TRY(w.f_time.reserve(mf * 4));
@@ -497,101 +450,260 @@ Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *f
         k_segments<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_dst.as<u32>(), w.seg_lo.as<u32>(), w.seg_hi.as<u32>());
         k_pos<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_src.as<u32>(), w.f_time.as<u32>(), w.seg_lo.as<u32>(),
                                                  w.seg_hi.as<u32>(), w.pos.as<u32>(), w.mark.as<u32>());
-        g.prof.stats.launches += 3;
+        *launches += 3;
         TM_CUDA(cudaGetLastError());
-        TM_TRY(exclusive_scan(g, w.mark.as<u32>(), mf + 1, d_cnt + 1));
+        TM_TRY(exclusive_scan_on(st, w.block_sums, w.mark.as<u32>(), mf + 1, d_cnt + 1, launches));
         k_checkpoints<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.pos.as<u32>(), w.mark.as<u32>(), w.cp_in.as<u32>(),
                                                          w.cp_out.as<u32>());
-        g.prof.stats.launches++;
+        *launches += 1;
         TM_CUDA(cudaGetLastError());
         TM_CUDA(cudaMemcpyAsync(h_cnt + 1, d_cnt + 1, 4, cudaMemcpyDeviceToHost, st));
     }
-    TM_TRY(g.prof.end(st, pa, FAM_PREP));
+    TM_TRY(j.prof->end(st, pa, FAM_PREP));
     TM_CUDA(cudaStreamSynchronize(st));
-    const u64 ncp = mf > 0 ? h_cnt[1] : 0;
+    if (j.mf > 0) j.ncp = h_cnt[1];
 
-    if (mf > 0) {
-        // lane width: power of two >= 4, at most LANES_MAX
-        u32 L = 4;
-        while (L < LANES_MAX && L < npts) L <<= 1;
-        const int T = (int)(L / 2 > 32 ? 32 : L / 2);
-        const u32 lane_groups = L / (2 * T);
-        TM_TRY(w.x.reserve((u64)n * L * 8));
-        TM_TRY(w.C0.reserve(std::max<u64>(ncp, 1) * L * 8));
-        TM_TRY(w.C1.reserve(std::max<u64>(ncp, 1) * L * 8));
-        TM_TRY(w.out.reserve(L * 8));
-        TM_TRY(w.wtab.reserve((u64)k * L * 8));
-        const u32 chunk = 128;
-        const u64 n_chunks = (mf + chunk - 1) / chunk;
-        for (u32 r = 0; r < q.repeats; r++) {
-            const QueryKeys keys = make_keys(mix64(q.seed + (u64)(r + 1) * TM_GOLDEN));
-            u64 qsum = 0;
-            for (u64 p0 = q.p_begin; p0 < q.p_end; p0 += L) {
-                const u64 cnt = std::min<u64>(L, q.p_end - p0);
-                cudaEvent_t ca = nullptr;
-                TM_TRY(g.prof.begin(st, &ca));
-                k_wtab<<<grid_for((u64)k * L, 128), 128, 0, st>>>(k, L, p0, keys, w.wtab.as<u64>());
-                k_coef<<<grid_for((u64)n * L, 256), 256, 0, st>>>(n, L, w.vflag.as<uint8_t>(), g.d_color,
-                                                                  w.slot_begin.as<u32>(), w.slot_count.as<u32>(),
-                                                                  keys, w.wtab.as<u64>(), w.x.as<u64>());
-                g.prof.stats.launches += 2;
-                TM_CUDA(cudaGetLastError());
-                TM_CUDA(cudaMemsetAsync(w.out.p, 0, L * 8, st));
-                TM_TRY(g.prof.end(st, ca, FAM_COEF));
-                LayerParams lp;
-                lp.src = w.f_src.as<u32>();
-                lp.dst = w.f_dst.as<u32>();
-                lp.time = w.f_time.as<u32>();
-                lp.cp_in = w.cp_in.as<u32>();
-                lp.cp_out = w.cp_out.as<u32>();
-                lp.seg_hi = w.seg_hi.as<u32>();
-                lp.x = w.x.as<u64>();
-                lp.out = w.out.as<u64>();
-                lp.m_f = mf;
-                lp.n_chunks = n_chunks;
-                lp.ky = keys.ky;
-                lp.L = L;
-                lp.lane_groups = lane_groups;
-                lp.chunk = chunk;
-                lp.k = k;
-                lp.start = q.start;
-                lp.end = q.end;
-                u64 *bufs[2] = {w.C0.as<u64>(), w.C1.as<u64>()};
-                for (u32 ell = 2; ell <= k; ell++) {
-                    lp.ell = ell;
-                    lp.Cin = bufs[ell & 1];
-                    lp.Cout = bufs[(ell + 1) & 1];
-                    cudaEvent_t la = nullptr;
-                    TM_TRY(g.prof.begin(st, &la));
-                    TM_TRY(launch_layer(g, lp, T, n_chunks * lane_groups));
-                    TM_TRY(g.prof.end(st, la, FAM_LAYER));
-                }
-                g.prof.stats.layer_arc_lanes += mf * (k - 1) * L;
-                g.prof.stats.layer_cp_lanes += ncp * (k - 2) * L;
-                // algorithmic bytes: per arc-lane one 8-byte read of the source
-                // state (x at layer 2, a checkpoint above); per checkpoint-lane
-                // one 8-byte write (layers 2..k-1)
-                g.prof.stats.layer_bytes += (mf * (k - 1) + ncp * (k - 2)) * (u64)L * 8;
-                g.prof.stats.layer_gf_muls += (mf * (k - 1) + ncp * (k - 2)) * (u64)L;
-                TM_CUDA(cudaMemcpyAsync(h_out, w.out.p, L * 8, cudaMemcpyDeviceToHost, st));
-                TM_CUDA(cudaStreamSynchronize(st));
-                for (u64 i = 0; i < cnt; i++) {
-                    qsum ^= h_out[i];
-                    if (r == 0) vals[p0 - q.p_begin + i] = h_out[i];
-                }
-            }
-            if (r == 0) *sieve_sum = qsum;
-            if (qsum != 0) *found = 1;
-        }
+    const u64 npts = q.p_end - q.p_begin;
+    j.vals.assign(npts, 0);
+    j.r = 0;
+    j.p0 = q.p_begin;
+    j.qsum = 0;
+    j.found = 0;
+    j.sieve_sum = 0;
+    j.done = (j.mf == 0);
+    if (j.done) return Status();
+    // lane width: power of two >= 4, at most LANES_MAX
+    u32 L = 4;
+    while (L < LANES_MAX && L < npts) L <<= 1;
+    j.L = L;
+    j.T = L / 2 > 32 ? 32 : L / 2;
+    j.lane_groups = L / (2 * j.T);
+    j.chunk = CHUNK;
+    j.n_chunks = (j.mf + CHUNK - 1) / CHUNK;
+    TM_TRY(w.x.reserve((u64)n * L * 8));
+    TM_TRY(w.C0.reserve(std::max<u64>(j.ncp, 1) * L * 8));
+    TM_TRY(w.C1.reserve(std::max<u64>(j.ncp, 1) * L * 8));
+    TM_TRY(w.out.reserve(L * 8));
+    TM_TRY(w.wtab.reserve((u64)q.k * L * 8));
+    TM_TRY(w.partial.reserve(j.n_chunks * L * 8));
+    return Status();
+}
+
+Status job_batch_begin(Job &j)
+{
+    Graph &g = *j.g;
+    Workspace &w = *j.ws;
+    const cudaStream_t st = j.st;
+    const u32 L = j.L, k = j.q.k, n = g.n;
+    const QueryKeys keys = make_keys(mix64(j.q.seed + (u64)(j.r + 1) * TM_GOLDEN));
+    j.ky = keys.ky;
+    cudaEvent_t ca = nullptr;
+    TM_TRY(j.prof->begin(st, &ca));
+    k_wtab<<<grid_for((u64)k * L, 128), 128, 0, st>>>(k, L, j.p0, keys, w.wtab.as<u64>());
+    k_coef<<<grid_for((u64)n * L, 256), 256, 0, st>>>(n, L, w.vflag.as<uint8_t>(), g.d_color,
+                                                      w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
+                                                      w.wtab.as<u64>(), w.x.as<u64>());
+    j.prof->stats.launches += 2;
+    TM_CUDA(cudaGetLastError());
+    TM_CUDA(cudaMemsetAsync(w.out.p, 0, L * 8, st));
+    TM_TRY(j.prof->end(st, ca, FAM_COEF));
+    j.ell = 2;
+    return Status();
+}
+
+LayerParams job_layer_params(const Job &j)
+{
+    const Workspace &w = *j.ws;
+    LayerParams lp;
+    lp.src = w.f_src.as<u32>();
+    lp.dst = w.f_dst.as<u32>();
+    lp.time = w.f_time.as<u32>();
+    lp.cp_in = w.cp_in.as<u32>();
+    lp.cp_out = w.cp_out.as<u32>();
+    lp.seg_hi = w.seg_hi.as<u32>();
+    lp.x = w.x.as<u64>();
+    u64 *bufs[2] = {w.C0.as<u64>(), w.C1.as<u64>()};
+    lp.Cin = bufs[j.ell & 1];
+    lp.Cout = bufs[(j.ell + 1) & 1];
+    lp.partial = w.partial.as<u64>();
+    lp.m_f = j.mf;
+    lp.n_chunks = j.n_chunks;
+    lp.ky = j.ky;
+    lp.L = j.L;
+    lp.lane_groups = j.lane_groups;
+    lp.chunk = j.chunk;
+    lp.ell = j.ell;
+    lp.k = j.q.k;
+    lp.start = j.q.start;
+    lp.end = j.q.end;
+    lp.T = j.T;
+    return lp;
+}
+
+template <int T, bool TAB>
+static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const LayerParams *jobs,
+                             const u64 *prefix, u32 njobs, u64 teams)
+{
+    const int threads = 256;
+    const u64 teams_per_block = threads / T;
+    const unsigned blocks = (unsigned)((teams + teams_per_block - 1) / teams_per_block);
+    const size_t smem = TAB ? teams_per_block * 256 * 8 : 16;
+    static bool attr_set = false;
+    if (!attr_set) {
+        TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     160 * 1024));
+        TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     160 * 1024));
+        attr_set = true;
     }
-    TM_CUDA(cudaEventRecord(ev1, st));
+    if (!blocks) return Status();
+    if (njobs == 0) k_layer<T, TAB, false><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
+    else k_layer<T, TAB, true><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
+    return Status();
+}
+
+static Status launch_layer_class(cudaStream_t st, u32 T, const LayerParams &one, const LayerParams *jobs,
+                                 const u64 *prefix, u32 njobs, u64 teams)
+{
+    switch (T) {
+        case 2: return launch_layer_t<2, false>(st, one, jobs, prefix, njobs, teams);
+        case 4: return launch_layer_t<4, false>(st, one, jobs, prefix, njobs, teams);
+        case 8: return launch_layer_t<8, true>(st, one, jobs, prefix, njobs, teams);
+        case 16: return launch_layer_t<16, true>(st, one, jobs, prefix, njobs, teams);
+        default: return launch_layer_t<32, true>(st, one, jobs, prefix, njobs, teams);
+    }
+}
+
+static void count_layer(Profiler *prof, const Job &j)
+{
+    const u64 L = j.L, k = j.q.k;
+    prof->stats.layer_arc_lanes += j.mf * L;
+    if (j.ell < k) prof->stats.layer_cp_lanes += j.ncp * L;
+    // algorithmic bytes: per arc-lane one 8-byte read of the source state (x at
+    // layer 2, a checkpoint above); per checkpoint-lane one 8-byte write
+    const u64 writes = (j.ell < k) ? j.ncp : 0;
+    prof->stats.layer_bytes += (j.mf + writes) * L * 8;
+    prof->stats.layer_gf_muls += (j.mf + writes) * L;
+    if (j.T >= 8) prof->stats.layer_table_muls += j.mf * L;
+}
+
+Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &dev_params, void *host_params,
+                     size_t host_params_bytes, Profiler *prof)
+{
+    if (jobs.empty()) return Status();
+    if (jobs.size() == 1) {
+        const Job &j = *jobs[0];
+        cudaEvent_t la = nullptr;
+        TM_TRY(prof->begin(st, &la));
+        TM_TRY(launch_layer_class(st, j.T, job_layer_params(j), nullptr, nullptr, 0, j.n_chunks * j.lane_groups));
+        TM_CUDA(cudaGetLastError());
+        TM_TRY(prof->end(st, la, FAM_LAYER));
+        prof->stats.launches++;
+        prof->stats.layer_launches++;
+        count_layer(prof, j);
+        return Status();
+    }
+    // group by lane-width class; per class: job table + team prefix
+    const u32 classes[5] = {2, 4, 8, 16, 32};
+    size_t off = 0;
+    for (u32 T : classes) {
+        std::vector<const Job *> cls;
+        for (const Job *j : jobs)
+            if (j->T == T) cls.push_back(j);
+        if (cls.empty()) continue;
+        const size_t need = cls.size() * sizeof(LayerParams) + (cls.size() + 1) * sizeof(u64);
+        const size_t at = (off + 255) & ~(size_t)255;
+        if (at + need > host_params_bytes) return fail(TMOTIF_ERR_UNSUPPORTED, "too many jobs in one layer launch");
+        LayerParams *hp = (LayerParams *)((char *)host_params + at);
+        u64 *hpre = (u64 *)((char *)host_params + at + cls.size() * sizeof(LayerParams));
+        u64 teams = 0;
+        for (size_t i = 0; i < cls.size(); i++) {
+            hp[i] = job_layer_params(*cls[i]);
+            hpre[i] = teams;
+            teams += cls[i]->n_chunks * cls[i]->lane_groups;
+            count_layer(prof, *cls[i]);
+        }
+        hpre[cls.size()] = teams;
+        TM_TRY(dev_params.reserve(host_params_bytes));
+        char *dbase = (char *)dev_params.p + at;
+        TM_CUDA(cudaMemcpyAsync(dbase, (char *)host_params + at, need, cudaMemcpyHostToDevice, st));
+        cudaEvent_t la = nullptr;
+        TM_TRY(prof->begin(st, &la));
+        TM_TRY(launch_layer_class(st, T, hp[0], (const LayerParams *)dbase,
+                                  (const u64 *)(dbase + cls.size() * sizeof(LayerParams)), (u32)cls.size(), teams));
+        TM_CUDA(cudaGetLastError());
+        TM_TRY(prof->end(st, la, FAM_LAYER));
+        prof->stats.launches++;
+        prof->stats.layer_launches++;
+        off = at + need;
+    }
+    return Status();
+}
+
+Status job_readout_enqueue(Job &j)
+{
+    Workspace &w = *j.ws;
+    const unsigned slices = (unsigned)std::min<u64>(j.n_chunks, 128);
+    k_reduce_partials<<<slices, j.L, 0, j.st>>>(w.partial.as<u64>(), j.n_chunks, j.L, w.out.as<u64>());
+    j.prof->stats.launches++;
+    TM_CUDA(cudaGetLastError());
+    TM_CUDA(cudaMemcpyAsync((char *)w.host_pinned + 64, w.out.p, (u64)j.L * 8, cudaMemcpyDeviceToHost, j.st));
+    return Status();
+}
+
+void job_readout_finish(Job &j)
+{
+    const u64 *h_out = (const u64 *)((const char *)j.ws->host_pinned + 64);
+    const u64 cnt = std::min<u64>(j.L, j.q.p_end - j.p0);
+    for (u64 i = 0; i < cnt; i++) {
+        j.qsum ^= h_out[i];
+        if (j.r == 0) j.vals[j.p0 - j.q.p_begin + i] = h_out[i];
+    }
+    j.p0 += j.L;
+    if (j.p0 < j.q.p_end) return;  // next lane batch of this repeat
+    if (j.r == 0) j.sieve_sum = j.qsum;
+    if (j.qsum != 0) j.found = 1;
+    j.r++;
+    j.qsum = 0;
+    j.p0 = j.q.p_begin;
+    if (j.r >= j.q.repeats) j.done = true;
+}
+
+Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *found, u64 *sieve_sum,
+                    u64 *per_point, double *ms)
+{
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    TM_CUDA(cudaEventCreate(&ev0));
+    TM_CUDA(cudaEventCreate(&ev1));
+    TM_CUDA(cudaEventRecord(ev0, g.stream));
+    Job j;
+    j.g = &g;
+    j.q = q;
+    j.d_alive = d_alive;
+    j.ws = &g.ws;
+    j.st = g.stream;
+    j.prof = &g.prof;
+    TM_TRY(job_prep(j));
+    std::vector<Job *> one{&j};
+    DevBuf unused;
+    while (!j.done) {
+        TM_TRY(job_batch_begin(j));
+        for (; j.ell <= q.k; j.ell++) TM_TRY(launch_layers(j.st, one, unused, nullptr, 0, j.prof));
+        TM_TRY(job_readout_enqueue(j));
+        TM_CUDA(cudaStreamSynchronize(j.st));
+        job_readout_finish(j);
+    }
+    TM_CUDA(cudaEventRecord(ev1, g.stream));
     TM_CUDA(cudaEventSynchronize(ev1));
     float fms = 0;
     cudaEventElapsedTime(&fms, ev0, ev1);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     if (ms) *ms = fms;
-    if (per_point) std::memcpy(per_point, vals.data(), npts * sizeof(u64));
+    *found = j.found;
+    *sieve_sum = j.sieve_sum;
+    if (per_point && !j.vals.empty()) std::memcpy(per_point, j.vals.data(), j.vals.size() * sizeof(u64));
+    else if (per_point) std::memset(per_point, 0, (q.p_end - q.p_begin) * sizeof(u64));
     TM_TRY(g.prof.collect());
     return Status();
 }
@@ -606,11 +718,9 @@ __global__ void k_vflag_mask(u32 n, const uint8_t *alive, uint8_t *vflag)
     if (u < n) vflag[u] = alive[u] ? 1 : 0;
 }
 
-Status gather_arcs(Graph &g, const uint8_t *d_alive, u32 t_min, u32 t_max, std::vector<u32> *src,
-                   std::vector<u32> *dst, std::vector<u32> *time)
+Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const uint8_t *d_alive, u32 t_min,
+                   u32 t_max, std::vector<u32> *src, std::vector<u32> *dst, std::vector<u32> *time)
 {
-    Workspace &w = g.ws;
-    cudaStream_t st = g.stream;
     const u64 m = g.m;
     TM_TRY(w.vflag.reserve(std::max<u64>(g.n, 1)));
     TM_TRY(w.keep.reserve((m + 1) * 4));
@@ -618,10 +728,10 @@ Status gather_arcs(Graph &g, const uint8_t *d_alive, u32 t_min, u32 t_max, std::
     k_vflag_mask<<<grid_for(g.n, 256), 256, 0, st>>>(g.n, d_alive, w.vflag.as<uint8_t>());
     k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), t_min,
                                                  t_max, w.keep.as<u32>());
-    g.prof.stats.launches += 2;
+    prof.stats.launches += 2;
     TM_CUDA(cudaGetLastError());
     u32 *d_cnt = w.counters.as<u32>();
-    TM_TRY(exclusive_scan(g, w.keep.as<u32>(), m + 1, d_cnt));
+    TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt, (u64 *)&prof.stats.launches));
     u32 mf = 0;
     TM_CUDA(cudaMemcpyAsync(&mf, d_cnt, 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
@@ -634,7 +744,7 @@ Status gather_arcs(Graph &g, const uint8_t *d_alive, u32 t_min, u32 t_max, std::
     TM_TRY(w.f_time.reserve((u64)mf * 4));
     k_compact<<<grid_for(m, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.keep.as<u32>(), w.f_src.as<u32>(),
                                                 w.f_dst.as<u32>(), w.f_time.as<u32>());
-    g.prof.stats.launches++;
+    prof.stats.launches++;
     TM_CUDA(cudaGetLastError());
     TM_CUDA(cudaMemcpyAsync(src->data(), w.f_src.p, (u64)mf * 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaMemcpyAsync(dst->data(), w.f_dst.p, (u64)mf * 4, cudaMemcpyDeviceToHost, st));

@@ -175,6 +175,46 @@ def test_errors_are_reported(tm):
     assert_same(*both(tm, G, g, q.k, q.multiset, seed=3))
 
 
+def test_invalid_graphs_are_rejected(tm):
+    n = 4
+    src = np.array([0, 1, 2], np.uint32)
+    dst = np.array([1, 2, 3], np.uint32)
+    time = np.array([1, 2, 3], np.uint32)
+    color = np.zeros(n, np.uint32)
+    bad = [
+        (src, dst, np.array([1, 0, 3], np.uint32), color, 1, "timestamp"),
+        (src, np.array([1, 2, 9], np.uint32), time, color, 1, "vertex"),
+        (src, dst, time, np.array([0, 0, 5, 0], np.uint32), 2, "color"),
+    ]
+    for s, d, t, c, nc, word in bad:
+        with pytest.raises(tm.TmotifError) as e:
+            tm.tmotif_create_graph(n, s, d, t, c, nc)
+        assert e.value.code == 1 and word in str(e.value)
+    G = tm.tmotif_create_graph(n, src, dst, time, color, 1)  # the library is still usable
+    assert tm.tmotif_graph_get_info(G)["m_arcs"] == 3
+
+
+def test_device_graph_build_matches_canonical_set(tm):
+    # radix-sorted device build == the oracle's canonical arc set, directed and
+    # undirected, with duplicates, self-loops and wide ids/timestamps
+    rng = np.random.default_rng(5)
+    for n, m, tmax, und in ((50, 400, 9, False), (50, 400, 9, True), (3_000_000, 20000, 3_000_000, False),
+                            (70000, 50000, 1, True)):
+        src = rng.integers(0, n, m, dtype=np.uint32)
+        dst = rng.integers(0, n, m, dtype=np.uint32)
+        time = rng.integers(1, tmax + 1, m, dtype=np.uint32)
+        src[: m // 10] = dst[: m // 10]                      # self-loops
+        src[m // 10: m // 5] = src[m // 5: 3 * m // 10]      # duplicates
+        dst[m // 10: m // 5] = dst[m // 5: 3 * m // 10]
+        time[m // 10: m // 5] = time[m // 5: 3 * m // 10]
+        G = tm.tmotif_create_graph(n, src, dst, time, np.zeros(n, np.uint32), 1, undirected=und)
+        info = tm.tmotif_graph_get_info(G)
+        cs, cd, ct = oracle.canon(n, src, dst, time, und)
+        assert info["m_arcs"] == len(cs)
+        assert info["self_loops"] == int(np.sum(src == dst))
+        G.close()
+
+
 # ---------------------------------------------------------------------------
 # Extraction (Sec. 5.9): same deterministic procedure -> the same path
 # ---------------------------------------------------------------------------

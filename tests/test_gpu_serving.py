@@ -1,0 +1,121 @@
+"""Batching and serving: every result is the same alone and in the mix.
+
+The batch driver and the request server advance many decisions together in
+shared layer launches (different graphs, k, seeds, layers); GF(2^64)
+arithmetic is exact, so each sieve sum, decision and extracted path must equal
+the one tmotif_decide / tmotif_extract give for the same query alone.
+"""
+import random
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2001_07158_gb300 as tm
+
+    return tm
+
+
+def small_graphs(tm, count, seed):
+    rng = random.Random(seed)
+    out = []
+    for i in range(count):
+        n = rng.randint(50, 800)
+        g = synth.tour_graph(n, 8, 288, 12, seed=seed * 1000 + i)
+        G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors)
+        k = rng.randint(3, 7)
+        ms = [rng.randrange(12) for _ in range(k)]
+        out.append((G, {"k": k, "multiset": ms, "seed": rng.getrandbits(40), "t_max": rng.choice([0, 200])}))
+    return out
+
+
+def test_batch_equals_individual_decisions(tm):
+    items = small_graphs(tm, 60, seed=3)
+    graphs = [G for G, _ in items]
+    queries = [q for _, q in items]
+    res = tm.tmotif_decide_batch(graphs, queries)
+    for (G, q), r in zip(items, res):
+        alone = tm.tmotif_decide(G, **q)
+        assert r.found == alone.found and r.sieve_sum == alone.sieve_sum
+        assert np.array_equal(r.per_point, alone.per_point)
+
+
+def _serve_all(tm, srv, jobs, poll_sleep=0.0005, timeout=600):
+    tickets = []
+    for G, q, ex in jobs:
+        tickets.append(tm.tmotif_submit(srv, G, q["k"], q["multiset"], is_extract=ex, seed=q["seed"],
+                                        t_max=q.get("t_max", 0)))
+    results = [None] * len(jobs)
+    t0 = time.time()
+    while any(r is None for r in results):
+        for i, t in enumerate(tickets):
+            if results[i] is None:
+                r = tm.tmotif_poll(srv, t, jobs[i][1]["k"])
+                if r is not None:
+                    results[i] = r
+        assert time.time() - t0 < timeout
+        time.sleep(poll_sleep)
+    return results
+
+
+def test_server_mixed_requests_equal_alone(tm):
+    rng = random.Random(11)
+    g1, q1 = synth.config1_tiny()
+    g2 = synth.powerlaw_graph(20000, 200000, 500, 10, seed=19)
+    G1 = tm.tmotif_create_graph(g1.n, g1.src, g1.dst, g1.time, g1.color, g1.num_colors)
+    G2 = tm.tmotif_create_graph(g2.n, g2.src, g2.dst, g2.time, g2.color, g2.num_colors)
+    jobs = []
+    for i in range(40):
+        G, nc = (G1, 8) if rng.random() < 0.5 else (G2, 10)
+        k = rng.randint(3, 8)
+        q = {"k": k, "multiset": [rng.randrange(nc) for _ in range(k)], "seed": rng.getrandbits(40),
+             "t_max": rng.choice([0, 0, 300])}
+        jobs.append((G, q, rng.random() < 0.3 and k <= 6))
+    srv = tm.tmotif_server_create(0)
+    results = _serve_all(tm, srv, jobs)
+    srv.close()
+    for (G, q, ex), (dec, verts, times) in zip(jobs, results):
+        if ex:
+            f, v, t = tm.tmotif_extract(G, q["k"], q["multiset"], seed=q["seed"], t_max=q["t_max"])
+            assert dec.found == f
+            if f:
+                assert np.array_equal(verts, v) and np.array_equal(times, t)
+        else:
+            alone = tm.tmotif_decide(G, q["k"], q["multiset"], seed=q["seed"], t_max=q["t_max"])
+            assert dec.found == alone.found and dec.sieve_sum == alone.sieve_sum
+
+
+def test_server_budget_admission(tm):
+    g, q = synth.config1_tiny()
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors)
+    # a budget below one request's need is refused at submission
+    tiny = tm.tmotif_server_create(1 << 16)
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_submit(tiny, G, q.k, q.multiset, seed=1)
+    assert e.value.code == 7
+    tiny.close()
+    # a budget for about one request at a time still completes them all
+    one = tm.tmotif_server_create(24 << 20)
+    jobs = [(G, {"k": q.k, "multiset": q.multiset, "seed": s}, False) for s in range(1, 13)]
+    res = _serve_all(tm, one, jobs)
+    one.close()
+    for (G_, qq, _), (dec, _, _) in zip(jobs, res):
+        alone = tm.tmotif_decide(G, q.k, q.multiset, seed=qq["seed"])
+        assert dec.sieve_sum == alone.sieve_sum
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_poll(one if False else tm.tmotif_server_create(0), 12345, 4)
+    assert e.value.code == 6
