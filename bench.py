@@ -50,12 +50,16 @@ INT_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 #   holes, plus the reduction) -- used for the x-products;
 #   shared nibble table of a multiplier common to 64 lanes (build amortised)
 #   -- used for the y-products.
-OPS_PER_GF_MUL = 201.0
-OPS_PER_TABLE_MUL = 201.0
+# (probe instructions per product, less about 4 of loop overhead; see
+# profiles/gf_product_probe_instruction_counts.md)
+OPS_PER_GF_MUL = 207.7
+OPS_PER_TABLE_MUL = 127.7
 
 # DRAM traffic of one layer launch from an ncu capture, valid only for the
 # layer-kernel source it was taken on (source_sha() below, first 16 hex).
-LAYER_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+# (layer l = 4 launch of a cfg2 decision, full size, one-pass dram counters;
+# profiles/k_layer_cfg2_dram_full.md)
+LAYER_TRAFFIC = {"source_sha": "d9351bd1902886f9", "bytes_per_launch": 1137230080 + 399884544}
 
 
 def parse_args():
@@ -66,6 +70,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serving-requests", type=int, default=32)
     p.add_argument("--scale", type=float, default=1.0,
                    help="scale n and m of the workload (profiling captures of a smaller case)")
     return p.parse_args()
@@ -157,6 +163,86 @@ def cpu_baseline(g, q, points=None):
     dt = time.perf_counter() - t0
     return {"value": g.m * q.k * P / dt, "unit": UNIT, "cores": min(P, cores), "kind": "oracle",
             "sample": f"{P} of the {1 << q.k} sieve points of the same decision ({dt:.1f} s)"}
+
+
+def serving_benchmark(tm, stream, requests=128, load=0.7, seed=8):
+    """Config-5 serving: a stream of decide/extract requests (k in [3,10], 30 %
+    extract) against one resident power-law graph (n=2e6, m=2e7, 16 colours).
+
+    plain: requests one at a time, one query per launch sequence (FIFO);
+    their measured service times set the Poisson arrival rate at `load` of
+    the plain form's capacity and give its latencies by replaying the queue.
+    served: the same arrival schedule submitted to the continuous-batching
+    server (tmotif_submit / tmotif_poll), timed live.  Every served result
+    is checked against the plain one."""
+    import numpy as np
+
+    import synth
+
+    g, reqs = synth.config5_serving(requests=requests, seed=7)
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
+    warm = reqs[0][0]
+    tm.tmotif_decide(G, warm.k, warm.multiset, seed=warm.seed)
+    plain_res, service = [], []
+    for q, ex in reqs:
+        t0 = time.perf_counter()
+        if ex:
+            f, v, t = tm.tmotif_extract(G, q.k, q.multiset, seed=q.seed)
+            plain_res.append((f, None, v.tolist(), t.tolist()))
+        else:
+            d = tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed, per_point=False)
+            plain_res.append((d.found, d.sieve_sum, None, None))
+        service.append(time.perf_counter() - t0)
+    capacity = len(reqs) / sum(service)
+    rate = load * capacity
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    arrivals -= arrivals[0]
+    done_plain, t_free = [], 0.0
+    for a, s_ in zip(arrivals, service):
+        t_free = max(a, t_free) + s_
+        done_plain.append(t_free)
+    lat_plain = np.array(done_plain) - arrivals
+
+    srv = tm.tmotif_server_create(0)
+    tickets = [None] * len(reqs)
+    done_at = [None] * len(reqs)
+    served = [None] * len(reqs)
+    t_start = time.perf_counter()
+    nxt = 0
+    while any(d is None for d in done_at):
+        now = time.perf_counter() - t_start
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            q, ex = reqs[nxt]
+            tickets[nxt] = tm.tmotif_submit(srv, G, q.k, q.multiset, is_extract=ex, seed=q.seed)
+            nxt += 1
+        for i in range(nxt):
+            if done_at[i] is None:
+                r = tm.tmotif_poll(srv, tickets[i], reqs[i][0].k)
+                if r is not None:
+                    done_at[i] = time.perf_counter() - t_start
+                    served[i] = r
+        time.sleep(0.0002)
+    srv.close()
+    G.close()
+    lat_served = np.array(done_at) - arrivals
+    match = True
+    for (q, ex), pr, sr in zip(reqs, plain_res, served):
+        dec, v, t = sr
+        if ex:
+            match &= dec.found == pr[0] and (not dec.found or (v.tolist() == pr[2] and t.tolist() == pr[3]))
+        else:
+            match &= dec.found == pr[0] and dec.sieve_sum == pr[1]
+
+    def summary(lat, done):
+        span = max(done) - arrivals[0]
+        return {"queries_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+    return {"workload": "power-law n=2e6 m=2e7 t<=1000 16 colours; requests k~U{3..10}, 30% extract",
+            "requests": len(reqs), "arrival_rate_per_s": rate, "plain_capacity_per_s": capacity,
+            "plain": summary(lat_plain, done_plain), "served": summary(lat_served, done_at),
+            "results_match": bool(match)}
 
 
 def run_reference(args):
@@ -299,6 +385,8 @@ def run_ours(args):
             "gpu_launches": int(stats["launches"])}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, q)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_benchmark(tm, stream, requests=args.serving_requests)
     if rank == 0:
         print(json.dumps(line))
     G.close()
