@@ -38,6 +38,9 @@ extern "C" {
 
 #define TMOTIF_ANY 0xFFFFFFFFu
 #define TMOTIF_KMAX 20
+/* tmotif_query.flags: extract by halving self-reduction + DFS instead of by
+ * localisation (see tmotif_extract). */
+#define TMOTIF_EXTRACT_HALVING 1u
 
 enum {
     TMOTIF_OK = 0,
@@ -80,7 +83,8 @@ typedef struct {
  *                 independent evaluations, found = OR over them;
  *   point_begin, point_end  0,0 = all 2^k sieve points; otherwise only the
  *                 points [point_begin, point_end) are evaluated (sharding a
- *                 query across devices; combine the per-point sums by XOR). */
+ *                 query across devices; combine the per-point sums by XOR);
+ *   flags         0 or TMOTIF_EXTRACT_HALVING. */
 typedef struct {
     uint32_t k;
     const uint32_t *multiset;
@@ -89,6 +93,7 @@ typedef struct {
     uint64_t seed;
     uint32_t repeats;
     uint32_t point_begin, point_end;
+    uint32_t flags;
 } tmotif_query;
 
 /* Result of tmotif_decide.  per_point is caller-owned and optional (NULL or
@@ -142,15 +147,31 @@ int tmotif_graph_get_info(tmotif_graph_t g, tmotif_graph_info *info);
  * (k outside [2, TMOTIF_KMAX]), OOM, CUDA. */
 int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out);
 
-/* Extract one matching temporal path by self-reducibility (Sec. 5.9): verts
- * receives k vertex ids in path order and times the k-1 arc timestamps
- * (caller-owned).  found = 0 when no path exists.  The probe order is fixed:
- * candidates (vertices whose colour is in M) in ascending id; a block of
- * candidates is removed when the query stays YES without it, otherwise it is
- * halved; probe i uses seed mix(seed ^ i * 0xD1B54A32D192ED03); the survivors
- * go to a temporal DFS over start vertices in ascending id and arcs in
- * (time, dst) order.  Errors as tmotif_decide. */
+/* Extract one matching temporal path (Sec. 5.9): verts receives k vertex ids
+ * in path order and times the k-1 arc timestamps (caller-owned).  found = 0
+ * when no path exists.  Two procedures, both deterministic given the seed:
+ *   by localisation (default; the paper's second approach, with the sieve of
+ *     Sec. 5.7 localised to arcs): level 1 runs the sieve of the query with
+ *     per-arc sums at the last layer and takes the first arc (a1 -> b1, t1)
+ *     in (dst, time, src) order whose sum is nonzero -- a matching path ends
+ *     with it; level j asks for a path on the remaining colours ending at
+ *     a_{j-1} with all times below t_{j-1} and the later vertices masked, and
+ *     takes its first nonzero arc into a_{j-1}; k-1 sieves of shrinking size.
+ *     Level j uses seed mix(seed ^ j * 0xD1B54A32D192ED03);
+ *   by halving (flags = TMOTIF_EXTRACT_HALVING; the paper's first approach):
+ *     candidates (vertices whose colour is in M) in ascending id; a block of
+ *     candidates is removed when the query stays YES without it, otherwise it
+ *     is halved; probe i uses seed mix(seed ^ i * 0xD1B54A32D192ED03); the
+ *     survivors go to a temporal DFS over start vertices in ascending id and
+ *     arcs in (time, dst) order.
+ * Errors as tmotif_decide. */
 int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uint32_t *times, int *found);
+
+/* Vertex-localised sieve (Sec. 5.7): per_vertex[u] (caller-owned, n values)
+ * receives Q_u = sum over the 2^k points of P_{u,k,t}(z^A) -- nonzero exactly
+ * when (w.h.p.) a matching temporal path ends at u; out receives the whole
+ * decision (first repeat; repeats are ignored).  Errors as tmotif_decide. */
+int tmotif_localize(tmotif_graph_t g, const tmotif_query *q, uint64_t *per_vertex, tmotif_decision *out);
 
 /* Decide many (graph, query) pairs in one pass: every query runs its sieve
  * and the per-query phases of all of them share persistent launches (the

@@ -74,6 +74,10 @@ def _load():
             "or_brute_det": (i64, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32, u64, P]),
             "or_count_paths": (i64, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32, u64,
                                      P, P]),
+            "or_brute_arc_det": (i64, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32, u64, P]),
+            "or_arc_sums": (C.c_int, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32, u64, P]),
+            "or_extract_localized": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, u32, P, u32, u32, u32, u32,
+                                               u64, u32, P, P, P]),
             "or_decide": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u32, u32,
                                     u64, u32, u64, u64, P, P, P, C.c_int]),
             "or_extract": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, u32, P, u32, u32, u32, u32,
@@ -286,3 +290,42 @@ def extract(n, src, dst, time, color, num_colors, k, multiset, *, undirected=Fal
     if rc != 0:
         raise ValueError("oracle extract: invalid input")
     return bool(found.value), verts[:k].copy(), times[:k - 1].copy(), int(probes.value)
+
+
+def brute_arc_det(pb: Problem, qs: int):
+    """Per-arc sieve values from walk enumeration and the determinant identity:
+    for each arc, the sum over walks ending with it of prod(y) det(Z_walk)."""
+    out = np.zeros(max(pb.m, 1), np.uint64)
+    nw = _load().or_brute_arc_det(*pb._args(), qs, _ptr(out))
+    if nw < 0:
+        raise ValueError("oracle arc det failed")
+    return out[:pb.m], nw
+
+
+def arc_sums(pb: Problem, qs: int):
+    """Arc-localised sieve (Sec. 5.7 localisation, split by the last arc):
+    S_e = sum over points of the last-layer term of eq. gen-polynomial:3 that
+    arc e contributes.  Arcs of pb must be canonical (sorted by time)."""
+    out = np.zeros(max(pb.m, 1), np.uint64)
+    rc = _load().or_arc_sums(*pb._args(), qs, _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle arc sums failed")
+    return out[:pb.m]
+
+
+def extract_localized(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
+                      t_min=0, t_max=0, seed=1, repeats=1):
+    """Extraction by localisation: k-1 arc-localised sieves on shrinking
+    problems, the path built backwards from its last arc (Sec. 5.9, second
+    approach).  Returns (found, verts[k], times[k-1])."""
+    src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
+    verts = np.zeros(KMAX, np.uint32)
+    times = np.zeros(KMAX, np.uint32)
+    found = C.c_int(0)
+    rc = _load().or_extract_localized(n, len(src), _ptr(src), _ptr(dst), _ptr(time), int(bool(undirected)),
+                                      _ptr(color), num_colors, k, _ptr(ms), start, end, t_min, t_max, seed, repeats,
+                                      _ptr(verts), _ptr(times), C.byref(found))
+    if rc != 0:
+        raise ValueError("oracle localized extract: invalid input")
+    return bool(found.value), verts[:k].copy(), times[:k - 1].copy()
+

@@ -225,6 +225,9 @@ typedef struct {
     u32 t_min, t_max;     /* arc used iff t >= t_min and (t_max == 0 or t <= t_max) */
 } or_problem;
 
+static int or_check_query(u32 n, const u32 *color, u32 num_colors, u32 k, const u32 *multiset, u32 start,
+                          u32 end);
+
 static int or_arc_in_window(const or_problem *P, u32 t)
 {
     return t >= P->t_min && (P->t_max == 0 || t <= P->t_max);
@@ -388,6 +391,7 @@ typedef struct {
     const u32 *sb, *sc;
     u64 det_acc;
     u64 nwalks;
+    u64 *arc_acc;      /* det mode: per-arc sums of the walks ending with that arc */
 } or_enum;
 
 static u64 or_det(u64 *M, u32 k)
@@ -441,7 +445,16 @@ static void or_walk_done(or_enum *E)
                 Z[r * k + j] = z;
             }
         }
-        E->det_acc ^= or_gf_mul(yprod, or_det(Z, k));
+        u64 val = or_gf_mul(yprod, or_det(Z, k));
+        E->det_acc ^= val;
+        if (E->arc_acc) {
+            /* the walk's last arc: walk[k-2] -> walk[k-1] at time wt[k-2] */
+            for (u64 e = 0; e < P->m; e++)
+                if (P->src[e] == E->walk[k - 2] && P->dst[e] == E->walk[k - 1] && P->time[e] == E->wt[k - 2]) {
+                    E->arc_acc[e] ^= val;
+                    break;
+                }
+        }
     }
 }
 
@@ -516,6 +529,141 @@ i64 or_brute_det(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, 
     *q_out = E.det_acc;
     free(sb); free(sc);
     return (i64)E.nwalks;
+}
+
+/* Per-arc whole-sieve values from the determinant identity: for every arc e,
+ * the sum over temporal walks whose last arc is e of (prod y) det(Z_walk).
+ * arc_out has m entries (arcs as given).  Returns the number of walks. */
+i64 or_brute_arc_det(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32 *color,
+                     u32 num_colors, const uint8_t *alive, u32 k, const u32 *multiset, u32 start, u32 end,
+                     u32 t_min, u32 t_max, u64 qseed, u64 *arc_out)
+{
+    if (k < 2 || k > OR_KMAX) return -1;
+    or_problem P;
+    or_fill_problem(&P, n, m, src, dst, time, color, num_colors, alive, k, multiset, start, end, t_min, t_max);
+    u32 *sb = (u32 *)malloc(sizeof(u32) * (num_colors + 1));
+    u32 *sc = (u32 *)malloc(sizeof(u32) * (num_colors + 1));
+    if (or_slots(k, multiset, num_colors, sb, sc) != 0) { free(sb); free(sc); return -1; }
+    memset(arc_out, 0, sizeof(u64) * m);
+    or_enum E;
+    memset(&E, 0, sizeof(E));
+    E.P = &P; E.qs = qseed; E.det_mode = 1; E.sb = sb; E.sc = sc; E.arc_acc = arc_out;
+    or_walk_all(&E);
+    free(sb); free(sc);
+    return (i64)E.nwalks;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Arc-localised sieve: for each arc e = (a -> b, t) in the window whose head  */
+/* b may end the path, S_e = sum over all 2^k points A of the last-layer term */
+/* of eq. (gen-polynomial:3) that e contributes,                             */
+/*     x_b^A * y_{ba,k-1,t} * P_{a,k-1,t-1}(z^A),                            */
+/* i.e. the sieve of Lemma 5.5 applied to the walks whose last arc is e (the */
+/* vertex-localised sieve of Sec. 5.7, split further by the last arc).  The  */
+/* sum of S_e over the arcs into b is the vertex-localised value Q_b.        */
+/* Arcs must be canonical (sorted by time).  arc_out has m entries.          */
+/* ------------------------------------------------------------------------ */
+int or_arc_sums(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32 *color, u32 num_colors,
+                const uint8_t *alive, u32 k, const u32 *multiset, u32 start, u32 end, u32 t_min, u32 t_max,
+                u64 qseed, u64 *arc_out)
+{
+    if (k < 2 || k > OR_KMAX) return -1;
+    or_problem Pb;
+    or_fill_problem(&Pb, n, m, src, dst, time, color, num_colors, alive, k, multiset, start, end, t_min, t_max);
+    const or_problem *P = &Pb;
+    u32 *sb = (u32 *)malloc(sizeof(u32) * (num_colors + 1));
+    u32 *sc = (u32 *)malloc(sizeof(u32) * (num_colors + 1));
+    if (or_slots(k, multiset, num_colors, sb, sc) != 0) { free(sb); free(sc); return -1; }
+    u64 *x = (u64 *)malloc(sizeof(u64) * (n ? n : 1));
+    u64 *Pt = (u64 *)malloc(sizeof(u64) * (size_t)(k + 1) * (n ? n : 1));
+    memset(arc_out, 0, sizeof(u64) * m);
+    for (u64 point = 0; point < ((u64)1 << k); point++) {
+        or_all_x(P, qseed, sb, sc, point, x);
+        memset(Pt, 0, sizeof(u64) * (size_t)(k + 1) * n);
+        for (u32 u = 0; u < n; u++)
+            Pt[1 * (size_t)n + u] = (start == OR_ANY || start == u) ? x[u] : 0;
+        u64 e = 0;
+        while (e < m) {
+            u64 g0 = e;
+            u32 i = time[e];
+            while (e < m && time[e] == i) e++;
+            if (!or_arc_in_window(P, i)) continue;
+            for (u32 l = k; l >= 2; l--) {
+                for (u64 a = g0; a < e; a++) {
+                    u32 v = src[a], u = dst[a];
+                    u64 term = or_gf_mul(x[u], or_gf_mul(or_coef_y(qseed, v, u, i, l - 1), Pt[(size_t)(l - 1) * n + v]));
+                    Pt[(size_t)l * n + u] ^= term;
+                    if (l == k && (end == OR_ANY || end == u)) arc_out[a] ^= term;
+                }
+            }
+        }
+    }
+    free(x); free(Pt); free(sb); free(sc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Extraction by localisation (Sec. 5.9, second approach, with the sieve     */
+/* localised to arcs).  Level 1 runs the arc-localised sieve on the query   */
+/* and takes the first arc (a1 -> b1, t1) in (dst, time, src) order whose    */
+/* value is nonzero: some matching path ends with it.  Level j >= 2 asks for */
+/* a path on the remaining colours ending at a_{j-1} with every time below   */
+/* t_{j-1}, the vertices already chosen (after a_{j-1}) masked, and takes    */
+/* the first nonzero arc into a_{j-1}.  After k-1 levels the arcs chosen,    */
+/* read backwards, are the path.  Level j evaluates with seed                */
+/* or_probe_seed(seed, j); with repeats > 1 an arc counts when any repeat is */
+/* nonzero.                                                                  */
+/* ------------------------------------------------------------------------ */
+int or_extract_localized(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int undirected,
+                         const u32 *color, u32 num_colors, u32 k, const u32 *multiset, u32 start, u32 end,
+                         u32 t_min, u32 t_max, u64 seed, u32 repeats, u32 *verts, u32 *times, int *found)
+{
+    if (or_check_query(n, color, num_colors, k, multiset, start, end) != 0 || repeats < 1) return -1;
+    u64 cap = (undirected ? 2 * m : m) + 1;
+    u32 *cs = (u32 *)malloc(sizeof(u32) * cap), *cd = (u32 *)malloc(sizeof(u32) * cap), *ct = (u32 *)malloc(sizeof(u32) * cap);
+    i64 mc = or_canon(n, m, src, dst, time, undirected, cs, cd, ct);
+    if (mc < 0) { free(cs); free(cd); free(ct); return -1; }
+    u64 *sums = (u64 *)malloc(sizeof(u64) * (size_t)(mc + 1));
+    uint8_t *positive = (uint8_t *)malloc((size_t)mc + 1);
+    uint8_t *alive = (uint8_t *)malloc(n ? n : 1);
+    memset(alive, 1, n ? n : 1);
+    u32 ms[OR_KMAX];
+    for (u32 r = 0; r < k; r++) ms[r] = multiset[r];
+    u32 kk = k, cur_end = end, cur_tmax = t_max;
+    int rc = 0;
+    *found = 0;
+    for (u32 level = 1; kk >= 2; level++) {
+        memset(positive, 0, (size_t)mc + 1);
+        for (u32 r = 0; r < repeats && rc == 0; r++) {
+            if (or_arc_sums(n, (u64)mc, cs, cd, ct, color, num_colors, alive, kk, ms, start, cur_end, t_min,
+                            cur_tmax, or_query_seed(or_probe_seed(seed, level), r), sums) != 0) rc = -1;
+            for (i64 e = 0; e < mc; e++) if (sums[e]) positive[e] = 1;
+        }
+        if (rc) break;
+        /* first positive arc in (dst, time, src) order */
+        i64 best = -1;
+        for (i64 e = 0; e < mc; e++) {
+            if (!positive[e]) continue;
+            if (best < 0 || cd[e] < cd[best] || (cd[e] == cd[best] && (ct[e] < ct[best] ||
+                (ct[e] == ct[best] && cs[e] < cs[best])))) best = e;
+        }
+        if (best < 0) break;                       /* no path (or a false negative) */
+        u32 a = cs[best], b = cd[best], t = ct[best];
+        if (level == 1) verts[k - 1] = b;
+        verts[kk - 2] = a;
+        times[kk - 2] = t;
+        /* drop b's colour from the multiset; b is no longer available */
+        for (u32 r = 0; r < kk; r++)
+            if (ms[r] == color[b]) { ms[r] = ms[kk - 1]; break; }
+        kk--;
+        alive[b] = 0;
+        if (kk < 2) { *found = 1; break; }
+        if (t <= 1) break;
+        cur_end = a;
+        cur_tmax = t - 1;
+    }
+    free(sums); free(positive); free(alive); free(cs); free(cd); free(ct);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -20,6 +20,7 @@ import numpy as np
 
 TMOTIF_ANY = 0xFFFFFFFF
 TMOTIF_KMAX = 20
+TMOTIF_EXTRACT_HALVING = 1
 ERRORS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "NOT_FOUND", 7: "BUSY"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,7 +42,7 @@ class _GraphDesc(C.Structure):
 class _Query(C.Structure):
     _fields_ = [("k", C.c_uint32), ("multiset", C.c_void_p), ("start", C.c_uint32), ("end", C.c_uint32),
                 ("t_min", C.c_uint32), ("t_max", C.c_uint32), ("seed", C.c_uint64), ("repeats", C.c_uint32),
-                ("point_begin", C.c_uint32), ("point_end", C.c_uint32)]
+                ("point_begin", C.c_uint32), ("point_end", C.c_uint32), ("flags", C.c_uint32)]
 
 
 class _Decision(C.Structure):
@@ -71,6 +72,7 @@ def _load():
         "tmotif_graph_get_info": (C.c_int, [P, C.POINTER(_Info)]),
         "tmotif_decide": (C.c_int, [P, C.POINTER(_Query), C.POINTER(_Decision)]),
         "tmotif_extract": (C.c_int, [P, C.POINTER(_Query), P, P, C.POINTER(C.c_int)]),
+        "tmotif_localize": (C.c_int, [P, C.POINTER(_Query), P, C.POINTER(_Decision)]),
         "tmotif_decide_batch": (C.c_int, [P, P, C.c_uint32, P]),
         "tmotif_server_create": (C.c_int, [C.c_size_t, C.POINTER(P)]),
         "tmotif_submit": (C.c_int, [P, P, C.POINTER(_Query), C.c_int, C.POINTER(C.c_uint64)]),
@@ -162,9 +164,10 @@ def tmotif_graph_get_info(g: Graph) -> dict:
     return {f: getattr(info, f) for f, _ in _Info._fields_}
 
 
-def _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end):
+def _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end, flags=0):
     ms = _u32(multiset)
-    q = _Query(k, ms.ctypes.data, start, end, t_min, t_max, seed & (2**64 - 1), repeats, point_begin, point_end)
+    q = _Query(k, ms.ctypes.data, start, end, t_min, t_max, seed & (2**64 - 1), repeats, point_begin, point_end,
+               flags)
     return q, ms
 
 
@@ -179,13 +182,24 @@ def tmotif_decide(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_
 
 
 def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                   repeats=1):
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0)
+                   repeats=1, method="localized"):
+    """method: "localized" (default) or "halving" (TMOTIF_EXTRACT_HALVING)."""
+    flags = TMOTIF_EXTRACT_HALVING if method == "halving" else 0
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags)
     verts = np.zeros(k, np.uint32)
     times = np.zeros(max(k - 1, 1), np.uint32)
     found = C.c_int(0)
     _check(_lib.tmotif_extract(g.handle, C.byref(q), verts.ctypes.data, times.ctypes.data, C.byref(found)))
     return bool(found.value), verts, times[:k - 1]
+
+
+def tmotif_localize(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1):
+    """Vertex-localised sieve: (decision, per_vertex Q_u for every vertex)."""
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, 1, 0, 0)
+    pv = np.zeros(max(g.n, 1), np.uint64)
+    d = _Decision(0, 0, None, 0.0)
+    _check(_lib.tmotif_localize(g.handle, C.byref(q), pv.ctypes.data, C.byref(d)))
+    return Decision(bool(d.found), int(d.sieve_sum), None, float(d.ms)), pv[:g.n]
 
 
 def tmotif_decide_batch(graphs, queries):
@@ -289,8 +303,9 @@ def tmotif_server_create(hbm_budget_bytes: int) -> Server:
 
 
 def tmotif_submit(s: Server, g: Graph, k, multiset, *, is_extract=False, start=TMOTIF_ANY, end=TMOTIF_ANY,
-                  t_min=0, t_max=0, seed=1, repeats=1) -> int:
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0)
+                  t_min=0, t_max=0, seed=1, repeats=1, method="localized") -> int:
+    flags = TMOTIF_EXTRACT_HALVING if method == "halving" else 0
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags)
     t = C.c_uint64(0)
     _check(_lib.tmotif_submit(s.handle, g.handle, C.byref(q), int(bool(is_extract)), C.byref(t)))
     return int(t.value)

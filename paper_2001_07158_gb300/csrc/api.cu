@@ -95,14 +95,14 @@ void DevBuf::release()
 void Workspace::set_stream(cudaStream_t s)
 {
     DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &keep, &pos,
-                     &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial};
+                     &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list};
     for (DevBuf *b : all) b->stream = s;
 }
 
 void Workspace::release()
 {
     DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &keep, &pos,
-                     &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial};
+                     &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list};
     for (DevBuf *b : all) b->release();
     if (host_pinned) cudaFreeHost(host_pinned);
     host_pinned = nullptr;
@@ -112,7 +112,7 @@ void Workspace::release()
 size_t Workspace::bytes() const
 {
     const DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &keep, &pos,
-                           &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial};
+                           &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->bytes;
     return s;
@@ -231,7 +231,7 @@ Status build_graph(const tmotif_graph_desc *d, Graph *g)
     g->num_colors = d->num_colors;
     g->max_time = tmax;
     g->stream = (cudaStream_t)d->cuda_stream;
-    g->h_color.assign(d->color, d->color + d->n);
+    g->h_color = std::make_shared<std::vector<u32>>(d->color, d->color + d->n);
     std::vector<u32> hs(w), hd(w), ht(w);
     for (u64 e = 0; e < w; e++) { hs[e] = arcs[e].src; hd[e] = arcs[e].dst; ht[e] = arcs[e].time; }
     arcs.clear();
@@ -250,16 +250,23 @@ Status build_graph(const tmotif_graph_desc *d, Graph *g)
     return Status();
 }
 
-static void free_graph(Graph *g)
+void release_graph_arrays(Graph *g)
 {
     if (!g) return;
     dev_free(g->d_src, g->stream);
     dev_free(g->d_dst, g->stream);
     dev_free(g->d_time, g->stream);
     dev_free(g->d_color, g->stream);
+    g->d_src = g->d_dst = g->d_time = g->d_color = nullptr;
     g->ws.release();
     cudaStreamSynchronize(g->stream);
     g->prof.destroy();
+}
+
+static void free_graph(Graph *g)
+{
+    if (!g) return;
+    release_graph_arrays(g);
     delete static_cast<tmotif_graph *>(g);
 }
 
@@ -282,6 +289,7 @@ Status parse_query(const Graph &g, const tmotif_query *q, QuerySpec *out)
     out->t_max = q->t_max;
     out->seed = q->seed;
     out->repeats = q->repeats;
+    out->flags = q->flags;
     const u64 full = 1ull << q->k;
     if (q->point_begin == 0 && q->point_end == 0) {
         out->p_begin = 0;
@@ -375,9 +383,36 @@ int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uin
         if (!s.ok()) return s.code;
         if (qs.p_begin != 0 || qs.p_end != (1ull << qs.k))
             return fail(TMOTIF_ERR_INVALID, "extraction needs the full point range").code;
-        u32 probes = 0;
-        s = extract_path(*g, qs, verts, times, found, &probes);
+        if (qs.flags & TMOTIF_EXTRACT_HALVING) {
+            u32 probes = 0;
+            s = extract_path(*g, qs, verts, times, found, &probes);
+        } else {
+            s = extract_localized(*g, qs, verts, times, found);
+        }
         return s.code;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
+}
+
+int tmotif_localize(tmotif_graph_t g, const tmotif_query *q, uint64_t *per_vertex, tmotif_decision *out)
+{
+    if (!g || !per_vertex || !out) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    try {
+        QuerySpec qs;
+        Status s = parse_query(*g, q, &qs);
+        if (!s.ok()) return s.code;
+        if (qs.p_begin != 0 || qs.p_end != (1ull << qs.k))
+            return fail(TMOTIF_ERR_INVALID, "localisation needs the full point range").code;
+        int found = 0;
+        u64 sum = 0;
+        double ms = 0;
+        s = sieve_localize(*g, qs, (u64 *)per_vertex, &found, &sum, &ms);
+        if (!s.ok()) return s.code;
+        out->found = found;
+        out->sieve_sum = sum;
+        out->ms = ms;
+        return TMOTIF_OK;
     } catch (const std::bad_alloc &) {
         return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
     }

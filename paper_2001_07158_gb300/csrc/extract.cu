@@ -32,11 +32,13 @@ void ExtractState::init(const Graph &g, const QuerySpec &q)
     alive.assign(g.n, 0);
     R.clear();
     for (u32 u = 0; u < g.n; u++)
-        if (in_m[g.h_color[u]]) {
+        if (in_m[(*g.h_color)[u]]) {
             alive[u] = 1;
             R.push_back(u);
         }
     n_alive = R.size();
+    alive_at_build = n_alive;
+    sub.reset();
     stack.clear();
     stack.push_back({0, (u64)R.size()});
     probes = 0;
@@ -101,6 +103,26 @@ void ExtractState::result(bool yes)
     stage = SEARCHING;
 }
 
+Status ExtractState::maybe_compact(Graph &root, Workspace &w, cudaStream_t st)
+{
+    if (2 * n_alive > alive_at_build) return Status();
+    // the survivors so far, with the block under probe still in: a probe
+    // that answers NO puts it back
+    std::vector<uint8_t> keep = alive;
+    if (stage == PROBING)
+        for (u64 i = cur_lo; i < cur_hi; i++) keep[R[i]] = 1;
+    TM_TRY(w.alive.reserve(std::max<size_t>(keep.size(), 1)));
+    TM_CUDA(cudaMemcpyAsync(w.alive.p, keep.data(), keep.size(), cudaMemcpyHostToDevice, st));
+    std::unique_ptr<Graph, void (*)(Graph *)> next(new Graph(), [](Graph *g) {
+        release_graph_arrays(g);
+        delete g;
+    });
+    TM_TRY(make_subgraph(*current(root), w, st, w.alive.as<uint8_t>(), next.get()));
+    sub = std::move(next);
+    alive_at_build = n_alive;
+    return Status();
+}
+
 namespace {
 
 struct Dfs {
@@ -154,7 +176,7 @@ Status extract_finish(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, c
     TM_TRY(gather_arcs(g, w, st, prof, w.alive.as<uint8_t>(), q.t_min, q.t_max, &as, &ad, &at));
     Dfs D;
     D.q = &q;
-    D.color = &g.h_color;
+    D.color = g.h_color.get();
     std::vector<size_t> idx(as.size());
     std::iota(idx.begin(), idx.end(), 0);
     std::sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
@@ -169,7 +191,7 @@ Status extract_finish(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, c
     for (u32 u = 0; u < g.n && !D.found; u++) {
         if (!ex.alive[u]) continue;
         if (q.start != TMOTIF_ANY && u != q.start) continue;
-        auto nd = D.need.find(g.h_color[u]);
+        auto nd = D.need.find((*g.h_color)[u]);
         if (nd == D.need.end() || nd->second == 0) continue;
         nd->second--;
         D.onpath[u] = true;
@@ -196,19 +218,137 @@ Status extract_path(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *f
     QuerySpec pq;
     while (ex.next_probe(&pq)) {
         const uint8_t *mask = nullptr;
+        Graph *cur = &g;
         if (ex.stage == ExtractState::PROBING) {
-            TM_CUDA(cudaMemcpyAsync(g.ws.alive.p, ex.alive.data(), g.n, cudaMemcpyHostToDevice, g.stream));
-            mask = g.ws.alive.as<uint8_t>();
+            TM_TRY(ex.maybe_compact(g, g.ws, g.stream));
+            cur = ex.current(g);
+            TM_TRY(cur->ws.alive.reserve(std::max<u32>(g.n, 1)));
+            TM_CUDA(cudaMemcpyAsync(cur->ws.alive.p, ex.alive.data(), g.n, cudaMemcpyHostToDevice, cur->stream));
+            mask = cur->ws.alive.as<uint8_t>();
         }
         int yes = 0;
         u64 sum = 0;
         double ms = 0;
-        TM_TRY(sieve_decide(g, pq, mask, &yes, &sum, nullptr, &ms));
+        TM_TRY(sieve_decide(*cur, pq, mask, &yes, &sum, nullptr, &ms));
         ex.result(yes != 0);
         if (ex.stage == ExtractState::NOT_FOUND) return Status();
     }
     *probes = ex.probes;
-    return extract_finish(g, g.ws, g.stream, g.prof, ex, verts, times, found);
+    Graph *cur = ex.current(g);
+    return extract_finish(*cur, cur->ws, cur->stream, cur->prof, ex, verts, times, found);
+}
+
+// ---------------------------------------------------------------------------
+// Extraction by localisation (Sec. 5.9, second approach, localised to arcs).
+// Level 1: the arc-localised sieve of the query; its first nonzero arc
+// (a1 -> b1, t1) in (dst, time, src) order ends a matching path.  Level j:
+// a path on the remaining colours ending at a_{j-1}, every time below
+// t_{j-1}, the vertices chosen after a_{j-1} masked; its first nonzero arc
+// into a_{j-1} extends the path backwards.  Level j evaluates with seed
+// mix64(seed ^ j * TM_PROBE); with repeats > 1 an arc counts when any repeat
+// is nonzero, and the first such arc is taken.
+// ---------------------------------------------------------------------------
+void LocalizedExtract::init(const Graph &g, const QuerySpec &q)
+{
+    query = q;
+    color = g.h_color;
+    ms = q.multiset;
+    alive.assign(g.n, 1);
+    verts.assign(q.k, 0);
+    times.assign(q.k, 0);
+    kk = q.k;
+    level = 1;
+    rep = 0;
+    cur_end = q.end;
+    cur_tmax = q.t_max;
+    best = NONE;
+    done = false;
+    found = false;
+}
+
+bool LocalizedExtract::next(QuerySpec *sub, u32 *repeat, const std::vector<uint8_t> **mask)
+{
+    if (done) return false;
+    *sub = query;
+    sub->k = kk;
+    sub->multiset.assign(ms.begin(), ms.begin() + kk);
+    sub->end = cur_end;
+    sub->t_max = cur_tmax;
+    sub->seed = mix64(query.seed ^ ((u64)level * TM_PROBE));
+    sub->repeats = 1;
+    sub->p_begin = 0;
+    sub->p_end = 1ull << kk;
+    *repeat = rep;
+    *mask = level > 1 ? &alive : nullptr;
+    return true;
+}
+
+void LocalizedExtract::result(u32 idx, u32 a, u32 b, u32 t)
+{
+    if (idx != NONE && idx < best) {
+        best = idx;
+        ba = a;
+        bb = b;
+        bt = t;
+    }
+    if (++rep < query.repeats) return;  // more repeats of this level
+    rep = 0;
+    if (best == NONE) {  // no path (or a false negative)
+        done = true;
+        return;
+    }
+    if (level == 1) verts[query.k - 1] = bb;
+    verts[kk - 2] = ba;
+    times[kk - 2] = bt;
+    // bb's colour leaves the multiset and bb leaves the graph
+    const u32 cb = (*color)[bb];
+    for (u32 r = 0; r < kk; r++)
+        if (ms[r] == cb) {
+            ms[r] = ms[kk - 1];
+            break;
+        }
+    kk--;
+    alive[bb] = 0;
+    best = NONE;
+    if (kk < 2) {
+        found = true;
+        done = true;
+        return;
+    }
+    if (bt <= 1) {  // nothing can come before time 1
+        done = true;
+        return;
+    }
+    cur_end = ba;
+    cur_tmax = bt - 1;
+    level++;
+}
+
+Status extract_localized(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *found)
+{
+    *found = 0;
+    LocalizedExtract ex;
+    ex.init(g, q);
+    QuerySpec sub;
+    u32 rep = 0;
+    const std::vector<uint8_t> *mask = nullptr;
+    while (ex.next(&sub, &rep, &mask)) {
+        const uint8_t *d_mask = nullptr;
+        if (mask) {
+            TM_TRY(g.ws.alive.reserve(std::max<u32>(g.n, 1)));
+            TM_CUDA(cudaMemcpyAsync(g.ws.alive.p, mask->data(), g.n, cudaMemcpyHostToDevice, g.stream));
+            d_mask = g.ws.alive.as<uint8_t>();
+        }
+        u32 best = NONE, a = 0, b = 0, t = 0;
+        TM_TRY(sieve_first_arc(g, sub, rep, d_mask, &best, &a, &b, &t));
+        ex.result(best, a, b, t);
+    }
+    if (ex.found) {
+        for (u32 r = 0; r < q.k; r++) verts[r] = ex.verts[r];
+        for (u32 r = 0; r + 1 < q.k; r++) times[r] = ex.times[r];
+        *found = 1;
+    }
+    return Status();
 }
 
 }  // namespace tmo

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -89,6 +90,8 @@ struct Workspace {
     DevBuf out;                         // L u64: per-lane sieve sums
     DevBuf wtab;                        // k * L u64: W_d^A
     DevBuf alive;                       // n bytes: extraction probe mask
+    DevBuf act, act_list;               // n+1 u32 active flags/offsets, n u32 active vertices
+    DevBuf arc_sum;                     // m_f u64: arc-localised sieve sums
     DevBuf partial;                     // chunks * L u64: per-chunk sieve sums
     void *host_pinned = nullptr;        // small pinned readback area
     size_t host_pinned_bytes = 0;
@@ -107,7 +110,7 @@ struct Graph {
     // resident arcs sorted by (dst, time, src)
     u32 *d_src = nullptr, *d_dst = nullptr, *d_time = nullptr;
     u32 *d_color = nullptr;
-    std::vector<u32> h_color;           // host copy for extraction bookkeeping
+    std::shared_ptr<std::vector<u32>> h_color;  // host copy for extraction bookkeeping
     std::vector<u64> pair_hist;         // arcs per (colour(src), colour(dst)), if few colours
     Workspace ws;
     Profiler prof;
@@ -122,6 +125,7 @@ struct QuerySpec {
     u64 seed = 0;
     u32 repeats = 1;
     u64 p_begin = 0, p_end = 0;         // resolved point range
+    u32 flags = 0;
 };
 
 Status parse_query(const Graph &g, const tmotif_query *q, QuerySpec *out);
@@ -134,6 +138,7 @@ struct LayerParams {
     const u64 *Cin;
     u64 *Cout;
     u64 *partial;   // last layer: per (chunk, lane) sums
+    u64 *arc_sum;   // last layer, arc localisation: per filtered arc, XOR over lanes (or null)
     u64 m_f;
     u64 n_chunks;
     u64 ky;
@@ -152,7 +157,7 @@ struct Job {
     cudaStream_t st = nullptr;
     Profiler *prof = nullptr;
     // sizes known after prep
-    u64 mf = 0, ncp = 0;
+    u64 mf = 0, ncp = 0, n_act = 0;
     u32 L = 0, T = 0, lane_groups = 0, chunk = 128;
     u64 n_chunks = 0;
     // progress
@@ -165,6 +170,10 @@ struct Job {
     bool done = false;
     std::vector<u64> vals;  // repeat-0 per-point sums on [p_begin, p_end)
     u64 ky = 0;           // y key of the current repeat
+    bool multi_slot = false;  // readouts go to per-batch host slots (one sync per decision)
+    bool localize = false;    // accumulate arc-localised sums at the last layer
+    u32 rep_offset = 0;       // repeat index of the first repeat this job evaluates
+    u64 batch_seq = 0;    // batch number across repeats (slot index)
 };
 
 // Job steps.  prep: filter, checkpoints, buffer sizing (synchronises the
@@ -196,6 +205,13 @@ Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *f
 Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const uint8_t *d_alive, u32 t_min,
                    u32 t_max, std::vector<u32> *src, std::vector<u32> *dst, std::vector<u32> *time);
 
+// Device arrays of a graph (arcs, colours, workspace, profiler events).
+void release_graph_arrays(Graph *g);
+// The arcs of g whose endpoints both have alive[u] != 0 (device mask), as a
+// new resident graph with the same vertex ids (extraction's shrinking
+// subgraph).  Uses workspace w on stream st.
+Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_t *d_alive, Graph *sub);
+
 // Extraction (Sec. 5.9) as a state machine: next_probe() gives the next
 // decision to run (the first one is the query itself, the rest mask the
 // vertices with alive[u] == 0), result() takes its answer.  When
@@ -211,6 +227,13 @@ struct ExtractState {
     u64 n_alive = 0, cur_lo = 0, cur_hi = 0, cur_cnt = 0;
     u32 probes = 0;
     Stage stage = FIRST;
+    // Probes run on a compacted copy of the arcs among alive vertices, rebuilt
+    // whenever the alive candidates halve (results are unchanged: masked
+    // vertices contribute nothing).
+    std::unique_ptr<Graph, void (*)(Graph *)> sub{nullptr, release_graph_arrays};
+    u64 alive_at_build = 0;
+    Graph *current(Graph &root) { return sub ? sub.get() : &root; }
+    Status maybe_compact(Graph &root, Workspace &w, cudaStream_t st);
     void init(const Graph &g, const QuerySpec &q);
     bool next_probe(QuerySpec *pq);
     void result(bool yes);
@@ -219,6 +242,38 @@ struct ExtractState {
 Status extract_finish(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const ExtractState &ex, u32 *verts,
                       u32 *times, int *found);
 Status extract_path(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *found, u32 *probes);
+
+// The first filtered arc (lowest index) whose arc-localised sum in the job's
+// workspace is nonzero; *best = NONE when there is none.  Synchronises.
+Status job_first_arc(Job &j, u32 *best, u32 *a, u32 *b, u32 *t);
+
+// Extraction by localisation as a state machine: next() gives the next
+// arc-localised decision to run (its query, repeat and vertex mask),
+// result() takes the first nonzero arc it found (best = NONE if none).
+struct LocalizedExtract {
+    QuerySpec query;
+    std::shared_ptr<std::vector<u32>> color;
+    std::vector<u32> ms;
+    std::vector<uint8_t> alive;
+    std::vector<u32> verts, times;
+    u32 kk = 0, level = 0, rep = 0, cur_end = TMOTIF_ANY, cur_tmax = 0;
+    u32 best = 0xFFFFFFFFu, ba = 0, bb = 0, bt = 0;
+    bool done = false, found = false;
+    void init(const Graph &g, const QuerySpec &q);
+    bool next(QuerySpec *sub, u32 *repeat, const std::vector<uint8_t> **mask);
+    void result(u32 idx, u32 a, u32 b, u32 t);
+};
+
+// Arc-localised sieve for one repeat: the job's arc sums, then the first
+// filtered arc (lowest index, i.e. first in (dst, time, src) order) whose sum
+// is nonzero; *best = NONE when there is none, else (*a -> *b, *t).
+Status sieve_first_arc(Graph &g, const QuerySpec &q, u32 repeat, const uint8_t *d_alive, u32 *best, u32 *a, u32 *b,
+                       u32 *t);
+// Per-vertex localised values Q_u (Sec. 5.7) for every vertex: XOR over the
+// arc sums of the arcs into u.  per_vertex (host) has n entries.
+Status sieve_localize(Graph &g, const QuerySpec &q, u64 *per_vertex, int *found, u64 *sieve_sum, double *ms);
+// Extraction by localisation (k-1 arc-localised sieves, path built backwards).
+Status extract_localized(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *found);
 
 Status build_graph(const tmotif_graph_desc *d, Graph *g);
 // Device build; *done = false (and no error) when the packed arc key would not

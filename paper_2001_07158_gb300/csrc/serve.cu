@@ -69,15 +69,15 @@ public:
     Scheduler(cudaStream_t st, size_t budget) : st_(st), budget_(budget) {}
     ~Scheduler()
     {
-        dev_params_.release();
+        for (auto &d : dev_params_) d.release();
         if (host_params_) cudaFreeHost(host_params_);
         prof.destroy();
     }
 
     Status init()
     {
-        TM_CUDA(cudaMallocHost(&host_params_, kParamsBytes));
-        dev_params_.stream = st_;
+        TM_CUDA(cudaMallocHost(&host_params_, kSlotBytes * kMaxLayersPerSync));
+        for (auto &d : dev_params_) d.stream = st_;
         return Status();
     }
 
@@ -122,26 +122,35 @@ public:
         return Status();
     }
 
-    // One step: coefficients for jobs starting a lane batch, one shared layer
-    // launch per lane-width class, readouts of finished batches, one sync.
+    // Advance every active job layer by layer (coefficients for jobs starting
+    // a lane batch, one shared layer launch per lane-width class per layer)
+    // until some job finishes its lane batch; then read out, sync once, and
+    // retire finished jobs.  At most kMaxLayersPerSync layers are enqueued
+    // before the host looks again (to admit new work).
     Status step(std::vector<std::unique_ptr<SJob>> *done)
     {
         if (active_.empty()) return Status();
-        std::vector<Job *> layer;
-        for (auto &sj : active_) {
-            if (sj->state == J_BEGIN) {
-                TM_TRY(job_batch_begin(sj->job));
-                sj->state = J_LAYER;
+        for (int rounds = 0; rounds < kMaxLayersPerSync; rounds++) {
+            std::vector<Job *> layer;
+            for (auto &sj : active_) {
+                if (sj->state == J_BEGIN) {
+                    TM_TRY(job_batch_begin(sj->job));
+                    sj->state = J_LAYER;
+                }
+                layer.push_back(&sj->job);
             }
-            layer.push_back(&sj->job);
-        }
-        TM_TRY(launch_layers(st_, layer, dev_params_, host_params_, kParamsBytes, &prof));
-        for (auto &sj : active_) {
-            sj->job.ell++;
-            if (sj->job.ell > sj->job.q.k) {
-                TM_TRY(job_readout_enqueue(sj->job));
-                sj->state = J_READOUT;
+            TM_TRY(launch_layers(st_, layer, dev_params_[rounds], (char *)host_params_ + rounds * kSlotBytes,
+                                 kSlotBytes, &prof));
+            bool readout = false;
+            for (auto &sj : active_) {
+                sj->job.ell++;
+                if (sj->job.ell > sj->job.q.k) {
+                    TM_TRY(job_readout_enqueue(sj->job));
+                    sj->state = J_READOUT;
+                    readout = true;
+                }
             }
+            if (readout) break;
         }
         TM_CUDA(cudaStreamSynchronize(st_));
         TM_TRY(prof.collect());
@@ -167,12 +176,14 @@ public:
     u64 steps = 0;
 
 private:
-    static const size_t kParamsBytes = 4 << 20;
+    // one job-table slot (host pinned + device) per layer round between syncs
+    static const int kMaxLayersPerSync = 8;
+    static const size_t kSlotBytes = 1 << 20;
     cudaStream_t st_;
     size_t budget_;
     size_t in_use_ = 0;
     std::vector<std::unique_ptr<SJob>> active_;
-    DevBuf dev_params_;
+    DevBuf dev_params_[kMaxLayersPerSync];
     void *host_params_ = nullptr;
 };
 
@@ -264,7 +275,9 @@ struct Request {
     Graph *g = nullptr;
     QuerySpec q;
     bool is_extract = false;
-    ExtractState ex;
+    bool halving = false;
+    ExtractState ex;         // halving procedure
+    LocalizedExtract lex;    // localisation procedure
     Clock::time_point t_submit;
     bool done = false;
     int code = TMOTIF_OK;
@@ -314,15 +327,35 @@ struct tmotif_server {
             *out = std::move(sj);
             return true;
         }
+        if (!r->halving) {
+            QuerySpec sub;
+            u32 rep = 0;
+            const std::vector<uint8_t> *mask = nullptr;
+            if (!r->lex.next(&sub, &rep, &mask)) return false;
+            sj->job.q = sub;
+            sj->job.localize = true;
+            sj->job.rep_offset = rep;
+            if (mask) {
+                Status s = sched->set_mask(*sj, *mask);
+                if (!s.ok()) {
+                    complete(r, s);
+                    return false;
+                }
+            }
+            *out = std::move(sj);
+            return true;
+        }
         QuerySpec pq;
         if (!r->ex.next_probe(&pq)) return false;
         sj->job.q = pq;
         if (r->ex.stage == ExtractState::PROBING) {
-            Status s = sched->set_mask(*sj, r->ex.alive);
+            Status s = r->ex.maybe_compact(*r->g, finish_ws, st);
+            if (s.ok()) s = sched->set_mask(*sj, r->ex.alive);
             if (!s.ok()) {
                 complete(r, s);
                 return false;
             }
+            sj->job.g = r->ex.current(*r->g);
         }
         *out = std::move(sj);
         return true;
@@ -332,10 +365,19 @@ struct tmotif_server {
     {
         r->verts.assign(r->q.k, 0);
         r->times.assign(r->q.k, 0);
+        if (!r->halving) {
+            r->found = r->lex.found ? 1 : 0;
+            if (r->lex.found) {
+                r->verts = r->lex.verts;
+                r->times = r->lex.times;
+            }
+            complete(r, Status());
+            return;
+        }
         Status s;
         if (r->ex.stage == ExtractState::SHRUNK)
-            s = extract_finish(*r->g, finish_ws, st, sched->prof, r->ex, r->verts.data(), r->times.data(),
-                               &r->found);
+            s = extract_finish(*r->ex.current(*r->g), finish_ws, st, sched->prof, r->ex, r->verts.data(),
+                               r->times.data(), &r->found);
         else
             r->found = 0;
         complete(r, s);
@@ -398,10 +440,24 @@ struct tmotif_server {
                     complete(r, Status());
                     continue;
                 }
-                r->ex.result(sj->job.found != 0);
-                if (r->ex.stage == ExtractState::NOT_FOUND) {
-                    finish_extract(r);
-                    continue;
+                if (!r->halving) {
+                    u32 best = NONE, a = 0, b = 0, t = 0;
+                    Status s = sj->job.done && sj->job.mf == 0 ? Status() : job_first_arc(sj->job, &best, &a, &b, &t);
+                    if (!s.ok()) {
+                        complete(r, s);
+                        continue;
+                    }
+                    r->lex.result(best, a, b, t);
+                    if (r->lex.done) {
+                        finish_extract(r);
+                        continue;
+                    }
+                } else {
+                    r->ex.result(sj->job.found != 0);
+                    if (r->ex.stage == ExtractState::NOT_FOUND) {
+                        finish_extract(r);
+                        continue;
+                    }
                 }
                 // next probe joins the front of the admission queue (the request keeps its turn)
                 std::unique_ptr<SJob> nj;
@@ -450,7 +506,9 @@ extern "C" int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_q
             return fail(TMOTIF_ERR_BUSY, "request needs more device memory than the server budget").code;
         r->g = g;
         r->is_extract = is_extract != 0;
-        if (r->is_extract) r->ex.init(*g, r->q);
+        r->halving = (r->q.flags & TMOTIF_EXTRACT_HALVING) != 0;
+        if (r->is_extract && r->halving) r->ex.init(*g, r->q);
+        if (r->is_extract && !r->halving) r->lex.init(*g, r->q);
         r->t_submit = Clock::now();
         std::lock_guard<std::mutex> lock(s->mu);
         r->ticket = s->next_ticket++;

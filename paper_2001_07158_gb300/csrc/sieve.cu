@@ -34,13 +34,25 @@ static Status exclusive_scan(Graph &g, u32 *a, u64 N, u32 *d_total)
 // ---------------------------------------------------------------------------
 // Per-query preparation
 // ---------------------------------------------------------------------------
-__global__ void k_vflag(u32 n, const u32 *color, const u32 *slot_count, const uint8_t *alive, uint8_t *vflag)
+// vflag[u] = 1 for vertices with a query colour (and alive); act[u] the same
+// as u32 flags (n+1 entries, act[n] = 0) for the active-vertex scan.
+__global__ void k_vflag(u32 n, const u32 *color, const u32 *slot_count, const uint8_t *alive, uint8_t *vflag,
+                        u32 *act)
 {
     u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= n) return;
+    if (u > n) return;
+    if (u == n) { act[n] = 0; return; }
     bool f = slot_count[color[u]] > 0;
     if (alive) f = f && alive[u];
     vflag[u] = f ? 1 : 0;
+    act[u] = f ? 1u : 0u;
+}
+
+// act[] holds exclusive offsets: list[act[u]] = u for active u.
+__global__ void k_active_list(u32 n, const u32 *act, u32 *list)
+{
+    u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n && act[u + 1] != act[u]) list[act[u]] = (u32)u;
 }
 
 __global__ void k_keep(u64 m, const u32 *src, const u32 *dst, const u32 *time, const uint8_t *vflag, u32 t_min,
@@ -128,19 +140,30 @@ __global__ void k_wtab(u32 k, u32 L, u64 p0, QueryKeys keys, u64 *wtab)
     wtab[i] = s;
 }
 
-// x_u^A = sum_{d in S_c(u)} v_{u,d} W_d^A, for vertices that carry a query colour.
-__global__ void k_coef(u32 n, u32 L, const uint8_t *vflag, const u32 *color, const u32 *slot_begin,
-                       const u32 *slot_count, QueryKeys keys, const u64 *wtab, u64 *x)
+// x_u^A = sum_{d in S_c(u)} v_{u,d} W_d^A for the active vertices: one warp
+// per vertex; v_{u,d} is common to all lanes, so the warp builds its nibble
+// table once per slot and each lane's product is 16 table loads.
+__global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L, const u32 *color,
+                                              const u32 *slot_begin, const u32 *slot_count, QueryKeys keys,
+                                              const u64 *wtab, u64 *x)
 {
-    u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (u64)n * L) return;
-    u32 u = (u32)(i / L), lane = (u32)(i % L);
-    if (!vflag[u]) return;
-    u32 c = color[u];
-    u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
-    u64 s = 0;
-    for (u32 d = d0; d < d1; d++) s ^= gf_mul(coef_v(keys, u, d), wtab[(u64)d * L + lane]);
-    x[i] = s;
+    __shared__ __align__(128) u64 tabs[8][256];
+    u64 *tab = tabs[threadIdx.x >> 5];
+    const int tt = threadIdx.x & 31;
+    const u64 v = (u64)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (v >= n_act) return;  // whole warp leaves together
+    const u32 u = list[v], c = color[u];
+    const u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
+    u64 s0 = 0, s1 = 0;
+    for (u32 d = d0; d < d1; d++) {
+        __syncwarp();
+        gf_table_build(tab, coef_v(keys, u, d), tt, 32);
+        __syncwarp();
+        if ((u32)tt < L) s0 ^= gf_table_mul(tab, wtab[(u64)d * L + tt]);
+        if ((u32)tt + 32 < L) s1 ^= gf_table_mul(tab, wtab[(u64)d * L + tt + 32]);
+    }
+    if ((u32)tt < L) x[(u64)u * L + tt] = s0;
+    if ((u32)tt + 32 < L) x[(u64)u * L + tt + 32] = s1;
 }
 
 // ---------------------------------------------------------------------------
@@ -217,15 +240,25 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
                 have = true;
             }
             if (have) {  // uniform across the team
+                u64 h0, h1;
                 if (TAB) {
                     __syncwarp(team_mask);  // earlier lookups are done
                     gf_table_build(tab, yj, tt, T);
                     __syncwarp(team_mask);  // table complete
-                    acc0 ^= gf_table_mul(tab, in.x);
-                    acc1 ^= gf_table_mul(tab, in.y);
+                    h0 = gf_table_mul(tab, in.x);
+                    h1 = gf_table_mul(tab, in.y);
                 } else {
-                    acc0 ^= gf_mul(yj, in.x);
-                    acc1 ^= gf_mul(yj, in.y);
+                    h0 = gf_mul(yj, in.x);
+                    h1 = gf_mul(yj, in.y);
+                }
+                acc0 ^= h0;
+                acc1 ^= h1;
+                if (last && p.arc_sum && (p.end == NONE || dj == p.end)) {
+                    // this arc's last-layer term, summed over the lanes
+                    u64 v = gf_mul(xc0, h0) ^ gf_mul(xc1, h1);
+#pragma unroll
+                    for (int o = T / 2; o > 0; o >>= 1) v ^= __shfl_xor_sync(team_mask, v, o, T);
+                    if (tt == 0) p.arc_sum[base + j] ^= v;
                 }
             }
             if (coj != NONE) {
@@ -375,13 +408,14 @@ static const u32 LANES_MAX = 64;  // lanes per batch (one warp owns 64 lanes)
 static const u32 CHUNK = 128;     // arcs per team chunk (whole in-segments)
 static const size_t PIN_BYTES = 64 + LANES_MAX * 8;
 
-static Status ensure_pinned(Workspace &w)
+static Status ensure_pinned(Workspace &w, size_t bytes = PIN_BYTES)
 {
-    if (w.host_pinned_bytes >= PIN_BYTES) return Status();
+    if (w.host_pinned_bytes >= bytes) return Status();
     if (w.host_pinned) cudaFreeHost(w.host_pinned);
     w.host_pinned = nullptr;
-    TM_CUDA(cudaMallocHost(&w.host_pinned, PIN_BYTES));
-    w.host_pinned_bytes = PIN_BYTES;
+    w.host_pinned_bytes = 0;
+    TM_CUDA(cudaMallocHost(&w.host_pinned, bytes));
+    w.host_pinned_bytes = bytes;
     return Status();
 }
 
@@ -420,16 +454,23 @@ Status job_prep(Job &j)
     cudaEvent_t pa = nullptr;
     TM_TRY(j.prof->begin(st, &pa));
     TM_TRY(w.vflag.reserve(std::max<u64>(n, 1)));
+    TM_TRY(w.act.reserve(((u64)n + 1) * 4));
+    TM_TRY(w.act_list.reserve(std::max<u64>(n, 1) * 4));
     TM_TRY(w.keep.reserve((m + 1) * 4));
-    k_vflag<<<grid_for(n, 256), 256, 0, st>>>(n, g.d_color, w.slot_count.as<u32>(), j.d_alive, w.vflag.as<uint8_t>());
+    k_vflag<<<grid_for((u64)n + 1, 256), 256, 0, st>>>(n, g.d_color, w.slot_count.as<u32>(), j.d_alive,
+                                                       w.vflag.as<uint8_t>(), w.act.as<u32>());
     k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), q.t_min,
                                                  q.t_max, w.keep.as<u32>());
     *launches += 2;
     TM_CUDA(cudaGetLastError());
     TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt + 0, launches));
-    TM_CUDA(cudaMemcpyAsync(h_cnt, d_cnt, 4, cudaMemcpyDeviceToHost, st));
+    TM_TRY(exclusive_scan_on(st, w.block_sums, w.act.as<u32>(), (u64)n + 1, d_cnt + 2, launches));
+    k_active_list<<<grid_for(n, 256), 256, 0, st>>>(n, w.act.as<u32>(), w.act_list.as<u32>());
+    *launches += 1;
+    TM_CUDA(cudaMemcpyAsync(h_cnt, d_cnt, 12, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
     j.mf = h_cnt[0];
+    j.n_act = h_cnt[2];
     j.ncp = 0;
     if (j.mf > 0) {
         const u64 mf = j.mf;
@@ -486,6 +527,10 @@ Status job_prep(Job &j)
     TM_TRY(w.out.reserve(L * 8));
     TM_TRY(w.wtab.reserve((u64)q.k * L * 8));
     TM_TRY(w.partial.reserve(j.n_chunks * L * 8));
+    if (j.localize) {
+        TM_TRY(w.arc_sum.reserve(j.mf * 8));
+        TM_CUDA(cudaMemsetAsync(w.arc_sum.p, 0, j.mf * 8, st));
+    }
     return Status();
 }
 
@@ -494,15 +539,16 @@ Status job_batch_begin(Job &j)
     Graph &g = *j.g;
     Workspace &w = *j.ws;
     const cudaStream_t st = j.st;
-    const u32 L = j.L, k = j.q.k, n = g.n;
-    const QueryKeys keys = make_keys(mix64(j.q.seed + (u64)(j.r + 1) * TM_GOLDEN));
+    const u32 L = j.L, k = j.q.k;
+    const QueryKeys keys = make_keys(mix64(j.q.seed + (u64)(j.r + j.rep_offset + 1) * TM_GOLDEN));
     j.ky = keys.ky;
     cudaEvent_t ca = nullptr;
     TM_TRY(j.prof->begin(st, &ca));
     k_wtab<<<grid_for((u64)k * L, 128), 128, 0, st>>>(k, L, j.p0, keys, w.wtab.as<u64>());
-    k_coef<<<grid_for((u64)n * L, 256), 256, 0, st>>>(n, L, w.vflag.as<uint8_t>(), g.d_color,
-                                                      w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
-                                                      w.wtab.as<u64>(), w.x.as<u64>());
+    if (j.n_act)
+        k_coef<<<(unsigned)((j.n_act + 7) / 8), 256, 0, st>>>((u32)j.n_act, w.act_list.as<u32>(), L, g.d_color,
+                                                               w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
+                                                               w.wtab.as<u64>(), w.x.as<u64>());
     j.prof->stats.launches += 2;
     TM_CUDA(cudaGetLastError());
     TM_CUDA(cudaMemsetAsync(w.out.p, 0, L * 8, st));
@@ -526,6 +572,7 @@ LayerParams job_layer_params(const Job &j)
     lp.Cin = bufs[j.ell & 1];
     lp.Cout = bufs[(j.ell + 1) & 1];
     lp.partial = w.partial.as<u64>();
+    lp.arc_sum = j.localize ? w.arc_sum.as<u64>() : nullptr;
     lp.m_f = j.mf;
     lp.n_chunks = j.n_chunks;
     lp.ky = j.ky;
@@ -647,13 +694,16 @@ Status job_readout_enqueue(Job &j)
     k_reduce_partials<<<slices, j.L, 0, j.st>>>(w.partial.as<u64>(), j.n_chunks, j.L, w.out.as<u64>());
     j.prof->stats.launches++;
     TM_CUDA(cudaGetLastError());
-    TM_CUDA(cudaMemcpyAsync((char *)w.host_pinned + 64, w.out.p, (u64)j.L * 8, cudaMemcpyDeviceToHost, j.st));
+    const u64 slot = j.multi_slot ? j.batch_seq : 0;
+    TM_CUDA(cudaMemcpyAsync((char *)w.host_pinned + 64 + slot * j.L * 8, w.out.p, (u64)j.L * 8,
+                            cudaMemcpyDeviceToHost, j.st));
     return Status();
 }
 
 void job_readout_finish(Job &j)
 {
-    const u64 *h_out = (const u64 *)((const char *)j.ws->host_pinned + 64);
+    const u64 slot = j.multi_slot ? j.batch_seq : 0;
+    const u64 *h_out = (const u64 *)((const char *)j.ws->host_pinned + 64 + slot * j.L * 8);
     const u64 cnt = std::min<u64>(j.L, j.q.p_end - j.p0);
     for (u64 i = 0; i < cnt; i++) {
         j.qsum ^= h_out[i];
@@ -686,12 +736,28 @@ Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *f
     TM_TRY(job_prep(j));
     std::vector<Job *> one{&j};
     DevBuf unused;
-    while (!j.done) {
-        TM_TRY(job_batch_begin(j));
-        for (; j.ell <= q.k; j.ell++) TM_TRY(launch_layers(j.st, one, unused, nullptr, 0, j.prof));
-        TM_TRY(job_readout_enqueue(j));
+    if (!j.done) {
+        // every lane batch of every repeat back to back; one sync at the end
+        const u64 nb = (q.p_end - q.p_begin + j.L - 1) / j.L;
+        const u64 total = nb * q.repeats;
+        TM_TRY(ensure_pinned(g.ws, 64 + total * j.L * 8));
+        j.multi_slot = true;
+        for (u64 b = 0; b < total; b++) {
+            j.r = (u32)(b / nb);
+            j.p0 = q.p_begin + (b % nb) * j.L;
+            j.batch_seq = b;
+            TM_TRY(job_batch_begin(j));
+            for (; j.ell <= q.k; j.ell++) TM_TRY(launch_layers(j.st, one, unused, nullptr, 0, j.prof));
+            TM_TRY(job_readout_enqueue(j));
+        }
         TM_CUDA(cudaStreamSynchronize(j.st));
-        job_readout_finish(j);
+        j.r = 0;
+        j.p0 = q.p_begin;
+        j.qsum = 0;
+        for (u64 b = 0; b < total; b++) {
+            j.batch_seq = b;
+            job_readout_finish(j);
+        }
     }
     TM_CUDA(cudaEventRecord(ev1, g.stream));
     TM_CUDA(cudaEventSynchronize(ev1));
@@ -750,6 +816,165 @@ Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, cons
     TM_CUDA(cudaMemcpyAsync(dst->data(), w.f_dst.p, (u64)mf * 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaMemcpyAsync(time->data(), w.f_time.p, (u64)mf * 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
+    return Status();
+}
+
+Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_t *d_alive, Graph *sub)
+{
+    const u64 m = g.m;
+    TM_TRY(w.vflag.reserve(std::max<u64>(g.n, 1)));
+    TM_TRY(w.keep.reserve((m + 1) * 4));
+    TM_TRY(w.counters.reserve(64));
+    k_vflag_mask<<<grid_for(g.n, 256), 256, 0, st>>>(g.n, d_alive, w.vflag.as<uint8_t>());
+    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), 0, 0,
+                                                 w.keep.as<u32>());
+    TM_CUDA(cudaGetLastError());
+    u32 *d_cnt = w.counters.as<u32>();
+    TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt, nullptr));
+    u32 mk = 0;
+    TM_CUDA(cudaMemcpyAsync(&mk, d_cnt, 4, cudaMemcpyDeviceToHost, st));
+    TM_CUDA(cudaStreamSynchronize(st));
+    sub->n = g.n;
+    sub->m_input = mk;
+    sub->m = mk;
+    sub->num_colors = g.num_colors;
+    sub->max_time = g.max_time;
+    sub->stream = st;
+    sub->h_color = g.h_color;
+    sub->ws.set_stream(st);
+    const u64 mb = std::max<u64>(mk, 1) * 4;
+    TM_TRY(dev_alloc((void **)&sub->d_src, mb, st));
+    TM_TRY(dev_alloc((void **)&sub->d_dst, mb, st));
+    TM_TRY(dev_alloc((void **)&sub->d_time, mb, st));
+    TM_TRY(dev_alloc((void **)&sub->d_color, std::max<u64>(g.n, 1) * 4, st));
+    if (mk)
+        k_compact<<<grid_for(m, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.keep.as<u32>(), sub->d_src,
+                                                    sub->d_dst, sub->d_time);
+    TM_CUDA(cudaMemcpyAsync(sub->d_color, g.d_color, (u64)g.n * 4, cudaMemcpyDeviceToDevice, st));
+    TM_CUDA(cudaGetLastError());
+    sub->resident_bytes = 3 * mb + (u64)g.n * 4;
+    return Status();
+}
+
+__global__ void k_first_nonzero(const u64 *sums, u64 mf, u32 *best)
+{
+    const u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < mf && sums[e]) atomicMin(best, (u32)e);
+}
+
+__global__ void k_vertex_sums(const u64 *sums, const u32 *f_dst, u64 mf, u64 *per_vertex)
+{
+    const u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < mf && sums[e]) atomicXor(&per_vertex[f_dst[e]], sums[e]);
+}
+
+// Run one job with arc localisation to the end (all lane batches of its one
+// repeat), leaving the arc sums in the graph's workspace.
+static Status run_localized(Graph &g, const QuerySpec &q, u32 repeat, const uint8_t *d_alive, Job *jout)
+{
+    Job &j = *jout;
+    j.g = &g;
+    j.q = q;
+    j.q.repeats = 1;
+    j.rep_offset = repeat;
+    j.d_alive = d_alive;
+    j.ws = &g.ws;
+    j.st = g.stream;
+    j.prof = &g.prof;
+    j.localize = true;
+    TM_TRY(job_prep(j));
+    if (j.done) return Status();
+    std::vector<Job *> one{&j};
+    DevBuf unused;
+    const u64 nb = (j.q.p_end - j.q.p_begin + j.L - 1) / j.L;
+    TM_TRY(ensure_pinned(g.ws, 64 + nb * j.L * 8));
+    j.multi_slot = true;
+    for (u64 b = 0; b < nb; b++) {
+        j.r = 0;
+        j.p0 = j.q.p_begin + b * j.L;
+        j.batch_seq = b;
+        TM_TRY(job_batch_begin(j));
+        for (; j.ell <= j.q.k; j.ell++) TM_TRY(launch_layers(j.st, one, unused, nullptr, 0, j.prof));
+        TM_TRY(job_readout_enqueue(j));
+    }
+    return Status();
+}
+
+Status job_first_arc(Job &j, u32 *best, u32 *a, u32 *b, u32 *t)
+{
+    *best = NONE;
+    if (j.mf == 0) return Status();
+    Workspace &w = *j.ws;
+    u32 *d_best = w.counters.as<u32>() + 4;
+    TM_CUDA(cudaMemsetAsync(d_best, 0xFF, 4, j.st));
+    k_first_nonzero<<<grid_for(j.mf, 256), 256, 0, j.st>>>(w.arc_sum.as<u64>(), j.mf, d_best);
+    j.prof->stats.launches++;
+    TM_CUDA(cudaGetLastError());
+    u32 hb = NONE;
+    TM_CUDA(cudaMemcpyAsync(&hb, d_best, 4, cudaMemcpyDeviceToHost, j.st));
+    TM_CUDA(cudaStreamSynchronize(j.st));
+    *best = hb;
+    if (hb == NONE) return Status();
+    TM_CUDA(cudaMemcpyAsync(a, w.f_src.as<u32>() + hb, 4, cudaMemcpyDeviceToHost, j.st));
+    TM_CUDA(cudaMemcpyAsync(b, w.f_dst.as<u32>() + hb, 4, cudaMemcpyDeviceToHost, j.st));
+    TM_CUDA(cudaMemcpyAsync(t, w.f_time.as<u32>() + hb, 4, cudaMemcpyDeviceToHost, j.st));
+    TM_CUDA(cudaStreamSynchronize(j.st));
+    return Status();
+}
+
+Status sieve_first_arc(Graph &g, const QuerySpec &q, u32 repeat, const uint8_t *d_alive, u32 *best, u32 *a, u32 *b,
+                       u32 *t)
+{
+    *best = NONE;
+    Job j;
+    TM_TRY(run_localized(g, q, repeat, d_alive, &j));
+    if (j.done) return Status();  // no arc kept
+    return job_first_arc(j, best, a, b, t);
+}
+
+Status sieve_localize(Graph &g, const QuerySpec &q, u64 *per_vertex, int *found, u64 *sieve_sum, double *ms)
+{
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    TM_CUDA(cudaEventCreate(&ev0));
+    TM_CUDA(cudaEventCreate(&ev1));
+    TM_CUDA(cudaEventRecord(ev0, g.stream));
+    Job j;
+    TM_TRY(run_localized(g, q, 0, nullptr, &j));
+    Workspace &w = g.ws;
+    DevBuf pv;
+    pv.stream = g.stream;
+    TM_TRY(pv.reserve(std::max<u64>(g.n, 1) * 8));
+    TM_CUDA(cudaMemsetAsync(pv.p, 0, (u64)g.n * 8, g.stream));
+    if (!j.done && j.mf) {
+        k_vertex_sums<<<grid_for(j.mf, 256), 256, 0, g.stream>>>(w.arc_sum.as<u64>(), w.f_dst.as<u32>(), j.mf,
+                                                                 pv.as<u64>());
+        g.prof.stats.launches++;
+        TM_CUDA(cudaGetLastError());
+    }
+    TM_CUDA(cudaMemcpyAsync(per_vertex, pv.p, (u64)g.n * 8, cudaMemcpyDeviceToHost, g.stream));
+    TM_CUDA(cudaEventRecord(ev1, g.stream));
+    TM_CUDA(cudaStreamSynchronize(g.stream));
+    pv.release();
+    float fms = 0;
+    cudaEventElapsedTime(&fms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (ms) *ms = fms;
+    u64 s = 0;
+    if (!j.done) {
+        j.r = 0;
+        j.p0 = j.q.p_begin;
+        j.qsum = 0;
+        const u64 nb = (j.q.p_end - j.q.p_begin + j.L - 1) / j.L;
+        for (u64 b = 0; b < nb; b++) {
+            j.batch_seq = b;
+            job_readout_finish(j);
+        }
+        s = j.sieve_sum;
+    }
+    *sieve_sum = s;
+    *found = s != 0;
+    TM_TRY(g.prof.collect());
     return Status();
 }
 

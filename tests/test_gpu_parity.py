@@ -222,7 +222,7 @@ def test_extraction_matches_oracle(tm):
     g, q = synth.config1_tiny()
     G = gpu_graph(tm, g)
     for seed in (1, 2, 3):
-        f, v, t = tm.tmotif_extract(G, q.k, q.multiset, seed=seed)
+        f, v, t = tm.tmotif_extract(G, q.k, q.multiset, seed=seed, method="halving")
         fo, vo, to, _ = oracle.extract(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=seed)
         assert f == fo and np.array_equal(v, vo) and np.array_equal(t, to)
     rng = random.Random(99)
@@ -230,13 +230,49 @@ def test_extraction_matches_oracle(tm):
         g, k, ms, kw = _random_case(rng)
         kw.pop("repeats", None)
         G = gpu_graph(tm, g)
-        f, v, t = tm.tmotif_extract(G, k, ms, **kw)
+        f, v, t = tm.tmotif_extract(G, k, ms, method="halving", **kw)
         fo, vo, to, _ = oracle.extract(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms,
                                        undirected=g.undirected, **kw)
         assert f == fo
         if f:
             assert np.array_equal(v, vo) and np.array_equal(t, to)
         G.close()
+
+
+def test_localized_extraction_matches_oracle(tm):
+    g, q = synth.config1_tiny()
+    G = gpu_graph(tm, g)
+    for seed in (1, 2, 3):
+        f, v, t = tm.tmotif_extract(G, q.k, q.multiset, seed=seed)
+        fo, vo, to = oracle.extract_localized(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset,
+                                              seed=seed)
+        assert f and fo and np.array_equal(v, vo) and np.array_equal(t, to)
+    rng = random.Random(123)
+    for _ in range(40):
+        g, k, ms, kw = _random_case(rng)
+        G = gpu_graph(tm, g)
+        f, v, t = tm.tmotif_extract(G, k, ms, **kw)
+        fo, vo, to = oracle.extract_localized(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms,
+                                              undirected=g.undirected, **kw)
+        assert f == fo
+        if f:
+            assert np.array_equal(v, vo) and np.array_equal(t, to)
+        G.close()
+
+
+def test_vertex_localized_sieve_matches_oracle(tm):
+    rng = random.Random(321)
+    cases = [synth.config1_brute(), synth.config1_tiny()]
+    for g, q in cases:
+        G = gpu_graph(tm, g)
+        d, pv = tm.tmotif_localize(G, q.k, q.multiset, seed=9)
+        cs, cd, ct = oracle.canon(g.n, g.src, g.dst, g.time)
+        pb = oracle.Problem(g.n, cs, cd, ct, g.color, g.num_colors, q.k, q.multiset)
+        arc = oracle.arc_sums(pb, oracle.query_seed(9, 0))
+        want = np.zeros(g.n, np.uint64)
+        np.bitwise_xor.at(want, cd.astype(np.int64), arc)
+        assert np.array_equal(pv, want)
+        assert d.sieve_sum == int(np.bitwise_xor.reduce(want))
 
 
 # ---------------------------------------------------------------------------

@@ -333,3 +333,56 @@ def test_time_window_bounds_are_inclusive(oracle_mod):
         assert not dec(t_min=4, t_max=7)
         assert dec(t_max=7) and not dec(t_max=6)
         assert dec(t_min=3) and not dec(t_min=4)
+
+
+# ---------------------------------------------------------------------------
+# Localised sieve and extraction by localisation (Sec. 5.7, Sec. 5.9)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("trial", range(30))
+def test_arc_sums_equal_walk_enumeration(oracle_mod, trial):
+    rng = random.Random(4000 + trial)
+    n, src, dst, time, color, _ = rand_graph(rng)
+    und = trial % 3 == 0
+    k = rng.randint(2, 5)
+    ms = [rng.randrange(3) for _ in range(k)]
+    kw = _constraints(rng, n, 6)
+    pb = problem(n, src, dst, time, color, und, k, ms, **kw)
+    qs = oracle.query_seed(rng.getrandbits(63), 0)
+    s = oracle.arc_sums(pb, qs)
+    bf, _ = oracle.brute_arc_det(pb, qs)
+    assert np.array_equal(s, bf)
+    # localising is a split of the whole sieve: XOR of all arc sums == Q
+    assert int(np.bitwise_xor.reduce(s)) == int(np.bitwise_xor.reduce(oracle.sieve_points(pb, qs)))
+
+
+@pytest.mark.parametrize("trial", range(40))
+def test_localized_extraction_returns_valid_path(oracle_mod, trial):
+    rng = random.Random(8000 + trial)
+    n, src, dst, time, color, _ = rand_graph(rng, n_lo=5, n_hi=12, t_hi=7)
+    und = trial % 3 == 0
+    k = rng.randint(2, 5)
+    ms = [rng.randrange(3) for _ in range(k)]
+    kw = {}
+    r = rng.random()
+    if r < 0.2:
+        kw["start"] = rng.randrange(n)
+    elif r < 0.4:
+        kw["end"] = rng.randrange(n)
+    if rng.random() < 0.3:
+        kw["t_max"] = rng.randint(2, 7)
+    pb = problem(n, src, dst, time, color, und, k, ms, **kw)
+    truth = oracle.count_paths(pb, limit=1)[0] > 0
+    found, verts, times = oracle.extract_localized(n, src, dst, time, color, 3, k, ms, undirected=und,
+                                                   seed=trial + 11, **kw)
+    assert found == truth
+    if found:
+        verify_path(n, src, dst, time, color, und, k, ms, verts, times, **kw)
+
+
+def test_localized_extraction_on_config1(oracle_mod):
+    g, q = synth.config1_tiny()
+    for seed in (1, 2, 3):
+        found, verts, times = oracle.extract_localized(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k,
+                                                       q.multiset, seed=seed)
+        assert found
+        verify_path(g.n, g.src, g.dst, g.time, g.color, False, q.k, q.multiset, verts, times)
