@@ -41,6 +41,9 @@ extern "C" {
 /* tmotif_query.flags: extract by halving self-reduction + DFS instead of by
  * localisation (see tmotif_extract). */
 #define TMOTIF_EXTRACT_HALVING 1u
+/* tmotif_query.flags: extract an optimum solution -- a path whose latest arc
+ * time is the least possible (tmotif_optimum_time), as in Sec. 5.8-5.9. */
+#define TMOTIF_EXTRACT_OPTIMUM 2u
 
 enum {
     TMOTIF_OK = 0,
@@ -84,7 +87,7 @@ typedef struct {
  *   point_begin, point_end  0,0 = all 2^k sieve points; otherwise only the
  *                 points [point_begin, point_end) are evaluated (sharding a
  *                 query across devices; combine the per-point sums by XOR);
- *   flags         0 or TMOTIF_EXTRACT_HALVING. */
+ *   flags         0 or TMOTIF_EXTRACT_HALVING and/or TMOTIF_EXTRACT_OPTIMUM. */
 typedef struct {
     uint32_t k;
     const uint32_t *multiset;
@@ -166,6 +169,14 @@ int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out)
  *     arcs in (time, dst) order.
  * Errors as tmotif_decide. */
 int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uint32_t *times, int *found);
+
+/* Optimum timestamp (Sec. 5.8): *t_opt = the least t' such that the query
+ * restricted to arcs with t_min <= time <= t' is YES, found by binary search
+ * with O(log t) decisions (each with the query's seed and repeats):
+ * lo = max(t_min, 1), hi = t_max (0: the largest time); no path when hi is
+ * NO; otherwise mid = lo + (hi - lo) / 2 moves hi to mid on YES and lo to
+ * mid + 1 on NO.  *found = 0 when no path exists.  Errors as tmotif_decide. */
+int tmotif_optimum_time(tmotif_graph_t g, const tmotif_query *q, uint32_t *t_opt, int *found);
 
 /* Vertex-localised sieve (Sec. 5.7): per_vertex[u] (caller-owned, n values)
  * receives Q_u = sum over the 2^k points of P_{u,k,t}(z^A) -- nonzero exactly

@@ -76,6 +76,9 @@ def _load():
                                      P, P]),
             "or_brute_arc_det": (i64, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32, u64, P]),
             "or_arc_sums": (C.c_int, [u32, u64, P, P, P, P, u32, P, u32, P, u32, u32, u32, u32, u64, P]),
+            "or_optimum_time": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, u32, P, u32, u32, u32, u32, u64, u32,
+                                          P, P, C.c_int]),
+            "or_min_last_time": (i64, [u32, u64, P, P, P, P, u32, u32, P, u32, u32, u32, u32, P]),
             "or_extract_localized": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, u32, P, u32, u32, u32, u32,
                                                u64, u32, P, P, P]),
             "or_decide": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u32, u32,
@@ -328,4 +331,30 @@ def extract_localized(n, src, dst, time, color, num_colors, k, multiset, *, undi
     if rc != 0:
         raise ValueError("oracle localized extract: invalid input")
     return bool(found.value), verts[:k].copy(), times[:k - 1].copy()
+
+
+def optimum_time(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
+                 t_min=0, t_max=0, seed=1, repeats=1, nthreads=0):
+    """Optimum timestamp (Sec. 5.8): least t' with a matching path using only
+    arcs in [t_min, t'], by binary search.  Returns (found, t_opt)."""
+    src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
+    t = u32(0)
+    found = C.c_int(0)
+    rc = _load().or_optimum_time(n, len(src), _ptr(src), _ptr(dst), _ptr(time), int(bool(undirected)), _ptr(color),
+                                 num_colors, k, _ptr(ms), start, end, t_min, t_max, seed, repeats, C.byref(t),
+                                 C.byref(found), nthreads)
+    if rc != 0:
+        raise ValueError("oracle optimum time: invalid input")
+    return bool(found.value), int(t.value)
+
+
+def min_last_time(pb: Problem):
+    """Least last-arc time over all matching paths (exhaustive DFS); None if none."""
+    t = u32(0)
+    c = _load().or_min_last_time(pb.n, pb.m, _ptr(pb.src), _ptr(pb.dst), _ptr(pb.time), _ptr(pb.color),
+                                 pb.num_colors, pb.k, _ptr(pb.multiset), pb.start, pb.end, pb.t_min, pb.t_max,
+                                 C.byref(t))
+    if c < 0:
+        raise ValueError("oracle dfs failed")
+    return int(t.value) if c > 0 else None
 

@@ -676,6 +676,7 @@ typedef struct {
     u32 need[256];       /* remaining multiplicity per colour (colours < 256 here) */
     uint8_t *onpath;
     u64 count, limit;
+    u32 min_last;        /* least last-arc time over the paths counted */
     u32 walk[OR_KMAX], wt[OR_KMAX];
     u32 *first_v, *first_t; /* first path found */
 } or_dfs;
@@ -685,6 +686,7 @@ static int or_dfs_rec(or_dfs *D, u32 depth, u32 last_t)
     const or_problem *P = D->P;
     if (depth == P->k) {
         if (P->end != OR_ANY && D->walk[P->k - 1] != P->end) return 0;
+        if (D->count == 0 || D->wt[P->k - 2] < D->min_last) D->min_last = D->wt[P->k - 2];
         if (D->count == 0 && D->first_v) {
             for (u32 r = 0; r < P->k; r++) D->first_v[r] = D->walk[r];
             for (u32 r = 0; r + 1 < P->k; r++) D->first_t[r] = D->wt[r];
@@ -743,6 +745,33 @@ i64 or_count_paths(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time
     or_problem P;
     or_fill_problem(&P, n, m, src, dst, time, color, num_colors, alive, k, multiset, start, end, t_min, t_max);
     return or_dfs_run(&P, limit, first_v, first_t);
+}
+
+/* Least last-arc time over all matching temporal paths (exhaustive DFS);
+ * returns the number of paths (0: *min_last untouched). */
+i64 or_min_last_time(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32 *color,
+                     u32 num_colors, u32 k, const u32 *multiset, u32 start, u32 end, u32 t_min, u32 t_max,
+                     u32 *min_last)
+{
+    or_problem P;
+    or_fill_problem(&P, n, m, src, dst, time, color, num_colors, NULL, k, multiset, start, end, t_min, t_max);
+    if (P.k < 2 || P.k > OR_KMAX || P.num_colors > 256) return -1;
+    or_dfs D;
+    memset(&D, 0, sizeof(D));
+    D.P = &P;
+    for (u32 r = 0; r < P.k; r++) D.need[P.multiset[r]]++;
+    D.onpath = (uint8_t *)calloc(P.n ? P.n : 1, 1);
+    for (u32 u = 0; u < P.n; u++) {
+        if (P.start != OR_ANY && P.start != u) continue;
+        u32 c = P.color[u];
+        if (D.need[c] == 0) continue;
+        D.need[c]--; D.onpath[u] = 1; D.walk[0] = u;
+        or_dfs_rec(&D, 1, 0);
+        D.need[c]++; D.onpath[u] = 0;
+    }
+    free(D.onpath);
+    if (D.count) *min_last = D.min_last;
+    return (i64)D.count;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -811,6 +840,57 @@ int or_decide(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int
     (void)nthreads;
     free(cs); free(cd); free(ct);
     return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Optimum timestamp (Sec. 5.8): the least t' for which the query restricted */
+/* to arcs with times in [t_min, t'] is YES, by binary search over t' with   */
+/* O(log t) decisions (each with the query's seed and repeats):             */
+/* lo = max(t_min, 1), hi = t_max (or the largest time); if hi is NO there   */
+/* is no path; otherwise while lo < hi: mid = lo + (hi - lo) / 2, YES at mid */
+/* sets hi = mid, NO sets lo = mid + 1.                                      */
+/* ------------------------------------------------------------------------ */
+int or_optimum_time(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int undirected,
+                    const u32 *color, u32 num_colors, u32 k, const u32 *multiset, u32 start, u32 end, u32 t_min,
+                    u32 t_max, u64 seed, u32 repeats, u32 *t_opt, int *found, int nthreads)
+{
+    if (or_check_query(n, color, num_colors, k, multiset, start, end) != 0 || repeats < 1) return -1;
+    u64 cap = (undirected ? 2 * m : m) + 1;
+    u32 *cs = (u32 *)malloc(sizeof(u32) * cap), *cd = (u32 *)malloc(sizeof(u32) * cap), *ct = (u32 *)malloc(sizeof(u32) * cap);
+    i64 mc = or_canon(n, m, src, dst, time, undirected, cs, cd, ct);
+    if (mc < 0) { free(cs); free(cd); free(ct); return -1; }
+#ifdef _OPENMP
+    int old = omp_get_max_threads();
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    (void)nthreads;
+    u32 tmax_all = 0;
+    for (i64 e = 0; e < mc; e++) if (ct[e] > tmax_all) tmax_all = ct[e];
+    u32 lo = t_min > 1 ? t_min : 1, hi = t_max ? t_max : tmax_all;
+    int rc = 0, yes = 0;
+    u64 q = 0;
+    *found = 0;
+    *t_opt = 0;
+    or_problem P;
+    or_fill_problem(&P, n, (u64)mc, cs, cd, ct, color, num_colors, NULL, k, multiset, start, end, t_min, hi);
+    if (hi >= lo && mc > 0) {
+        if (or_decide_canon(&P, seed, repeats, 0, 0, &yes, &q, NULL) != 0) rc = -1;
+        if (rc == 0 && yes) {
+            while (lo < hi) {
+                u32 mid = lo + (hi - lo) / 2;
+                P.t_max = mid;
+                if (or_decide_canon(&P, seed, repeats, 0, 0, &yes, &q, NULL) != 0) { rc = -1; break; }
+                if (yes) hi = mid;
+                else lo = mid + 1;
+            }
+            if (rc == 0) { *found = 1; *t_opt = lo; }
+        }
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(old);
+#endif
+    free(cs); free(cd); free(ct);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */

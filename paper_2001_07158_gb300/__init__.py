@@ -21,6 +21,7 @@ import numpy as np
 TMOTIF_ANY = 0xFFFFFFFF
 TMOTIF_KMAX = 20
 TMOTIF_EXTRACT_HALVING = 1
+TMOTIF_EXTRACT_OPTIMUM = 2
 ERRORS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "NOT_FOUND", 7: "BUSY"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -73,6 +74,7 @@ def _load():
         "tmotif_decide": (C.c_int, [P, C.POINTER(_Query), C.POINTER(_Decision)]),
         "tmotif_extract": (C.c_int, [P, C.POINTER(_Query), P, P, C.POINTER(C.c_int)]),
         "tmotif_localize": (C.c_int, [P, C.POINTER(_Query), P, C.POINTER(_Decision)]),
+        "tmotif_optimum_time": (C.c_int, [P, C.POINTER(_Query), C.POINTER(C.c_uint32), C.POINTER(C.c_int)]),
         "tmotif_decide_batch": (C.c_int, [P, P, C.c_uint32, P]),
         "tmotif_server_create": (C.c_int, [C.c_size_t, C.POINTER(P)]),
         "tmotif_submit": (C.c_int, [P, P, C.POINTER(_Query), C.c_int, C.POINTER(C.c_uint64)]),
@@ -182,15 +184,26 @@ def tmotif_decide(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_
 
 
 def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                   repeats=1, method="localized"):
-    """method: "localized" (default) or "halving" (TMOTIF_EXTRACT_HALVING)."""
-    flags = TMOTIF_EXTRACT_HALVING if method == "halving" else 0
+                   repeats=1, method="localized", optimum=False):
+    """method: "localized" (default) or "halving" (TMOTIF_EXTRACT_HALVING);
+    optimum: extract a path with the least latest time (TMOTIF_EXTRACT_OPTIMUM)."""
+    flags = (TMOTIF_EXTRACT_HALVING if method == "halving" else 0) | (TMOTIF_EXTRACT_OPTIMUM if optimum else 0)
     q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags)
     verts = np.zeros(k, np.uint32)
     times = np.zeros(max(k - 1, 1), np.uint32)
     found = C.c_int(0)
     _check(_lib.tmotif_extract(g.handle, C.byref(q), verts.ctypes.data, times.ctypes.data, C.byref(found)))
     return bool(found.value), verts, times[:k - 1]
+
+
+def tmotif_optimum_time(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
+                        repeats=1):
+    """Optimum timestamp (Sec. 5.8): (found, least t' with a path in [t_min, t'])."""
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0)
+    t = C.c_uint32(0)
+    f = C.c_int(0)
+    _check(_lib.tmotif_optimum_time(g.handle, C.byref(q), C.byref(t), C.byref(f)))
+    return bool(f.value), int(t.value)
 
 
 def tmotif_localize(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1):

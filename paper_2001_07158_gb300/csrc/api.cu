@@ -383,6 +383,17 @@ int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uin
         if (!s.ok()) return s.code;
         if (qs.p_begin != 0 || qs.p_end != (1ull << qs.k))
             return fail(TMOTIF_ERR_INVALID, "extraction needs the full point range").code;
+        if (qs.flags & TMOTIF_EXTRACT_OPTIMUM) {
+            u32 t_opt = 0;
+            int any = 0;
+            s = optimum_time(*g, qs, &t_opt, &any);
+            if (!s.ok()) return s.code;
+            if (!any) {
+                *found = 0;
+                return TMOTIF_OK;
+            }
+            qs.t_max = t_opt;
+        }
         if (qs.flags & TMOTIF_EXTRACT_HALVING) {
             u32 probes = 0;
             s = extract_path(*g, qs, verts, times, found, &probes);
@@ -390,6 +401,21 @@ int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uin
             s = extract_localized(*g, qs, verts, times, found);
         }
         return s.code;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
+}
+
+int tmotif_optimum_time(tmotif_graph_t g, const tmotif_query *q, uint32_t *t_opt, int *found)
+{
+    if (!g || !t_opt || !found) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    try {
+        QuerySpec qs;
+        Status s = parse_query(*g, q, &qs);
+        if (!s.ok()) return s.code;
+        if (qs.p_begin != 0 || qs.p_end != (1ull << qs.k))
+            return fail(TMOTIF_ERR_INVALID, "the optimum time needs the full point range").code;
+        return optimum_time(*g, qs, t_opt, found).code;
     } catch (const std::bad_alloc &) {
         return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
     }

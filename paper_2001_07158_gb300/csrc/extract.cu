@@ -351,4 +351,29 @@ Status extract_localized(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, i
     return Status();
 }
 
+Status optimum_time(Graph &g, const QuerySpec &q, u32 *t_opt, int *found)
+{
+    *found = 0;
+    *t_opt = 0;
+    u32 lo = q.t_min > 1 ? q.t_min : 1, hi = q.t_max ? q.t_max : g.max_time;
+    if (hi < lo || g.m == 0) return Status();
+    QuerySpec p = q;
+    p.t_max = hi;
+    int yes = 0;
+    u64 sum = 0;
+    double ms = 0;
+    TM_TRY(sieve_decide(g, p, nullptr, &yes, &sum, nullptr, &ms));
+    if (!yes) return Status();
+    while (lo < hi) {
+        const u32 mid = lo + (hi - lo) / 2;
+        p.t_max = mid;
+        TM_TRY(sieve_decide(g, p, nullptr, &yes, &sum, nullptr, &ms));
+        if (yes) hi = mid;
+        else lo = mid + 1;
+    }
+    *found = 1;
+    *t_opt = lo;
+    return Status();
+}
+
 }  // namespace tmo

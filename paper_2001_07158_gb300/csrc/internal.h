@@ -272,6 +272,8 @@ Status sieve_first_arc(Graph &g, const QuerySpec &q, u32 repeat, const uint8_t *
 // Per-vertex localised values Q_u (Sec. 5.7) for every vertex: XOR over the
 // arc sums of the arcs into u.  per_vertex (host) has n entries.
 Status sieve_localize(Graph &g, const QuerySpec &q, u64 *per_vertex, int *found, u64 *sieve_sum, double *ms);
+// Optimum timestamp by binary search over the window's upper end (Sec. 5.8).
+Status optimum_time(Graph &g, const QuerySpec &q, u32 *t_opt, int *found);
 // Extraction by localisation (k-1 arc-localised sieves, path built backwards).
 Status extract_localized(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *found);
 

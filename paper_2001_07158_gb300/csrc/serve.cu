@@ -53,6 +53,20 @@ size_t job_estimate(const Graph &g, const QuerySpec &q)
                     (u64)q.k * L * 8 + 4096 + (m / 4096 + 1) * 4);
 }
 
+// Estimated layer work of a request in arc-lane steps (kept arcs x layers x
+// points), doubled for an extraction (its shrinking levels add up to about
+// one more decision).
+double request_work(const Graph &g, const QuerySpec &q, bool extract)
+{
+    const double w = (double)kept_arc_bound(g, q) * (q.k - 1) * (double)(q.p_end - q.p_begin);
+    return extract ? 2 * w : w;
+}
+
+// Requests above this much work (about 25 ms of layer time on GB300) are
+// "large": they run one at a time in arrival order, while smaller requests
+// run beside them and may overtake them.
+const double LARGE_WORK = 4e9;
+
 enum JobState { J_BEGIN = 0, J_LAYER = 1, J_READOUT = 2 };
 
 struct SJob {
@@ -276,6 +290,7 @@ struct Request {
     QuerySpec q;
     bool is_extract = false;
     bool halving = false;
+    bool large = false;
     ExtractState ex;         // halving procedure
     LocalizedExtract lex;    // localisation procedure
     Clock::time_point t_submit;
@@ -303,9 +318,11 @@ struct tmotif_server {
     std::map<u64, std::unique_ptr<Request>> reqs;
     std::atomic<bool> stop{false};
     u64 next_ticket = 1;
+    Request *large_holder = nullptr;  // the large request now running, if any
 
     void complete(Request *r, Status s)
     {
+        if (large_holder == r) large_holder = nullptr;
         std::lock_guard<std::mutex> lock(mu);
         if (!s.ok()) {
             r->code = s.code;
@@ -399,19 +416,26 @@ struct tmotif_server {
                     waiting.push_back({r, nullptr});
                 }
             }
-            // admit in arrival order while the memory budget allows
-            while (!waiting.empty()) {
-                Request *r = waiting.front().first;
-                std::unique_ptr<SJob> &sj = waiting.front().second;
-                if (!sj && !next_job(r, &sj)) {  // nothing to run (error already recorded)
-                    if (!r->done) finish_extract(r);
-                    waiting.pop_front();
+            // admit in arrival order while the memory budget allows; a large
+            // request waits for the large slot, and smaller ones behind it
+            // may go first
+            for (auto it = waiting.begin(); it != waiting.end();) {
+                Request *r = it->first;
+                std::unique_ptr<SJob> &sj = it->second;
+                if (r->large && large_holder && large_holder != r) {
+                    ++it;
                     continue;
                 }
-                const size_t need = job_estimate(*r->g, sj->job.q);
+                if (!sj && !next_job(r, &sj)) {  // nothing to run (error already recorded)
+                    if (!r->done) finish_extract(r);
+                    it = waiting.erase(it);
+                    continue;
+                }
+                const size_t need = job_estimate(*sj->job.g, sj->job.q);
                 if (!sched->idle() && !sched->fits(need)) break;
+                if (r->large) large_holder = r;
                 Status s = sched->admit(std::move(sj), need, &done);
-                waiting.pop_front();
+                it = waiting.erase(it);
                 if (!s.ok()) complete(r, s);
             }
             if (!sched->idle()) {
@@ -459,7 +483,7 @@ struct tmotif_server {
                         continue;
                     }
                 }
-                // next probe joins the front of the admission queue (the request keeps its turn)
+                // next level/probe joins the front of the admission queue (the request keeps its turn)
                 std::unique_ptr<SJob> nj;
                 if (next_job(r, &nj)) waiting.push_front({r, std::move(nj)});
                 else if (!r->done) finish_extract(r);
@@ -507,6 +531,7 @@ extern "C" int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_q
         r->g = g;
         r->is_extract = is_extract != 0;
         r->halving = (r->q.flags & TMOTIF_EXTRACT_HALVING) != 0;
+        r->large = request_work(*g, r->q, r->is_extract) > LARGE_WORK;
         if (r->is_extract && r->halving) r->ex.init(*g, r->q);
         if (r->is_extract && !r->halving) r->lex.init(*g, r->q);
         r->t_submit = Clock::now();

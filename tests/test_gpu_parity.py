@@ -260,6 +260,25 @@ def test_localized_extraction_matches_oracle(tm):
         G.close()
 
 
+def test_optimum_time_and_optimum_extraction(tm):
+    rng = random.Random(77)
+    for trial in range(25):
+        g, k, ms, kw = _random_case(rng)
+        kw = {"seed": kw["seed"]}
+        G = gpu_graph(tm, g)
+        f, t = tm.tmotif_optimum_time(G, k, ms, **kw)
+        fo, to = oracle.optimum_time(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms,
+                                     undirected=g.undirected, **kw)
+        assert f == fo and (not f or t == to)
+        if f:
+            ff, v, tt = tm.tmotif_extract(G, k, ms, optimum=True, **kw)
+            assert ff and int(tt.max()) == t  # the extracted path ends at the optimum time
+            fe, ve, te = oracle.extract_localized(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms,
+                                                  undirected=g.undirected, t_max=t, **kw)
+            assert np.array_equal(v, ve) and np.array_equal(tt, te)
+        G.close()
+
+
 def test_vertex_localized_sieve_matches_oracle(tm):
     rng = random.Random(321)
     cases = [synth.config1_brute(), synth.config1_tiny()]

@@ -386,3 +386,24 @@ def test_localized_extraction_on_config1(oracle_mod):
                                                        q.multiset, seed=seed)
         assert found
         verify_path(g.n, g.src, g.dst, g.time, g.color, False, q.k, q.multiset, verts, times)
+
+
+# ---------------------------------------------------------------------------
+# Optimum timestamp (Sec. 5.8)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("trial", range(40))
+def test_optimum_time_equals_brute_force(oracle_mod, trial):
+    rng = random.Random(6000 + trial)
+    n, src, dst, time, color, _ = rand_graph(rng, n_lo=4, n_hi=10, t_hi=12)
+    und = trial % 4 == 0
+    k = rng.randint(2, 4)
+    ms = [rng.randrange(3) for _ in range(k)]
+    kw = {}
+    if trial % 5 == 1:
+        kw["t_min"] = rng.randint(1, 4)
+    pb = problem(n, src, dst, time, color, und, k, ms, **kw)
+    want = oracle.min_last_time(pb)
+    found, t = oracle.optimum_time(n, src, dst, time, color, 3, k, ms, undirected=und, seed=trial + 5, **kw)
+    assert found == (want is not None)
+    if found:
+        assert t == want
