@@ -83,6 +83,8 @@ def _load():
                                                u64, u32, P, P, P]),
             "or_decide": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u32, u32,
                                     u64, u32, u64, u64, P, P, P, C.c_int]),
+            "or_decide_ec": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u32, u32,
+                                       P, u64, u32, u64, u64, P, P, P, C.c_int]),
             "or_extract": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, u32, P, u32, u32, u32, u32,
                                      u64, u32, P, P, P, P, C.c_int]),
         }
@@ -103,7 +105,7 @@ def _ptr(a):
 
 
 # --------------------------------------------------------------------------
-# GF(2^64) and coefficients (Sec. 5.5 / Lemma 5.5; readings in the design doc)
+# GF(2^64) and coefficients (Sec. 5.5 / Lemma 5.5)
 # --------------------------------------------------------------------------
 def gf_mul(a: int, b: int) -> int:
     """Product in GF(2^64) = GF(2)[x]/(x^64 + x^4 + x^3 + x + 1)."""
@@ -275,6 +277,28 @@ def decide(n, src, dst, time, color, num_colors, k, multiset, *, undirected=Fals
                            point_begin, point_end, C.byref(found), C.byref(q), _ptr(pp), nthreads)
     if rc != 0:
         raise ValueError("oracle decide: invalid input")
+    return bool(found.value), int(q.value), pp[:npts]
+
+
+def decide_ec(n, src, dst, time, color, num_colors, k, multiset, timestamps, *, undirected=False, start=ANY,
+              end=ANY, t_min=0, t_max=0, seed=1, repeats=1, point_begin=0, point_end=0, alive=None, nthreads=0):
+    """EC-PathMotif decision (Sec. 6.3): the path's arc times must equal the
+    strictly increasing tuple `timestamps` (k-1 entries).  Returns (found,
+    sieve_sum, per_point) like decide()."""
+    src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
+    T = _u32(timestamps)
+    if len(T) != k - 1:
+        raise ValueError("oracle decide_ec: need k-1 timestamps")
+    npts = (1 << k) if point_end == 0 else point_end - point_begin
+    pp = np.zeros(max(npts, 1), np.uint64)
+    found = C.c_int(0)
+    q = u64(0)
+    al = None if alive is None else np.ascontiguousarray(np.asarray(alive, np.uint8))
+    rc = _load().or_decide_ec(n, len(src), _ptr(src), _ptr(dst), _ptr(time), int(bool(undirected)), _ptr(color),
+                              num_colors, _ptr(al), k, _ptr(ms), start, end, t_min, t_max, _ptr(T), seed, repeats,
+                              point_begin, point_end, C.byref(found), C.byref(q), _ptr(pp), nthreads)
+    if rc != 0:
+        raise ValueError("oracle decide_ec: invalid input")
     return bool(found.value), int(q.value), pp[:npts]
 
 

@@ -28,10 +28,14 @@
  *   - or_extract() is extraction by self-reducibility (Sec. 5.9) with the
  *     halving group test and a temporal DFS on the survivors.
  *
- * Readings of points the paper leaves open (field modulus, random-number
- * generator, slot assignment, boundary P_{u,1,0}, direction, duplicates,
- * start/end and time window, extraction order) are listed in the design doc and
- * implemented here exactly as stated there.
+ * Points the paper leaves open are read as follows (the GPU library makes
+ * the same readings in code of its own): field modulus x^64+x^4+x^3+x+1;
+ * random values from the splitmix64 output function keyed by the query seed
+ * and the variable's indices (y by arc content and walk position); slots of
+ * the distinct query colours in ascending order; P_{u,1,i} = x_u for i >= 0;
+ * arcs directed, undirected edges as two arcs; duplicate arcs merged and
+ * self-loops dropped; start/end as restrictions of the first and last
+ * vertex; an inclusive time window; extraction candidates in ascending id.
  *
  * Parity pins (tests/test_oracle_*.py): field axioms, x^64 mod f, inverse,
  * Frobenius, Rabin irreducibility, splitmix64 published outputs, the paper's
@@ -839,6 +843,111 @@ int or_decide(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int
     }
     (void)nthreads;
     free(cs); free(cd); free(ct);
+    return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* EC-PathMotif (Sec. 6.3): the path's arc times must equal the tuple        */
+/* T = (j_1, ..., j_{k-1}), j_1 < ... < j_{k-1}.  The recurrence there keeps */
+/* one value per vertex and walk length, with no "stay" term:               */
+/*   P_{u,1} = x_u,                                                          */
+/*   P_{u,l} = x_u * sum over arcs (v -> u, j_{l-1}) of                     */
+/*             y_{vu,l-1,j_{l-1}} * P_{v,l-1},      l = 2..k,               */
+/*   Q^A     = sum_{u end-ok} P_{u,k}.                                       */
+/* Two vertex arrays per point (O(n) memory, as the paper states).  Arcs    */
+/* outside the window [t_min, t_max] are not used either; start restricts   */
+/* P_{.,1}, end the final sum.                                               */
+/* ------------------------------------------------------------------------ */
+static int or_ec_core(const or_problem *P, const u32 *T, u64 qs, u64 p_begin, u64 p_end, u64 *out)
+{
+    u32 k = P->k, n = P->n;
+    u32 *sb = (u32 *)malloc(sizeof(u32) * (P->num_colors + 1));
+    u32 *sc = (u32 *)malloc(sizeof(u32) * (P->num_colors + 1));
+    if (or_slots(k, P->multiset, P->num_colors, sb, sc) != 0) { free(sb); free(sc); return -1; }
+    int err = 0;
+    i64 npts = (i64)(p_end - p_begin);
+#pragma omp parallel
+    {
+        u64 *x = (u64 *)malloc(sizeof(u64) * (n ? n : 1));
+        u64 *cur = (u64 *)malloc(sizeof(u64) * (n ? n : 1));
+        u64 *nxt = (u64 *)malloc(sizeof(u64) * (n ? n : 1));
+        if (!x || !cur || !nxt) {
+#pragma omp atomic write
+            err = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (i64 pi = 0; pi < npts; pi++) {
+            if (!x || !cur || !nxt) continue;
+            or_all_x(P, qs, sb, sc, p_begin + (u64)pi, x);
+            for (u32 u = 0; u < n; u++) cur[u] = (P->start == OR_ANY || P->start == u) ? x[u] : 0;
+            for (u32 l = 2; l <= k; l++) {
+                u32 j = T[l - 2];
+                memset(nxt, 0, sizeof(u64) * n);
+                if (or_arc_in_window(P, j))
+                    for (u64 e = 0; e < P->m; e++) {
+                        if (P->time[e] != j) continue;
+                        u32 v = P->src[e], u = P->dst[e];
+                        nxt[u] ^= or_gf_mul(or_coef_y(qs, v, u, j, l - 1), cur[v]);
+                    }
+                for (u32 u = 0; u < n; u++) cur[u] = or_gf_mul(x[u], nxt[u]);
+            }
+            u64 q = 0;
+            for (u32 u = 0; u < n; u++)
+                if (P->end == OR_ANY || P->end == u) q ^= cur[u];
+            out[pi] = q;
+        }
+        free(x); free(cur); free(nxt);
+    }
+    free(sb);
+    free(sc);
+    return err ? -1 : 0;
+}
+
+/* Public EC-PathMotif decision from the raw edge list; T holds k-1 strictly */
+/* increasing timestamps >= 1.  Outputs as or_decide.                        */
+int or_decide_ec(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int undirected, const u32 *color,
+                 u32 num_colors, const uint8_t *alive, u32 k, const u32 *multiset, u32 start, u32 end, u32 t_min,
+                 u32 t_max, const u32 *T, u64 seed, u32 repeats, u64 p_begin, u64 p_end, int *found,
+                 u64 *sieve_sum, u64 *per_point, int nthreads)
+{
+    if (or_check_query(n, color, num_colors, k, multiset, start, end) != 0 || repeats < 1) return -1;
+    for (u32 i = 0; i + 1 < k; i++)
+        if (T[i] == 0 || (i > 0 && T[i] <= T[i - 1])) return -1;
+    u64 full = (u64)1 << k;
+    if (p_end == 0) { p_begin = 0; p_end = full; }
+    if (p_begin >= p_end || p_end > full) return -1;
+    u64 cap = (undirected ? 2 * m : m) + 1;
+    u32 *cs = (u32 *)malloc(sizeof(u32) * cap), *cd = (u32 *)malloc(sizeof(u32) * cap), *ct = (u32 *)malloc(sizeof(u32) * cap);
+    u64 npts = p_end - p_begin;
+    u64 *vals = (u64 *)malloc(sizeof(u64) * npts);
+    i64 mc = or_canon(n, m, src, dst, time, undirected, cs, cd, ct);
+    int r = -1;
+    if (mc >= 0 && vals) {
+        or_problem P;
+        or_fill_problem(&P, n, (u64)mc, cs, cd, ct, color, num_colors, alive, k, multiset, start, end, t_min, t_max);
+#ifdef _OPENMP
+        int old = omp_get_max_threads();
+        if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+        r = 0;
+        *found = 0;
+        for (u32 rep = 0; rep < repeats && r == 0; rep++) {
+            r = or_ec_core(&P, T, or_query_seed(seed, rep), p_begin, p_end, vals);
+            if (r != 0) break;
+            u64 q = 0;
+            for (u64 i = 0; i < npts; i++) q ^= vals[i];
+            if (rep == 0) {
+                *sieve_sum = q;
+                if (per_point) memcpy(per_point, vals, sizeof(u64) * npts);
+            }
+            if (q != 0) *found = 1;
+        }
+#ifdef _OPENMP
+        if (nthreads > 0) omp_set_num_threads(old);
+#endif
+    }
+    (void)nthreads;
+    free(cs); free(cd); free(ct); free(vals);
     return r;
 }
 

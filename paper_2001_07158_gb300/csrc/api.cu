@@ -63,10 +63,32 @@ Status dev_alloc(void **p, size_t bytes, cudaStream_t s)
     cudaMemPool_t pool;
     TM_TRY(pool_for_current_device(&pool));
     cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 256), pool, s);
+    if (e == cudaErrorMemoryAllocation) {
+        // the pool keeps freed blocks cached; hand them back to the device
+        // (after every pending free has happened) and try once more
+        cudaGetLastError();
+        cudaDeviceSynchronize();
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 256), pool, s);
+    }
     if (e != cudaSuccess) {
         *p = nullptr;
         return cuda_fail(e, "device allocation");
     }
+    return Status();
+}
+
+Status device_headroom(size_t *bytes)
+{
+    *bytes = 0;
+    cudaMemPool_t pool;
+    TM_TRY(pool_for_current_device(&pool));
+    size_t free_b = 0, total_b = 0;
+    TM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    unsigned long long reserved = 0, used = 0;
+    TM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+    TM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    *bytes = free_b + (size_t)(reserved > used ? reserved - used : 0);
     return Status();
 }
 

@@ -43,6 +43,9 @@ Status cuda_fail(cudaError_t e, const char *what);
 // memory kept cached across frees so repeated graphs and queries reuse it).
 Status dev_alloc(void **p, size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
+// Bytes a new allocation could still obtain: free device memory plus the
+// pool's cached, unused blocks.
+Status device_headroom(size_t *bytes);
 
 // Colour-pair histograms are kept for up to this many colours.
 static const u32 PAIR_HIST_COLORS = 64;

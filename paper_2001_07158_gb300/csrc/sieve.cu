@@ -513,9 +513,19 @@ Status job_prep(Job &j)
     j.sieve_sum = 0;
     j.done = (j.mf == 0);
     if (j.done) return Status();
-    // lane width: power of two >= 4, at most LANES_MAX
+    // lane width: power of two >= 4, at most LANES_MAX, halved while the
+    // lane-proportional buffers (x, two checkpoint buffers, chunk partials)
+    // would not fit the device memory left (per-point values do not depend
+    // on the lane width)
     u32 L = 4;
     while (L < LANES_MAX && L < npts) L <<= 1;
+    {
+        size_t room = 0;
+        TM_TRY(device_headroom(&room));
+        room += w.x.bytes + w.C0.bytes + w.C1.bytes + w.partial.bytes;
+        const u64 per_lane = ((u64)n + 2 * std::max<u64>(j.ncp, 1) + (j.mf + CHUNK - 1) / CHUNK) * 8;
+        while (L > 4 && per_lane * L > room / 10 * 9) L >>= 1;
+    }
     j.L = L;
     j.T = L / 2 > 32 ? 32 : L / 2;
     j.lane_groups = L / (2 * j.T);

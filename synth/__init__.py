@@ -97,22 +97,28 @@ def powerlaw_graph(n, m, t_max, num_colors, seed, exponent=2.1, color_dist="unif
 
 
 def tour_graph(n, avg_deg, t_max, num_colors, seed, name="tour"):
-    """Transport-style graph: vehicles run tours over random stops; each hop is
-    an arc (stop_i -> stop_{i+1}) at a strictly later time slot."""
+    """Transport-style graph: vehicles run tours of 4-39 hops over random
+    stops; a tour starts in the first half of the day and each hop departs
+    1-3 slots after the previous one.  Tours are drawn in vectorised blocks."""
     r = _rng(seed)
     m_target = int(avg_deg * n)
     srcs, dsts, times = [], [], []
     total = 0
     while total < m_target:
-        length = int(r.integers(4, 40))
-        stops = r.integers(0, n, length + 1)
-        t0 = int(r.integers(1, max(2, t_max // 2)))
-        steps = r.integers(1, 4, length)
-        ts = t0 + np.cumsum(steps) - steps[0]
+        cnt = max(16, (m_target - total) // 15)
+        length = r.integers(4, 40, cnt)                   # hops per tour
+        t0 = r.integers(1, max(2, t_max // 2), cnt)       # first departure
+        first = np.cumsum(length) - length                # first hop of each tour
+        tour = np.repeat(np.arange(cnt), length)          # tour of each hop
+        steps = r.integers(1, 4, int(length.sum()))
+        cs = np.cumsum(steps)
+        start = (cs - steps)[first]                       # steps before each tour
+        ts = t0[tour] + (cs - start[tour]) - steps[first][tour]
+        stops = r.integers(0, n, int(length.sum()) + cnt)  # length+1 stops per tour
+        h = np.arange(len(steps)) + tour
         ok = ts <= t_max
-        ts, a, b = ts[ok], stops[:-1][ok], stops[1:][ok]
-        srcs.append(a); dsts.append(b); times.append(ts)
-        total += len(ts)
+        srcs.append(stops[h][ok]); dsts.append(stops[h + 1][ok]); times.append(ts[ok])
+        total += int(ok.sum())
     src = np.concatenate(srcs)[:m_target].astype(np.uint32)
     dst = np.concatenate(dsts)[:m_target].astype(np.uint32)
     time = np.concatenate(times)[:m_target].astype(np.uint32)
