@@ -87,7 +87,15 @@ typedef struct {
  *   point_begin, point_end  0,0 = all 2^k sieve points; otherwise only the
  *                 points [point_begin, point_end) are evaluated (sharding a
  *                 query across devices; combine the per-point sums by XOR);
- *   flags         0 or TMOTIF_EXTRACT_HALVING and/or TMOTIF_EXTRACT_OPTIMUM. */
+ *   flags         0 or TMOTIF_EXTRACT_HALVING and/or TMOTIF_EXTRACT_OPTIMUM;
+ *   timestamps    NULL, or the EC-PathMotif tuple T = (j_1, ..., j_{k-1}) of
+ *                 Sec. 6.3 (caller-owned host array of k-1 strictly increasing
+ *                 times >= 1; INVALID otherwise): the path's l-th arc must have
+ *                 time j_l.  Only arcs whose time is in T (and in the window)
+ *                 are used; a temporal path of k-1 arcs with strictly
+ *                 increasing times from a set of k-1 values uses them all in
+ *                 order, so this is exactly the EC recurrence of Sec. 6.3.
+ *                 Applies to decide, extract, batch and server requests. */
 typedef struct {
     uint32_t k;
     const uint32_t *multiset;
@@ -97,6 +105,7 @@ typedef struct {
     uint32_t repeats;
     uint32_t point_begin, point_end;
     uint32_t flags;
+    const uint32_t *timestamps;
 } tmotif_query;
 
 /* Result of tmotif_decide.  per_point is caller-owned and optional (NULL or

@@ -43,7 +43,8 @@ class _GraphDesc(C.Structure):
 class _Query(C.Structure):
     _fields_ = [("k", C.c_uint32), ("multiset", C.c_void_p), ("start", C.c_uint32), ("end", C.c_uint32),
                 ("t_min", C.c_uint32), ("t_max", C.c_uint32), ("seed", C.c_uint64), ("repeats", C.c_uint32),
-                ("point_begin", C.c_uint32), ("point_end", C.c_uint32), ("flags", C.c_uint32)]
+                ("point_begin", C.c_uint32), ("point_end", C.c_uint32), ("flags", C.c_uint32),
+                ("timestamps", C.c_void_p)]
 
 
 class _Decision(C.Structure):
@@ -166,16 +167,23 @@ def tmotif_graph_get_info(g: Graph) -> dict:
     return {f: getattr(info, f) for f, _ in _Info._fields_}
 
 
-def _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end, flags=0):
+def _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end, flags=0,
+           timestamps=None):
     ms = _u32(multiset)
+    ts = None if timestamps is None else _u32(timestamps)
+    if ts is not None and len(ts) != k - 1:
+        raise TmotifError(1, "EC timestamps: need k-1 values")
     q = _Query(k, ms.ctypes.data, start, end, t_min, t_max, seed & (2**64 - 1), repeats, point_begin, point_end,
-               flags)
-    return q, ms
+               flags, None if ts is None else ts.ctypes.data)
+    return q, (ms, ts)
 
 
 def tmotif_decide(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                  repeats=1, point_begin=0, point_end=0, per_point=True) -> Decision:
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end)
+                  repeats=1, point_begin=0, point_end=0, per_point=True, timestamps=None) -> Decision:
+    """PathMotif decision; with `timestamps` (k-1 strictly increasing times)
+    the EC-PathMotif decision of Sec. 6.3."""
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end,
+                     timestamps=timestamps)
     npts = (1 << k) if point_end == 0 else max(point_end - point_begin, 0)
     pp = np.zeros(max(npts, 1), np.uint64) if per_point else None
     d = _Decision(0, 0, pp.ctypes.data if per_point else None, 0.0)
@@ -184,11 +192,12 @@ def tmotif_decide(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_
 
 
 def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                   repeats=1, method="localized", optimum=False):
+                   repeats=1, method="localized", optimum=False, timestamps=None):
     """method: "localized" (default) or "halving" (TMOTIF_EXTRACT_HALVING);
-    optimum: extract a path with the least latest time (TMOTIF_EXTRACT_OPTIMUM)."""
+    optimum: extract a path with the least latest time (TMOTIF_EXTRACT_OPTIMUM);
+    timestamps: the EC-PathMotif tuple (Sec. 6.3), or None."""
     flags = (TMOTIF_EXTRACT_HALVING if method == "halving" else 0) | (TMOTIF_EXTRACT_OPTIMUM if optimum else 0)
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags)
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags, timestamps)
     verts = np.zeros(k, np.uint32)
     times = np.zeros(max(k - 1, 1), np.uint32)
     found = C.c_int(0)
@@ -197,18 +206,19 @@ def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t
 
 
 def tmotif_optimum_time(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                        repeats=1):
+                        repeats=1, timestamps=None):
     """Optimum timestamp (Sec. 5.8): (found, least t' with a path in [t_min, t'])."""
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0)
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, timestamps=timestamps)
     t = C.c_uint32(0)
     f = C.c_int(0)
     _check(_lib.tmotif_optimum_time(g.handle, C.byref(q), C.byref(t), C.byref(f)))
     return bool(f.value), int(t.value)
 
 
-def tmotif_localize(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1):
+def tmotif_localize(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
+                    timestamps=None):
     """Vertex-localised sieve: (decision, per_vertex Q_u for every vertex)."""
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, 1, 0, 0)
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, 1, 0, 0, timestamps=timestamps)
     pv = np.zeros(max(g.n, 1), np.uint64)
     d = _Decision(0, 0, None, 0.0)
     _check(_lib.tmotif_localize(g.handle, C.byref(q), pv.ctypes.data, C.byref(d)))
@@ -228,7 +238,8 @@ def tmotif_decide_batch(graphs, queries):
         k = qd.pop("k")
         ms = qd.pop("multiset")
         q, kp = _query(k, ms, qd.get("start", TMOTIF_ANY), qd.get("end", TMOTIF_ANY), qd.get("t_min", 0),
-                       qd.get("t_max", 0), qd.get("seed", 1), qd.get("repeats", 1), 0, 0)
+                       qd.get("t_max", 0), qd.get("seed", 1), qd.get("repeats", 1), 0, 0,
+                       timestamps=qd.get("timestamps"))
         qarr[i] = q
         keep.append(kp)
         pp = np.zeros(1 << k, np.uint64)
@@ -316,9 +327,9 @@ def tmotif_server_create(hbm_budget_bytes: int) -> Server:
 
 
 def tmotif_submit(s: Server, g: Graph, k, multiset, *, is_extract=False, start=TMOTIF_ANY, end=TMOTIF_ANY,
-                  t_min=0, t_max=0, seed=1, repeats=1, method="localized") -> int:
+                  t_min=0, t_max=0, seed=1, repeats=1, method="localized", timestamps=None) -> int:
     flags = TMOTIF_EXTRACT_HALVING if method == "halving" else 0
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags)
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags, timestamps)
     t = C.c_uint64(0)
     _check(_lib.tmotif_submit(s.handle, g.handle, C.byref(q), int(bool(is_extract)), C.byref(t)))
     return int(t.value)

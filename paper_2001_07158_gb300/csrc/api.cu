@@ -312,6 +312,15 @@ Status parse_query(const Graph &g, const tmotif_query *q, QuerySpec *out)
     out->seed = q->seed;
     out->repeats = q->repeats;
     out->flags = q->flags;
+    out->times_exact.clear();
+    if (q->timestamps) {
+        for (u32 i = 0; i + 1 < q->k; i++) {
+            const u32 t = q->timestamps[i];
+            if (t == 0 || (i > 0 && t <= q->timestamps[i - 1]))
+                return fail(TMOTIF_ERR_INVALID, "EC timestamps must be k-1 strictly increasing times >= 1");
+            out->times_exact.push_back(t);
+        }
+    }
     const u64 full = 1ull << q->k;
     if (q->point_begin == 0 && q->point_end == 0) {
         out->p_begin = 0;

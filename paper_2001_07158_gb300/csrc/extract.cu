@@ -173,7 +173,7 @@ Status extract_finish(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, c
     TM_TRY(w.alive.reserve(std::max<u32>(g.n, 1)));
     TM_CUDA(cudaMemcpyAsync(w.alive.p, ex.alive.data(), g.n, cudaMemcpyHostToDevice, st));
     std::vector<u32> as, ad, at;
-    TM_TRY(gather_arcs(g, w, st, prof, w.alive.as<uint8_t>(), q.t_min, q.t_max, &as, &ad, &at));
+    TM_TRY(gather_arcs(g, w, st, prof, w.alive.as<uint8_t>(), q.filter(), &as, &ad, &at));
     Dfs D;
     D.q = &q;
     D.color = g.h_color.get();

@@ -120,15 +120,33 @@ struct Graph {
     size_t resident_bytes = 0;
 };
 
+// Arc filter of a query, passed by value to the filter kernel: the time
+// window and, for EC-PathMotif, the set of allowed times (n_times = 0: any).
+struct ArcFilter {
+    u32 t_min = 0, t_max = 0;
+    u32 n_times = 0;
+    u32 times[TMOTIF_KMAX];
+};
+
 struct QuerySpec {
     u32 k = 0;
     std::vector<u32> multiset;
     u32 start = TMOTIF_ANY, end = TMOTIF_ANY;
     u32 t_min = 0, t_max = 0;
+    std::vector<u32> times_exact;       // EC-PathMotif tuple (empty: none)
     u64 seed = 0;
     u32 repeats = 1;
     u64 p_begin = 0, p_end = 0;         // resolved point range
     u32 flags = 0;
+    ArcFilter filter() const
+    {
+        ArcFilter f;
+        f.t_min = t_min;
+        f.t_max = t_max;
+        f.n_times = (u32)times_exact.size();
+        for (u32 i = 0; i < f.n_times; i++) f.times[i] = times_exact[i];
+        return f;
+    }
 };
 
 Status parse_query(const Graph &g, const tmotif_query *q, QuerySpec *out);
@@ -205,8 +223,8 @@ Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *f
 // Arcs among the vertices with alive[u] != 0 (device mask) inside the time
 // window, copied to the host in (dst, time, src) order, using workspace w on
 // stream st.
-Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const uint8_t *d_alive, u32 t_min,
-                   u32 t_max, std::vector<u32> *src, std::vector<u32> *dst, std::vector<u32> *time);
+Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const uint8_t *d_alive, ArcFilter f,
+                   std::vector<u32> *src, std::vector<u32> *dst, std::vector<u32> *time);
 
 // Device arrays of a graph (arcs, colours, workspace, profiler events).
 void release_graph_arrays(Graph *g);

@@ -295,6 +295,7 @@ Status decide_noalloc(const u32 *src, const u32 *dst, const u32 *time, u64 m, co
     if (!q || !q->multiset) return fail(TMOTIF_ERR_INVALID, "null query");
     if (q->k < 2 || q->k > TMOTIF_KMAX) return fail(TMOTIF_ERR_UNSUPPORTED, "k must be in [2, 20]");
     if (q->repeats != 1) return fail(TMOTIF_ERR_INVALID, "the allocation-free decision evaluates one repeat");
+    if (q->timestamps) return fail(TMOTIF_ERR_UNSUPPORTED, "the allocation-free decision takes no EC timestamps");
     if (num_colors == 0 || num_colors > NA_COLORS_MAX) return fail(TMOTIF_ERR_INVALID, "num_colors must be in [1, 4096]");
     if (n == 0 || (m > 0 && (!src || !dst || !time)) || !color || !d_out)
         return fail(TMOTIF_ERR_INVALID, "null graph or output pointer");

@@ -55,14 +55,21 @@ __global__ void k_active_list(u32 n, const u32 *act, u32 *list)
     if (u < n && act[u + 1] != act[u]) list[act[u]] = (u32)u;
 }
 
-__global__ void k_keep(u64 m, const u32 *src, const u32 *dst, const u32 *time, const uint8_t *vflag, u32 t_min,
-                       u32 t_max, u32 *keep)
+// Arc e is kept iff both endpoints are flagged, its time lies in the window
+// and, for EC-PathMotif (Sec. 6.3), its time is one of the tuple's.
+__global__ void k_keep(u64 m, const u32 *src, const u32 *dst, const u32 *time, const uint8_t *vflag, ArcFilter f,
+                       u32 *keep)
 {
     u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (e > m) return;
     if (e == m) { keep[m] = 0; return; }
     u32 t = time[e];
-    bool k = vflag[src[e]] && vflag[dst[e]] && t >= t_min && (t_max == 0 || t <= t_max);
+    bool k = vflag[src[e]] && vflag[dst[e]] && t >= f.t_min && (f.t_max == 0 || t <= f.t_max);
+    if (k && f.n_times) {
+        bool in = false;
+        for (u32 i = 0; i < f.n_times; i++) in |= (f.times[i] == t);
+        k = in;
+    }
     keep[e] = k ? 1 : 0;
 }
 
@@ -459,8 +466,8 @@ Status job_prep(Job &j)
     TM_TRY(w.keep.reserve((m + 1) * 4));
     k_vflag<<<grid_for((u64)n + 1, 256), 256, 0, st>>>(n, g.d_color, w.slot_count.as<u32>(), j.d_alive,
                                                        w.vflag.as<uint8_t>(), w.act.as<u32>());
-    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), q.t_min,
-                                                 q.t_max, w.keep.as<u32>());
+    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), q.filter(),
+                                                 w.keep.as<u32>());
     *launches += 2;
     TM_CUDA(cudaGetLastError());
     TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt + 0, launches));
@@ -794,16 +801,16 @@ __global__ void k_vflag_mask(u32 n, const uint8_t *alive, uint8_t *vflag)
     if (u < n) vflag[u] = alive[u] ? 1 : 0;
 }
 
-Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const uint8_t *d_alive, u32 t_min,
-                   u32 t_max, std::vector<u32> *src, std::vector<u32> *dst, std::vector<u32> *time)
+Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, const uint8_t *d_alive, ArcFilter f,
+                   std::vector<u32> *src, std::vector<u32> *dst, std::vector<u32> *time)
 {
     const u64 m = g.m;
     TM_TRY(w.vflag.reserve(std::max<u64>(g.n, 1)));
     TM_TRY(w.keep.reserve((m + 1) * 4));
     TM_TRY(w.counters.reserve(64));
     k_vflag_mask<<<grid_for(g.n, 256), 256, 0, st>>>(g.n, d_alive, w.vflag.as<uint8_t>());
-    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), t_min,
-                                                 t_max, w.keep.as<u32>());
+    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), f,
+                                                 w.keep.as<u32>());
     prof.stats.launches += 2;
     TM_CUDA(cudaGetLastError());
     u32 *d_cnt = w.counters.as<u32>();
@@ -836,8 +843,8 @@ Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_
     TM_TRY(w.keep.reserve((m + 1) * 4));
     TM_TRY(w.counters.reserve(64));
     k_vflag_mask<<<grid_for(g.n, 256), 256, 0, st>>>(g.n, d_alive, w.vflag.as<uint8_t>());
-    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), 0, 0,
-                                                 w.keep.as<u32>());
+    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(),
+                                                 ArcFilter(), w.keep.as<u32>());
     TM_CUDA(cudaGetLastError());
     u32 *d_cnt = w.counters.as<u32>();
     TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt, nullptr));

@@ -295,6 +295,71 @@ def test_vertex_localized_sieve_matches_oracle(tm):
 
 
 # ---------------------------------------------------------------------------
+# EC-PathMotif (Sec. 6.3): the path's arc times are a given tuple T
+# ---------------------------------------------------------------------------
+def _ec_both(tm, G, g, k, ms, T, **kw):
+    d = tm.tmotif_decide(G, k, ms, timestamps=T, **kw)
+    o = oracle.decide_ec(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, T, undirected=g.undirected,
+                         **kw)
+    return d, o
+
+
+def test_ec_pathmotif_matches_oracle(tm):
+    rng = random.Random(606)
+    cases = 0
+    for i in range(150):
+        if i % 2:
+            g, k, ms, kw = _random_case(rng)
+        else:  # dense: many EC walks
+            n = rng.randint(8, 40)
+            g = synth.uniform_graph(n, rng.randint(5 * n, 30 * n), 8, 3, seed=900 + i)
+            g.undirected = rng.random() < 0.3
+            k = rng.randint(2, 6)
+            ms = [rng.randrange(3) for _ in range(k)]
+            kw = {"seed": rng.getrandbits(63)}
+        t_hi = int(g.time.max()) if len(g.time) else 1
+        if t_hi < k - 1:
+            continue
+        T = sorted(rng.sample(range(1, t_hi + 1), k - 1))
+        G = gpu_graph(tm, g)
+        assert_same(*_ec_both(tm, G, g, k, ms, T, **kw))
+        G.close()
+        cases += 1
+    assert cases > 100
+
+
+def test_ec_pathmotif_planted_tuple_and_extraction(tm):
+    # T taken from a path that exists: EC says YES, and the extracted path
+    # (both procedures) has exactly the times T
+    g, q = synth.config1_tiny()
+    G = gpu_graph(tm, g)
+    f, v, t, _ = oracle.extract(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed)
+    assert f
+    T = [int(x) for x in t]
+    arcs = set(zip(g.src.tolist(), g.dst.tolist(), g.time.tolist()))
+    for seed in (1, 2, 3):
+        d, o = _ec_both(tm, G, g, q.k, q.multiset, T, seed=seed)
+        assert_same(d, o)
+        assert d.found
+        for method in ("localized", "halving"):
+            fe, ve, te = tm.tmotif_extract(G, q.k, q.multiset, seed=seed, timestamps=T, method=method)
+            assert fe and te.tolist() == T
+            assert len(set(ve.tolist())) == q.k
+            assert sorted(g.color[ve].tolist()) == sorted(q.multiset.tolist())
+            assert all((int(ve[r]), int(ve[r + 1]), T[r]) in arcs for r in range(q.k - 1))
+    # a tuple with the order of two times swapped is rejected; one shifted
+    # past every arc finds nothing
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide(G, q.k, q.multiset, timestamps=[T[1], T[0]] + T[2:])
+    assert e.value.code == 1
+    late = [1000 + i for i in range(q.k - 1)]
+    d, o = _ec_both(tm, G, g, q.k, q.multiset, late, seed=4)
+    assert_same(d, o)
+    assert not d.found and d.sieve_sum == 0
+    G.close()
+
+
+# ---------------------------------------------------------------------------
 # Full size (the benchmark workload): sampled points against the oracle
 # ---------------------------------------------------------------------------
 @pytest.fixture(scope="module")
