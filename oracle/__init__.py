@@ -83,6 +83,9 @@ def _load():
                                                u64, u32, P, P, P]),
             "or_decide": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u32, u32,
                                     u64, u32, u64, u64, P, P, P, C.c_int]),
+            "or_static_through": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u64, P,
+                                            C.c_int]),
+            "or_static_brute": (i64, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u64, C.c_int, P]),
             "or_decide_ec": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, P, u32, P, u32, u32, u32, u32,
                                        P, u64, u32, u64, u64, P, P, P, C.c_int]),
             "or_extract": (C.c_int, [u32, u64, P, P, P, C.c_int, P, u32, u32, P, u32, u32, u32, u32,
@@ -300,6 +303,57 @@ def decide_ec(n, src, dst, time, color, num_colors, k, multiset, timestamps, *, 
     if rc != 0:
         raise ValueError("oracle decide_ec: invalid input")
     return bool(found.value), int(q.value), pp[:npts]
+
+
+def static_through(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
+                   seed=1, alive=None, nthreads=0):
+    """Static preprocessing sieve (Sec. 7.1 (ii)): per-vertex sums Q_u over
+    the merged static graph; Q_u != 0 iff u lies on a static path with
+    colours M (w.h.p.).  Returns n uint64 values."""
+    src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
+    qv = np.zeros(max(n, 1), np.uint64)
+    al = None if alive is None else np.ascontiguousarray(np.asarray(alive, np.uint8))
+    rc = _load().or_static_through(n, len(src), _ptr(src), _ptr(dst), _ptr(time), int(bool(undirected)),
+                                   _ptr(color), num_colors, _ptr(al), k, _ptr(ms), start, end, seed, _ptr(qv),
+                                   nthreads)
+    if rc != 0:
+        raise ValueError("oracle static_through: invalid input")
+    return qv[:n]
+
+
+def static_brute(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
+                 seed=1, alive=None, det_mode=False):
+    """Static sums by walk enumeration (det_mode: via det(Z)).  Returns
+    (Q_u values, number of static walks)."""
+    src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
+    qv = np.zeros(max(n, 1), np.uint64)
+    al = None if alive is None else np.ascontiguousarray(np.asarray(alive, np.uint8))
+    nw = _load().or_static_brute(n, len(src), _ptr(src), _ptr(dst), _ptr(time), int(bool(undirected)),
+                                 _ptr(color), num_colors, _ptr(al), k, _ptr(ms), start, end, seed,
+                                 int(bool(det_mode)), _ptr(qv))
+    if nw < 0:
+        raise ValueError("oracle static_brute: invalid input")
+    return qv[:n], int(nw)
+
+
+def decide_preprocessed(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY,
+                        end=ANY, t_min=0, t_max=0, seed=1, repeats=1, point_begin=0, point_end=0, alive=None,
+                        timestamps=None, nthreads=0):
+    """Decision after the static preprocessing sieve: vertices with Q_u = 0
+    are removed (Sec. 7.1 (ii)), then the temporal sieve runs on the rest.
+    Returns (found, sieve_sum, per_point, keep_mask)."""
+    qv = static_through(n, src, dst, time, color, num_colors, k, multiset, undirected=undirected, start=start,
+                        end=end, seed=seed, alive=alive, nthreads=nthreads)
+    keep = qv != 0
+    if alive is not None:
+        keep &= np.asarray(alive, bool)
+    kw = dict(undirected=undirected, start=start, end=end, t_min=t_min, t_max=t_max, seed=seed, repeats=repeats,
+              point_begin=point_begin, point_end=point_end, alive=keep.astype(np.uint8), nthreads=nthreads)
+    if timestamps is None:
+        f, s, pp = decide(n, src, dst, time, color, num_colors, k, multiset, **kw)
+    else:
+        f, s, pp = decide_ec(n, src, dst, time, color, num_colors, k, multiset, timestamps, **kw)
+    return f, s, pp, keep
 
 
 def extract(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,

@@ -847,6 +847,250 @@ int or_decide(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Static preprocessing sieve (Sec. 7.1 (ii) with eq. gen-polynomial:1).     */
+/* The temporal graph is merged into the static graph                        */
+/*   E_s = {(a, b) : some canonical arc a -> b, at any time}.                */
+/* A vertex is kept iff it lies on at least one static path whose colours   */
+/* are M (first vertex = start and last = end when given).  Per point A:    */
+/*   F_1(u) = x_u [u start-ok],                                              */
+/*   F_l(u) = x_u sum_{(v,u) in E_s} yf(v->u, l-1) F_{l-1}(v),               */
+/*   B_1(u) = [u end-ok],                                                    */
+/*   B_l(u) = sum_{(u,w) in E_s} yb(u->w, k-l+1) x_w B_{l-1}(w),             */
+/*   Q_u^A  = sum_{r=1..k} F_r(u) B_{k-r+1}(u).                              */
+/* F_r(u) encodes the walk prefixes of r vertices that end at u, B_{k-r+1}(u) */
+/* the k-r vertices that follow u, so each product term is the monomial of  */
+/* a whole walk of k vertices with u at position r; the arc from position p */
+/* to p+1 carries yf before u and yb from u on.  Q_u = sum_A Q_u^A is       */
+/* non-zero (up to the sieve's one-sided error) iff such a walk is a path   */
+/* with colours M (Lemmas 5.2-5.5 applied to each vertex's terms).          */
+/*   yf(a->b, p) = mix64(mix64(kf ^ (a<<32 | b)) ^ p), kf = mix64(qs ^ 0x4444..44) */
+/*   yb(a->b, p) = mix64(mix64(kb ^ (a<<32 | b)) ^ p), kb = mix64(qs ^ 0x5555..55) */
+/* ------------------------------------------------------------------------ */
+#define OR_TAG_YF 0x4444444444444444ull
+#define OR_TAG_YB 0x5555555555555555ull
+
+static u64 or_static_y(u64 qs, u64 tag, u32 a, u32 b, u32 p)
+{
+    u64 key = or_fmix64(qs ^ tag);
+    return or_fmix64(or_fmix64(key ^ (((u64)a << 32) | b)) ^ (u64)p);
+}
+
+static int or_u64_cmp(const void *x, const void *y)
+{
+    u64 a = *(const u64 *)x, b = *(const u64 *)y;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* Distinct pairs (a << 32 | b) of the canonical arcs, ascending. */
+static u64 or_static_pairs(const or_problem *P, u64 *pairs)
+{
+    for (u64 e = 0; e < P->m; e++) pairs[e] = ((u64)P->src[e] << 32) | P->dst[e];
+    qsort(pairs, P->m, sizeof(u64), or_u64_cmp);
+    u64 w = 0;
+    for (u64 e = 0; e < P->m; e++)
+        if (w == 0 || pairs[w - 1] != pairs[e]) pairs[w++] = pairs[e];
+    return w;
+}
+
+static int or_static_core(const or_problem *P, u64 qs, u64 *Qv)
+{
+    u32 k = P->k, n = P->n;
+    u32 *sb = (u32 *)malloc(sizeof(u32) * (P->num_colors + 1));
+    u32 *sc = (u32 *)malloc(sizeof(u32) * (P->num_colors + 1));
+    u64 *pairs = (u64 *)malloc(sizeof(u64) * (P->m ? P->m : 1));
+    if (!sb || !sc || !pairs || or_slots(k, P->multiset, P->num_colors, sb, sc) != 0) {
+        free(sb); free(sc); free(pairs);
+        return -1;
+    }
+    u64 ms = or_static_pairs(P, pairs);
+    memset(Qv, 0, sizeof(u64) * n);
+    int err = 0;
+    i64 npts = (i64)1 << k;
+#pragma omp parallel
+    {
+        u64 *x = (u64 *)malloc(sizeof(u64) * (n ? n : 1));
+        u64 *F = (u64 *)malloc(sizeof(u64) * (size_t)(k + 1) * (n ? n : 1)); /* F[l*n + u] */
+        u64 *B = (u64 *)malloc(sizeof(u64) * (size_t)(k + 1) * (n ? n : 1)); /* B[l*n + u] */
+        u64 *acc = (u64 *)calloc(n ? n : 1, sizeof(u64));
+        if (!x || !F || !B || !acc) {
+#pragma omp atomic write
+            err = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (i64 pt = 0; pt < npts; pt++) {
+            if (!x || !F || !B || !acc) continue;
+            or_all_x(P, qs, sb, sc, (u64)pt, x);
+            memset(F, 0, sizeof(u64) * (size_t)(k + 1) * n);
+            memset(B, 0, sizeof(u64) * (size_t)(k + 1) * n);
+            for (u32 u = 0; u < n; u++) {
+                F[1 * (size_t)n + u] = (P->start == OR_ANY || P->start == u) ? x[u] : 0;
+                B[1 * (size_t)n + u] = (P->end == OR_ANY || P->end == u) ? 1 : 0;
+            }
+            for (u32 l = 2; l <= k; l++) {
+                for (u64 e = 0; e < ms; e++) {
+                    u32 a = (u32)(pairs[e] >> 32), b = (u32)pairs[e];
+                    /* forward: arc a -> b enters the l-th vertex b */
+                    F[(size_t)l * n + b] ^= or_gf_mul(or_static_y(qs, OR_TAG_YF, a, b, l - 1),
+                                                      F[(size_t)(l - 1) * n + a]);
+                    /* backward: a at position k-l+1 followed by b */
+                    B[(size_t)l * n + a] ^= or_gf_mul(or_static_y(qs, OR_TAG_YB, a, b, k - l + 1),
+                                                      or_gf_mul(x[b], B[(size_t)(l - 1) * n + b]));
+                }
+                for (u32 u = 0; u < n; u++) F[(size_t)l * n + u] = or_gf_mul(x[u], F[(size_t)l * n + u]);
+            }
+            for (u32 u = 0; u < n; u++) {
+                u64 q = 0;
+                for (u32 r = 1; r <= k; r++)
+                    q ^= or_gf_mul(F[(size_t)r * n + u], B[(size_t)(k - r + 1) * n + u]);
+                acc[u] ^= q;
+            }
+        }
+#pragma omp critical
+        {
+            if (acc)
+                for (u32 u = 0; u < n; u++) Qv[u] ^= acc[u];
+        }
+        free(x); free(F); free(B); free(acc);
+    }
+    free(sb); free(sc); free(pairs);
+    return err ? -1 : 0;
+}
+
+/* Public: per-vertex static sums Q_u (n values) from the raw edge list, with */
+/* the query seed of repeat 0.                                                */
+int or_static_through(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int undirected,
+                      const u32 *color, u32 num_colors, const uint8_t *alive, u32 k, const u32 *multiset,
+                      u32 start, u32 end, u64 seed, u64 *Qv, int nthreads)
+{
+    if (or_check_query(n, color, num_colors, k, multiset, start, end) != 0) return -1;
+    u64 cap = (undirected ? 2 * m : m) + 1;
+    u32 *cs = (u32 *)malloc(sizeof(u32) * cap), *cd = (u32 *)malloc(sizeof(u32) * cap), *ct = (u32 *)malloc(sizeof(u32) * cap);
+    i64 mc = or_canon(n, m, src, dst, time, undirected, cs, cd, ct);
+    int r = -1;
+    if (mc >= 0) {
+        or_problem P;
+        or_fill_problem(&P, n, (u64)mc, cs, cd, ct, color, num_colors, alive, k, multiset, start, end, 0, 0);
+#ifdef _OPENMP
+        int old = omp_get_max_threads();
+        if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+        r = or_static_core(&P, or_query_seed(seed, 0), Qv);
+#ifdef _OPENMP
+        if (nthreads > 0) omp_set_num_threads(old);
+#endif
+    }
+    (void)nthreads;
+    free(cs); free(cd); free(ct);
+    return r;
+}
+
+/* Brute force for the static sums: enumerate every static walk of k        */
+/* vertices over E_s (from start, to end when given) and, for each position */
+/* r of each walk, add to Q_{w_r} either                                     */
+/*   det_mode 0: the sum over all 2^k points of the walk's monomial with the  */
+/*               yf / yb split at r, or                                       */
+/*   det_mode 1: (product of the split y's) * det(Z_walk), the same sum by   */
+/*               the characteristic-2 identity sum_A prod_r z^A = det(Z).     */
+/* Exponential: tiny graphs only.  Returns the number of walks.               */
+typedef struct {
+    const or_problem *P;
+    const u64 *pairs;
+    u64 ms, qs;
+    const u32 *sb, *sc;
+    const u64 *xs; /* 2^k points x n */
+    int det_mode;
+    u32 walk[OR_KMAX];
+    u64 nwalks;
+    u64 *Qv;
+} or_senum;
+
+static void or_static_walk_done(or_senum *E)
+{
+    const or_problem *P = E->P;
+    u32 k = P->k, n = P->n;
+    if (P->end != OR_ANY && E->walk[k - 1] != P->end) return;
+    E->nwalks++;
+    u64 det = 0;
+    if (E->det_mode) {
+        u64 Z[OR_KMAX * OR_KMAX];
+        for (u32 r = 0; r < k; r++) {
+            u32 u = E->walk[r], c = P->color[u];
+            int dead = (P->alive && !P->alive[u]);
+            for (u32 j = 0; j < k; j++) {
+                u64 z = 0;
+                if (!dead)
+                    for (u32 d = E->sb[c]; d < E->sb[c] + E->sc[c]; d++)
+                        z ^= or_gf_mul(or_coef_v(E->qs, u, d), or_coef_w(E->qs, d, j));
+                Z[r * k + j] = z;
+            }
+        }
+        det = or_det(Z, k);
+    }
+    for (u32 r = 1; r <= k; r++) { /* u = walk[r-1] at position r */
+        u64 yprod = 1;
+        for (u32 p = 1; p < k; p++) {
+            u64 tag = p < r ? OR_TAG_YF : OR_TAG_YB;
+            yprod = or_gf_mul(yprod, or_static_y(E->qs, tag, E->walk[p - 1], E->walk[p], p));
+        }
+        u64 sum = 0;
+        if (E->det_mode) {
+            sum = or_gf_mul(yprod, det);
+        } else {
+            for (u64 pt = 0; pt < ((u64)1 << k); pt++) {
+                u64 mono = yprod;
+                for (u32 i = 0; i < k; i++) mono = or_gf_mul(mono, E->xs[pt * n + E->walk[i]]);
+                sum ^= mono;
+            }
+        }
+        E->Qv[E->walk[r - 1]] ^= sum;
+    }
+}
+
+static void or_static_walk_rec(or_senum *E, u32 depth)
+{
+    if (depth == E->P->k) { or_static_walk_done(E); return; }
+    u32 cur = E->walk[depth - 1];
+    for (u64 e = 0; e < E->ms; e++) {
+        if ((u32)(E->pairs[e] >> 32) != cur) continue;
+        E->walk[depth] = (u32)E->pairs[e];
+        or_static_walk_rec(E, depth + 1);
+    }
+}
+
+i64 or_static_brute(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int undirected,
+                    const u32 *color, u32 num_colors, const uint8_t *alive, u32 k, const u32 *multiset, u32 start,
+                    u32 end, u64 seed, int det_mode, u64 *Qv)
+{
+    if (or_check_query(n, color, num_colors, k, multiset, start, end) != 0) return -1;
+    u64 cap = (undirected ? 2 * m : m) + 1;
+    u32 *cs = (u32 *)malloc(sizeof(u32) * cap), *cd = (u32 *)malloc(sizeof(u32) * cap), *ct = (u32 *)malloc(sizeof(u32) * cap);
+    i64 mc = or_canon(n, m, src, dst, time, undirected, cs, cd, ct);
+    if (mc < 0) { free(cs); free(cd); free(ct); return -1; }
+    or_problem P;
+    or_fill_problem(&P, n, (u64)mc, cs, cd, ct, color, num_colors, alive, k, multiset, start, end, 0, 0);
+    u32 *sb = (u32 *)malloc(sizeof(u32) * (num_colors + 1));
+    u32 *sc = (u32 *)malloc(sizeof(u32) * (num_colors + 1));
+    u64 *pairs = (u64 *)malloc(sizeof(u64) * (P.m ? P.m : 1));
+    or_slots(k, multiset, num_colors, sb, sc);
+    u64 qs = or_query_seed(seed, 0);
+    u64 npts = (u64)1 << k;
+    u64 *xs = (u64 *)malloc(sizeof(u64) * (size_t)npts * (n ? n : 1));
+    for (u64 pt = 0; pt < npts; pt++) or_all_x(&P, qs, sb, sc, pt, xs + pt * n);
+    or_senum E;
+    memset(&E, 0, sizeof(E));
+    E.P = &P; E.pairs = pairs; E.ms = or_static_pairs(&P, pairs); E.qs = qs; E.sb = sb; E.sc = sc;
+    E.xs = xs; E.det_mode = det_mode; E.Qv = Qv;
+    memset(Qv, 0, sizeof(u64) * n);
+    for (u32 u = 0; u < n; u++) {
+        if (start != OR_ANY && start != u) continue;
+        E.walk[0] = u;
+        or_static_walk_rec(&E, 1);
+    }
+    free(xs); free(sb); free(sc); free(pairs); free(cs); free(cd); free(ct);
+    return (i64)E.nwalks;
+}
+
+/* ------------------------------------------------------------------------ */
 /* EC-PathMotif (Sec. 6.3): the path's arc times must equal the tuple        */
 /* T = (j_1, ..., j_{k-1}), j_1 < ... < j_{k-1}.  The recurrence there keeps */
 /* one value per vertex and walk length, with no "stay" term:               */
