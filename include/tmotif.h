@@ -44,6 +44,13 @@ extern "C" {
 /* tmotif_query.flags: extract an optimum solution -- a path whose latest arc
  * time is the least possible (tmotif_optimum_time), as in Sec. 5.8-5.9. */
 #define TMOTIF_EXTRACT_OPTIMUM 2u
+/* tmotif_query.flags: static preprocessing sieve first (Sec. 7.1 (ii); see
+ * tmotif_static_sieve): decide / extract / optimum time / localise on the
+ * temporal graph restricted to the vertices it keeps.  Every temporal match
+ * survives, so decisions are unchanged; per-point sums are those of the
+ * restricted graph.  Not accepted by tmotif_decide_batch or tmotif_submit
+ * (UNSUPPORTED). */
+#define TMOTIF_PREPROCESS_STATIC 4u
 
 enum {
     TMOTIF_OK = 0,
@@ -87,7 +94,8 @@ typedef struct {
  *   point_begin, point_end  0,0 = all 2^k sieve points; otherwise only the
  *                 points [point_begin, point_end) are evaluated (sharding a
  *                 query across devices; combine the per-point sums by XOR);
- *   flags         0 or TMOTIF_EXTRACT_HALVING and/or TMOTIF_EXTRACT_OPTIMUM;
+ *   flags         0 or TMOTIF_EXTRACT_HALVING, TMOTIF_EXTRACT_OPTIMUM and/or
+ *                 TMOTIF_PREPROCESS_STATIC;
  *   timestamps    NULL, or the EC-PathMotif tuple T = (j_1, ..., j_{k-1}) of
  *                 Sec. 6.3 (caller-owned host array of k-1 strictly increasing
  *                 times >= 1; INVALID otherwise): the path's l-th arc must have
@@ -192,6 +200,21 @@ int tmotif_optimum_time(tmotif_graph_t g, const tmotif_query *q, uint32_t *t_opt
  * when (w.h.p.) a matching temporal path ends at u; out receives the whole
  * decision (first repeat; repeats are ignored).  Errors as tmotif_decide. */
 int tmotif_localize(tmotif_graph_t g, const tmotif_query *q, uint64_t *per_vertex, tmotif_decision *out);
+
+/* Static preprocessing sieve (Sec. 7.1 (ii), static generating function
+ * eq. gen-polynomial:1).  The temporal arcs are merged into the static graph
+ * E_s = {(a, b) : some arc a -> b}; per_vertex[u] (caller-owned, n values, or
+ * NULL) receives Q_u = sum over the 2^k points A of
+ *   sum_{r=1..k} F_r(u) B_{k-r+1}(u),
+ *   F_1(u) = x_u [u start-ok], F_l(u) = x_u sum_{(v,u)} yf(v->u, l-1) F_{l-1}(v),
+ *   B_1(u) = [u end-ok],      B_l(u) = sum_{(u,w)} yb(u->w, k-l+1) x_w B_{l-1}(w),
+ * with yf(a->b, p) = mix64(mix64(kf ^ (a << 32 | b)) ^ p), yb likewise with
+ * kb, kf = mix64(qs ^ 0x4444444444444444), kb = mix64(qs ^ 0x5555555555555555)
+ * and qs the repeat-0 query seed: nonzero exactly when (w.h.p.) u lies on a
+ * static path with colours M (start/end as given).  kept (optional)
+ * receives the number of such vertices.  The time window and EC timestamps
+ * do not restrict E_s.  Errors as tmotif_decide. */
+int tmotif_static_sieve(tmotif_graph_t g, const tmotif_query *q, uint64_t *per_vertex, uint32_t *kept);
 
 /* Decide many (graph, query) pairs in one pass: every query runs its sieve
  * and the per-query phases of all of them share persistent launches (the

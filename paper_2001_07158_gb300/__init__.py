@@ -22,6 +22,7 @@ TMOTIF_ANY = 0xFFFFFFFF
 TMOTIF_KMAX = 20
 TMOTIF_EXTRACT_HALVING = 1
 TMOTIF_EXTRACT_OPTIMUM = 2
+TMOTIF_PREPROCESS_STATIC = 4
 ERRORS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "NOT_FOUND", 7: "BUSY"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -75,6 +76,7 @@ def _load():
         "tmotif_decide": (C.c_int, [P, C.POINTER(_Query), C.POINTER(_Decision)]),
         "tmotif_extract": (C.c_int, [P, C.POINTER(_Query), P, P, C.POINTER(C.c_int)]),
         "tmotif_localize": (C.c_int, [P, C.POINTER(_Query), P, C.POINTER(_Decision)]),
+        "tmotif_static_sieve": (C.c_int, [P, C.POINTER(_Query), P, C.POINTER(C.c_uint32)]),
         "tmotif_optimum_time": (C.c_int, [P, C.POINTER(_Query), C.POINTER(C.c_uint32), C.POINTER(C.c_int)]),
         "tmotif_decide_batch": (C.c_int, [P, P, C.c_uint32, P]),
         "tmotif_server_create": (C.c_int, [C.c_size_t, C.POINTER(P)]),
@@ -179,11 +181,13 @@ def _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, po
 
 
 def tmotif_decide(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                  repeats=1, point_begin=0, point_end=0, per_point=True, timestamps=None) -> Decision:
+                  repeats=1, point_begin=0, point_end=0, per_point=True, timestamps=None,
+                  preprocess=False) -> Decision:
     """PathMotif decision; with `timestamps` (k-1 strictly increasing times)
-    the EC-PathMotif decision of Sec. 6.3."""
+    the EC-PathMotif decision of Sec. 6.3; with `preprocess` the static
+    preprocessing sieve first (TMOTIF_PREPROCESS_STATIC)."""
     q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end,
-                     timestamps=timestamps)
+                     TMOTIF_PREPROCESS_STATIC if preprocess else 0, timestamps)
     npts = (1 << k) if point_end == 0 else max(point_end - point_begin, 0)
     pp = np.zeros(max(npts, 1), np.uint64) if per_point else None
     d = _Decision(0, 0, pp.ctypes.data if per_point else None, 0.0)
@@ -192,11 +196,12 @@ def tmotif_decide(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_
 
 
 def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                   repeats=1, method="localized", optimum=False, timestamps=None):
+                   repeats=1, method="localized", optimum=False, timestamps=None, preprocess=False):
     """method: "localized" (default) or "halving" (TMOTIF_EXTRACT_HALVING);
     optimum: extract a path with the least latest time (TMOTIF_EXTRACT_OPTIMUM);
     timestamps: the EC-PathMotif tuple (Sec. 6.3), or None."""
     flags = (TMOTIF_EXTRACT_HALVING if method == "halving" else 0) | (TMOTIF_EXTRACT_OPTIMUM if optimum else 0)
+    flags |= TMOTIF_PREPROCESS_STATIC if preprocess else 0
     q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags, timestamps)
     verts = np.zeros(k, np.uint32)
     times = np.zeros(max(k - 1, 1), np.uint32)
@@ -206,9 +211,10 @@ def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t
 
 
 def tmotif_optimum_time(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                        repeats=1, timestamps=None):
+                        repeats=1, timestamps=None, preprocess=False):
     """Optimum timestamp (Sec. 5.8): (found, least t' with a path in [t_min, t'])."""
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, timestamps=timestamps)
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0,
+                     TMOTIF_PREPROCESS_STATIC if preprocess else 0, timestamps)
     t = C.c_uint32(0)
     f = C.c_int(0)
     _check(_lib.tmotif_optimum_time(g.handle, C.byref(q), C.byref(t), C.byref(f)))
@@ -216,13 +222,24 @@ def tmotif_optimum_time(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_A
 
 
 def tmotif_localize(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
-                    timestamps=None):
+                    timestamps=None, preprocess=False):
     """Vertex-localised sieve: (decision, per_vertex Q_u for every vertex)."""
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, 1, 0, 0, timestamps=timestamps)
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, 1, 0, 0,
+                     TMOTIF_PREPROCESS_STATIC if preprocess else 0, timestamps)
     pv = np.zeros(max(g.n, 1), np.uint64)
     d = _Decision(0, 0, None, 0.0)
     _check(_lib.tmotif_localize(g.handle, C.byref(q), pv.ctypes.data, C.byref(d)))
     return Decision(bool(d.found), int(d.sieve_sum), None, float(d.ms)), pv[:g.n]
+
+
+def tmotif_static_sieve(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, seed=1):
+    """Static preprocessing sieve (Sec. 7.1 (ii)): (per-vertex Q_u, number of
+    kept vertices); Q_u != 0 iff u lies on a static path with colours M."""
+    q, keep = _query(k, multiset, start, end, 0, 0, seed, 1, 0, 0)
+    qv = np.zeros(max(g.n, 1), np.uint64)
+    kept = C.c_uint32(0)
+    _check(_lib.tmotif_static_sieve(g.handle, C.byref(q), qv.ctypes.data, C.byref(kept)))
+    return qv[:g.n], int(kept.value)
 
 
 def tmotif_decide_batch(graphs, queries):
@@ -239,7 +256,7 @@ def tmotif_decide_batch(graphs, queries):
         ms = qd.pop("multiset")
         q, kp = _query(k, ms, qd.get("start", TMOTIF_ANY), qd.get("end", TMOTIF_ANY), qd.get("t_min", 0),
                        qd.get("t_max", 0), qd.get("seed", 1), qd.get("repeats", 1), 0, 0,
-                       timestamps=qd.get("timestamps"))
+                       TMOTIF_PREPROCESS_STATIC if qd.get("preprocess") else 0, qd.get("timestamps"))
         qarr[i] = q
         keep.append(kp)
         pp = np.zeros(1 << k, np.uint64)
@@ -327,8 +344,9 @@ def tmotif_server_create(hbm_budget_bytes: int) -> Server:
 
 
 def tmotif_submit(s: Server, g: Graph, k, multiset, *, is_extract=False, start=TMOTIF_ANY, end=TMOTIF_ANY,
-                  t_min=0, t_max=0, seed=1, repeats=1, method="localized", timestamps=None) -> int:
-    flags = TMOTIF_EXTRACT_HALVING if method == "halving" else 0
+                  t_min=0, t_max=0, seed=1, repeats=1, method="localized", timestamps=None,
+                  preprocess=False) -> int:
+    flags = (TMOTIF_EXTRACT_HALVING if method == "halving" else 0) | (TMOTIF_PREPROCESS_STATIC if preprocess else 0)
     q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags, timestamps)
     t = C.c_uint64(0)
     _check(_lib.tmotif_submit(s.handle, g.handle, C.byref(q), int(bool(is_extract)), C.byref(t)))

@@ -280,6 +280,12 @@ void release_graph_arrays(Graph *g)
     dev_free(g->d_time, g->stream);
     dev_free(g->d_color, g->stream);
     g->d_src = g->d_dst = g->d_time = g->d_color = nullptr;
+    dev_free(g->s_in, g->stream);
+    dev_free(g->s_out, g->stream);
+    g->s_in = g->s_out = nullptr;
+    g->s_built = false;
+    g->m_static = 0;
+    g->sw.release();
     g->ws.release();
     cudaStreamSynchronize(g->stream);
     g->prof.destroy();
@@ -384,6 +390,50 @@ int tmotif_graph_get_info(tmotif_graph_t g, tmotif_graph_info *info)
     return TMOTIF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// With TMOTIF_PREPROCESS_STATIC: the static sieve's kept vertices and the
+// graph of the arcs among them (same vertex ids; Sec. 7.1 (ii) rebuilds the
+// temporal graph on those vertices).  Otherwise the graph itself.
+struct Prepared {
+    Graph *g = nullptr;
+    std::unique_ptr<Graph, void (*)(Graph *)> sub{nullptr, [](Graph *x) {
+                                                      release_graph_arrays(x);
+                                                      delete x;
+                                                  }};
+    double ms = 0;
+};
+
+Status prepare(Graph &g, const QuerySpec &q, Prepared *p)
+{
+    p->g = &g;
+    if (!(q.flags & TMOTIF_PREPROCESS_STATIC)) return Status();
+    cudaEvent_t e0, e1;
+    TM_CUDA(cudaEventCreate(&e0));
+    TM_CUDA(cudaEventCreate(&e1));
+    TM_CUDA(cudaEventRecord(e0, g.stream));
+    g.sw.set_stream(g.stream);
+    TM_TRY(g.sw.mask.reserve(std::max<u32>(g.n, 1)));
+    TM_TRY(static_mask(g, q, nullptr, g.sw.mask.as<uint8_t>(), nullptr));
+    p->sub.reset(new Graph());
+    TM_TRY(make_subgraph(g, g.ws, g.stream, g.sw.mask.as<uint8_t>(), p->sub.get()));
+    TM_CUDA(cudaEventRecord(e1, g.stream));
+    TM_CUDA(cudaEventSynchronize(e1));
+    float f = 0;
+    cudaEventElapsedTime(&f, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->ms = f;
+    p->g = p->sub.get();
+    return Status();
+}
+
+}  // namespace
+
+extern "C" {
+
 int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out)
 {
     if (!g || !out) return fail(TMOTIF_ERR_INVALID, "null argument").code;
@@ -391,14 +441,17 @@ int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out)
         QuerySpec qs;
         Status s = parse_query(*g, q, &qs);
         if (!s.ok()) return s.code;
+        Prepared pre;
+        s = prepare(*g, qs, &pre);
+        if (!s.ok()) return s.code;
         int found = 0;
         u64 sum = 0;
         double ms = 0;
-        s = sieve_decide(*g, qs, nullptr, &found, &sum, (u64 *)out->per_point, &ms);
+        s = sieve_decide(*pre.g, qs, nullptr, &found, &sum, (u64 *)out->per_point, &ms);
         if (!s.ok()) return s.code;
         out->found = found;
         out->sieve_sum = sum;
-        out->ms = ms;
+        out->ms = ms + pre.ms;
         return TMOTIF_OK;
     } catch (const std::bad_alloc &) {
         return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
@@ -414,10 +467,14 @@ int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uin
         if (!s.ok()) return s.code;
         if (qs.p_begin != 0 || qs.p_end != (1ull << qs.k))
             return fail(TMOTIF_ERR_INVALID, "extraction needs the full point range").code;
+        Prepared pre;
+        s = prepare(*g, qs, &pre);
+        if (!s.ok()) return s.code;
+        Graph &G = *pre.g;
         if (qs.flags & TMOTIF_EXTRACT_OPTIMUM) {
             u32 t_opt = 0;
             int any = 0;
-            s = optimum_time(*g, qs, &t_opt, &any);
+            s = optimum_time(G, qs, &t_opt, &any);
             if (!s.ok()) return s.code;
             if (!any) {
                 *found = 0;
@@ -427,9 +484,9 @@ int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uin
         }
         if (qs.flags & TMOTIF_EXTRACT_HALVING) {
             u32 probes = 0;
-            s = extract_path(*g, qs, verts, times, found, &probes);
+            s = extract_path(G, qs, verts, times, found, &probes);
         } else {
-            s = extract_localized(*g, qs, verts, times, found);
+            s = extract_localized(G, qs, verts, times, found);
         }
         return s.code;
     } catch (const std::bad_alloc &) {
@@ -446,7 +503,10 @@ int tmotif_optimum_time(tmotif_graph_t g, const tmotif_query *q, uint32_t *t_opt
         if (!s.ok()) return s.code;
         if (qs.p_begin != 0 || qs.p_end != (1ull << qs.k))
             return fail(TMOTIF_ERR_INVALID, "the optimum time needs the full point range").code;
-        return optimum_time(*g, qs, t_opt, found).code;
+        Prepared pre;
+        s = prepare(*g, qs, &pre);
+        if (!s.ok()) return s.code;
+        return optimum_time(*pre.g, qs, t_opt, found).code;
     } catch (const std::bad_alloc &) {
         return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
     }
@@ -461,15 +521,48 @@ int tmotif_localize(tmotif_graph_t g, const tmotif_query *q, uint64_t *per_verte
         if (!s.ok()) return s.code;
         if (qs.p_begin != 0 || qs.p_end != (1ull << qs.k))
             return fail(TMOTIF_ERR_INVALID, "localisation needs the full point range").code;
+        Prepared pre;
+        s = prepare(*g, qs, &pre);
+        if (!s.ok()) return s.code;
         int found = 0;
         u64 sum = 0;
         double ms = 0;
-        s = sieve_localize(*g, qs, (u64 *)per_vertex, &found, &sum, &ms);
+        s = sieve_localize(*pre.g, qs, (u64 *)per_vertex, &found, &sum, &ms);
         if (!s.ok()) return s.code;
         out->found = found;
         out->sieve_sum = sum;
-        out->ms = ms;
+        out->ms = ms + pre.ms;
         return TMOTIF_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
+}
+
+int tmotif_static_sieve(tmotif_graph_t g, const tmotif_query *q, uint64_t *per_vertex, uint32_t *kept)
+{
+    if (!g) return fail(TMOTIF_ERR_INVALID, "null graph").code;
+    try {
+        QuerySpec qs;
+        Status s = parse_query(*g, q, &qs);
+        if (!s.ok()) return s.code;
+        g->sw.set_stream(g->stream);
+        s = g->sw.qv.reserve(std::max<u32>(g->n, 1) * 8ull);
+        if (!s.ok()) return s.code;
+        s = static_sieve(*g, qs, nullptr, g->sw.qv.as<u64>(), nullptr);
+        if (!s.ok()) return s.code;
+        std::vector<u64> h(g->n);
+        if (g->n) {
+            cudaError_t e = cudaMemcpyAsync(h.data(), g->sw.qv.p, (u64)g->n * 8, cudaMemcpyDeviceToHost, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "static sieve readback").code;
+        }
+        if (per_vertex && g->n) std::memcpy(per_vertex, h.data(), (u64)g->n * 8);
+        if (kept) {
+            u32 c = 0;
+            for (u64 v : h) c += v != 0;
+            *kept = c;
+        }
+        return g->prof.collect().code;
     } catch (const std::bad_alloc &) {
         return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
     }

@@ -179,6 +179,32 @@ struct Tmp {
 
 }  // namespace
 
+// Stable LSD radix sort of N 64-bit keys on their low `bits` bits (8-bit
+// digits); a and b are N-key buffers, *sorted points at the one holding the
+// result.  d_scratch: one device u32.
+Status radix_sort_u64(cudaStream_t st, u64 *a, u64 *b, u64 N, int bits, u32 *d_scratch, u64 **sorted,
+                      u64 *launches)
+{
+    *sorted = a;
+    if (N <= 1) return Status();
+    const u32 ntiles = (u32)std::max<u64>(1, (N + RS_TILE - 1) / RS_TILE);
+    Tmp hist(st);
+    DevBuf tiles;
+    tiles.stream = st;
+    TM_TRY(hist.get((u64)256 * ntiles * 4));
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<<<ntiles, RS_THREADS, 0, st>>>(a, N, shift, ntiles, hist.as<u32>());
+        TM_TRY(exclusive_scan_on(st, tiles, hist.as<u32>(), (u64)256 * ntiles, d_scratch, launches));
+        k_radix_scatter<<<ntiles, RS_THREADS, 0, st>>>(a, N, shift, ntiles, hist.as<u32>(), b);
+        TM_CUDA(cudaGetLastError());
+        if (launches) *launches += 2;
+        std::swap(a, b);
+    }
+    tiles.release();
+    *sorted = a;
+    return Status();
+}
+
 Status build_graph_device(const tmotif_graph_desc *d, Graph *g, bool *done)
 {
     *done = false;
@@ -232,19 +258,9 @@ Status build_graph_device(const tmotif_graph_desc *d, Graph *g, bool *done)
 
     // LSD radix sort over the bits in use plus the sentinel bit.
     const int bits = ks.total() + 1;
-    const u32 ntiles = (u32)std::max<u64>(1, (N + RS_TILE - 1) / RS_TILE);
-    TM_TRY(hist.get((u64)256 * ntiles * 4));
-    u64 *a = keys.as<u64>(), *b = keys2.as<u64>();
+    u64 *a = nullptr;
     u64 launches = 0;
-    if (N > 1) {
-        for (int shift = 0; shift < bits; shift += 8) {
-            k_radix_hist<<<ntiles, RS_THREADS, 0, st>>>(a, N, shift, ntiles, hist.as<u32>());
-            TM_TRY(exclusive_scan_on(st, tiles, hist.as<u32>(), (u64)256 * ntiles, d_small + 2, &launches));
-            k_radix_scatter<<<ntiles, RS_THREADS, 0, st>>>(a, N, shift, ntiles, hist.as<u32>(), b);
-            TM_CUDA(cudaGetLastError());
-            std::swap(a, b);
-        }
-    }
+    TM_TRY(radix_sort_u64(st, keys.as<u64>(), keys2.as<u64>(), N, bits, d_small + 2, &a, &launches));
     // dedupe (E^tau is a set), drop sentinels, unpack
     TM_TRY(flag.get((N + 1) * 4));
     k_unique<<<grid(N + 1, 256), 256, 0, st>>>(a, N, 1ull << ks.total(), flag.as<u32>());

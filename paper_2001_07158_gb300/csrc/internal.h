@@ -103,6 +103,17 @@ struct Workspace {
     void set_stream(cudaStream_t s);
 };
 
+// Per-graph scratch of the static preprocessing sieve (grown on demand).
+struct StaticWork {
+    DevBuf keep;      // pairs + 1 u32: filter flags, then offsets
+    DevBuf in, out;   // filtered pair lists (owner array, then other array)
+    DevBuf arrays;    // F_2..F_k, B_2..B_k, two x*B buffers: n x L u64 each
+    DevBuf qv;        // n u64: per-vertex sums Q_u
+    DevBuf mask;      // n bytes: kept vertices
+    void set_stream(cudaStream_t s);
+    void release();
+};
+
 struct Graph {
     u32 n = 0;
     u64 m_input = 0, m = 0;             // canonical arcs
@@ -118,6 +129,12 @@ struct Graph {
     Workspace ws;
     Profiler prof;
     size_t resident_bytes = 0;
+    // static graph E_s (built on first use): s_in = [dst | src] sorted by
+    // (dst, src), s_out = [src | dst] sorted by (src, dst), m_static pairs each
+    bool s_built = false;
+    u64 m_static = 0;
+    u32 *s_in = nullptr, *s_out = nullptr;
+    StaticWork sw;
 };
 
 // Arc filter of a query, passed by value to the filter kernel: the time
@@ -299,6 +316,19 @@ Status optimum_time(Graph &g, const QuerySpec &q, u32 *t_opt, int *found);
 Status extract_localized(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *found);
 
 Status build_graph(const tmotif_graph_desc *d, Graph *g);
+// Stable LSD radix sort of N 64-bit keys on their low `bits` bits; a and b
+// hold N keys each, *sorted points at the one with the result.
+Status radix_sort_u64(cudaStream_t st, u64 *a, u64 *b, u64 N, int bits, u32 *d_scratch, u64 **sorted,
+                      u64 *launches);
+
+// Static preprocessing sieve (Sec. 7.1 (ii)): the static graph of g (built
+// once), then per-vertex sums Q_u (device, n u64) for the query: nonzero iff
+// u lies on a static path with colours M.  kept_pairs (optional) receives
+// the number of static pairs among the query's vertices.
+Status static_graph_ensure(Graph &g);
+Status static_sieve(Graph &g, const QuerySpec &q, const uint8_t *d_alive, u64 *d_Qv, u64 *kept_pairs);
+// d_mask[u] = (Q_u != 0), device n bytes.
+Status static_mask(Graph &g, const QuerySpec &q, const uint8_t *d_alive, uint8_t *d_mask, u64 *kept_pairs);
 // Device build; *done = false (and no error) when the packed arc key would not
 // fit 64 bits, in which case the caller builds on the host.
 Status build_graph_device(const tmotif_graph_desc *d, Graph *g, bool *done);

@@ -227,6 +227,8 @@ extern "C" int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_qu
             if (!graphs[i]) return fail(TMOTIF_ERR_INVALID, "null graph in batch").code;
             Status s = parse_query(*graphs[i], &queries[i], &specs[i]);
             if (!s.ok()) return s.code;
+            if (specs[i].flags & TMOTIF_PREPROCESS_STATIC)
+                return fail(TMOTIF_ERR_UNSUPPORTED, "batched decisions take no static preprocessing").code;
             if (graphs[i]->stream != graphs[0]->stream)
                 return fail(TMOTIF_ERR_INVALID, "graphs of one batch must share a stream").code;
         }
@@ -524,6 +526,8 @@ extern "C" int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_q
         auto r = std::make_unique<Request>();
         Status st = parse_query(*g, q, &r->q);
         if (!st.ok()) return st.code;
+        if (r->q.flags & TMOTIF_PREPROCESS_STATIC)
+            return fail(TMOTIF_ERR_UNSUPPORTED, "the server takes no static preprocessing").code;
         if (is_extract && (r->q.p_begin != 0 || r->q.p_end != (1ull << r->q.k)))
             return fail(TMOTIF_ERR_INVALID, "extraction needs the full point range").code;
         if (job_estimate(*g, r->q) > s->budget)
