@@ -74,6 +74,11 @@ def parse_args():
     p.add_argument("--serving-requests", type=int, default=32)
     p.add_argument("--scale", type=float, default=1.0,
                    help="scale n and m of the workload (profiling captures of a smaller case)")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="mid",
+                   help="mid: the default decision (n=1e6, m=1e7, k=6); large5 / large10: power-law "
+                        "n=1e7 with m=5e8, k=5 / m=1e8, k=10; batch: 10,000 small tour graphs in one "
+                        "batched call (k in 5..8)")
+    p.add_argument("--preprocess", action="store_true", help="static preprocessing sieve before each decision")
     return p.parse_args()
 
 
@@ -141,9 +146,23 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def workload(scale=1.0):
+WORKLOADS = {
+    "mid": WORKLOAD,
+    "large5": "power-law out-degree 2.1, n=1e7, m=5e8, t in [1,1e4], 32 uniform colours; PathMotif k=5, 32 points",
+    "large10": "power-law out-degree 2.1, n=1e7, m=1e8, t in [1,1e4], 32 uniform colours; PathMotif k=10, "
+               "1024 points",
+    "batch": "10,000 tour-style graphs, n~U[100,5000], avg out-degree 8, t in [1,288], 12 colours; "
+             "k~U{5..8}; one batched call",
+}
+
+
+def workload(scale=1.0, name="mid"):
     import synth
 
+    if name == "large5":
+        return synth.config4_large(m=int(500_000_000 * scale), n=int(10_000_000 * scale), k=5, seed=5)
+    if name == "large10":
+        return synth.config4_large(m=int(100_000_000 * scale), n=int(10_000_000 * scale), k=10, seed=6)
     if scale == 1.0:
         return synth.config2_mid()
     return synth.config2_mid(n=int(1_000_000 * scale), m=int(10_000_000 * scale))
@@ -298,13 +317,15 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    g, q = workload(args.scale)
+    if args.workload == "batch":
+        return run_batch(args, tm, stream, dev, rank, world)
+    g, q = workload(args.scale, args.workload)
     seed = q.seed + 7919 * rank
     work_units = g.m * q.k * (1 << q.k)
 
     G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
     for i in range(args.warmup):
-        tm.tmotif_decide(G, q.k, q.multiset, seed=seed + i)
+        tm.tmotif_decide(G, q.k, q.multiset, seed=seed + i, preprocess=args.preprocess)
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -324,7 +345,8 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             flush.fill_(i & 0xFF)
             starts[i].record(stream)
-        d = tm.tmotif_decide(G, q.k, q.multiset, seed=seed + 1000 + i, per_point=False)
+        d = tm.tmotif_decide(G, q.k, q.multiset, seed=seed + 1000 + i, per_point=False,
+                             preprocess=args.preprocess)
         ends[i].record(stream)
         found.append(d.found)
     torch.cuda.synchronize()
@@ -377,7 +399,7 @@ def run_ours(args):
         G2 = tm.tmotif_create_graph(g.n, pin["src"].numpy().view(np.uint32), pin["dst"].numpy().view(np.uint32),
                                     pin["time"].numpy().view(np.uint32), cpin.numpy().view(np.uint32),
                                     g.num_colors, stream=stream)
-        d2 = tm.tmotif_decide(G2, q.k, q.multiset, seed=seed + 5000 + i)
+        d2 = tm.tmotif_decide(G2, q.k, q.multiset, seed=seed + 5000 + i, preprocess=args.preprocess)
         G2.close()
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = torch.tensor([statistics.mean(e2e_times) if e2e_times else float("nan")], dtype=torch.float64,
@@ -391,21 +413,83 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "k": int(q.k), "points": 1 << q.k,
+            "config": {"workload": WORKLOADS[args.workload], "n": g.n, "m": g.m, "k": int(q.k), "points": 1 << q.k,
+                       "preprocess": bool(args.preprocess),
                        "multiset": [int(c) for c in q.multiset], "found_all": all(found),
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
                        "parallelism": f"replicas x{world} (independent queries)"},
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
             "gpu_launches": int(stats["launches"])}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "mid":
         line["cpu_baseline"] = cpu_baseline(g, q)
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and not args.no_serving and args.workload == "mid":
         line["serving"] = serving_benchmark(tm, stream, requests=args.serving_requests)
     if rank == 0:
         print(json.dumps(line))
     G.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_batch(args, tm, stream, dev, rank, world):
+    """Batched decisions over many small graphs: a step is one
+    tmotif_decide_batch call over all of them (the graphs resident)."""
+    import torch
+
+    import synth
+
+    count = max(1, int(10_000 * args.scale))
+    items = synth.config3_batch(num_graphs=count, seed=4 + 1000 * rank)
+    graphs = [tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
+              for g, _ in items]
+    queries = [{"k": q.k, "multiset": q.multiset, "seed": q.seed} for _, q in items]
+    work = sum(int(g.m) * q.k * (1 << q.k) for g, q in items)
+    arcs = sum(int(g.m) for g, _ in items)
+    for _ in range(args.warmup):
+        tm.tmotif_decide_batch(graphs, queries)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    sampler = ClockSampler("")
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    found = 0
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        res = tm.tmotif_decide_batch(graphs, queries)
+        total_ms += res[0].ms  # device time of the call (events on the shared stream)
+        found = sum(r.found for r in res)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    # the plain form: one tmotif_decide per graph, back to back (same results)
+    t0 = time.perf_counter()
+    plain = [tm.tmotif_decide(G, per_point=False, **q) for G, q in zip(graphs, queries)]
+    torch.cuda.synchronize()
+    plain_ms = (time.perf_counter() - t0) * 1e3
+    same = all(p.found == r.found and p.sieve_sum == r.sieve_sum for p, r in zip(plain, res))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * work * args.steps / (total_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch"], "graphs": count, "arcs": arcs, "found": found,
+                       "l2": "flushed between timed steps", "parallelism": f"replicas x{world}"},
+            "clocks": clocks,
+            "plain": {"ms_per_step": plain_ms, "value": world * work / (plain_ms / 1e3), "results_match": same,
+                      "form": "one tmotif_decide per graph, sequential"}}
+    if rank == 0:
+        print(json.dumps(line))
+    for G in graphs:
+        G.close()
     return 0
 
 

@@ -95,7 +95,9 @@ public:
         return Status();
     }
 
-    bool fits(size_t bytes) const { return in_use_ + bytes <= budget_; }
+    // room for one more job: within the memory budget, and the job tables
+    // of one layer launch stay inside a slot
+    bool fits(size_t bytes) const { return in_use_ + bytes <= budget_ && active_.size() < kMaxActive; }
     size_t in_use() const { return in_use_; }
     size_t budget() const { return budget_; }
     bool idle() const { return active_.empty(); }
@@ -190,9 +192,11 @@ public:
     u64 steps = 0;
 
 private:
+    static_assert(4096 * (sizeof(LayerParams) + 8) + 5 * 256 < (1 << 20), "job tables exceed a slot");
     // one job-table slot (host pinned + device) per layer round between syncs
     static const int kMaxLayersPerSync = 8;
     static const size_t kSlotBytes = 1 << 20;
+    static const size_t kMaxActive = 4096;  // x (LayerParams + prefix) < kSlotBytes
     cudaStream_t st_;
     size_t budget_;
     size_t in_use_ = 0;
