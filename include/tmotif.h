@@ -1,14 +1,14 @@
 /*
  * tmotif.h -- C ABI of the GB300 temporal path-motif sieve.
  *
- * The library decides PathMotif (Sec. 4.3 of Thejaswi, Gionis, Lauri, "Finding
+ * The library decides PathMotif (Sec. 5.3 of Thejaswi, Gionis, Lauri, "Finding
  * path motifs in large temporal graphs using algebraic fingerprints"): given a
  * vertex-coloured temporal graph and a multiset M of k colours, is there a
  * temporal path (k distinct vertices, arcs with strictly increasing
- * timestamps, Sec. 3) whose vertex colours are exactly M?  It evaluates the
- * constrained multilinear sieve of Lemma 5.5 over GF(2^64): the temporal-walk
+ * timestamps, Sec. 4) whose vertex colours are exactly M?  It evaluates the
+ * constrained multilinear sieve of Lemma 6.5 over GF(2^64): the temporal-walk
  * generating function of eq. (gen-polynomial:3) at 2^k sieve points, summed;
- * a nonzero sum certifies a matching path.  Extraction follows Sec. 5.9 (self-
+ * a nonzero sum certifies a matching path.  Extraction follows Sec. 6.9 (self-
  * reducibility with halving, then temporal DFS).
  *
  * Conventions (all entry points):
@@ -17,11 +17,11 @@
  *   - Pointers in descriptors are HOST pointers owned by the caller; the
  *     library copies what it keeps.  Outputs go to caller-owned host buffers.
  *   - Handles are owned by the library and released by the matching destroy.
- *   - Vertex ids are in [0, n).  Timestamps are >= 1 (Z_+, Sec. 3).
+ *   - Vertex ids are in [0, n).  Timestamps are >= 1 (Z_+, Sec. 4).
  *   - 2 <= k <= TMOTIF_KMAX.  Colours are in [0, num_colors).
  *   - A YES answer (found = 1) is always right: the sieve's error is one-sided
- *     (Lemma 5.3/5.5).  A NO is wrong with probability at most
- *     (2k-1)/2^64 per independent repeat (Sec. 5.5).
+ *     (Lemmas 6.3/6.5).  A NO is wrong with probability at most
+ *     (2k-1)/2^64 per independent repeat (Sec. 6.5).
  *   - Work runs on the CUDA stream given at graph creation (NULL = the legacy
  *     default stream); calls return after their results are on the host.
  *   - A graph handle is used by one thread at a time.
@@ -42,9 +42,9 @@ extern "C" {
  * localisation (see tmotif_extract). */
 #define TMOTIF_EXTRACT_HALVING 1u
 /* tmotif_query.flags: extract an optimum solution -- a path whose latest arc
- * time is the least possible (tmotif_optimum_time), as in Sec. 5.8-5.9. */
+ * time is the least possible (tmotif_optimum_time), as in Sec. 6.8-6.9. */
 #define TMOTIF_EXTRACT_OPTIMUM 2u
-/* tmotif_query.flags: static preprocessing sieve first (Sec. 7.1 (ii); see
+/* tmotif_query.flags: static preprocessing sieve first (Sec. 8.1 (ii); see
  * tmotif_static_sieve): decide / extract / optimum time / localise on the
  * temporal graph restricted to the vertices it keeps.  Every temporal match
  * survives, so decisions are unchanged; per-point sums are those of the
@@ -66,7 +66,7 @@ enum {
 typedef struct tmotif_graph *tmotif_graph_t;   /* opaque, library-owned */
 typedef struct tmotif_server *tmotif_server_t; /* opaque, library-owned */
 
-/* A vertex-coloured temporal graph G^tau = (V, E^tau), Sec. 3.  Edge e is the
+/* A vertex-coloured temporal graph G^tau = (V, E^tau), Sec. 4.  Edge e is the
  * triple (src[e], dst[e], time[e]); with undirected = 0 it is the arc
  * src -> dst (moving from src to dst at that time); with undirected = 1 it
  * stands for both arcs.  E^tau is a set: identical arcs are kept once and
@@ -82,8 +82,8 @@ typedef struct {
     void *cuda_stream; /* cudaStream_t used for every call on this graph */
 } tmotif_graph_desc;
 
-/* A PathMotif query (Sec. 4.3), with the (s,d) variant of Sec. 6.1 as start/
- * end vertices and the latest-time restriction of Sec. 5.8 as a window.
+/* A PathMotif query (Sec. 5.3), with the (s,d) variant of Sec. 7.1 as start/
+ * end vertices and the latest-time restriction of Sec. 6.8 as a window.
  *   multiset      k colours in any order (caller-owned host array);
  *   start, end    TMOTIF_ANY or the required first / last vertex; M must count
  *                 their colours;
@@ -97,12 +97,12 @@ typedef struct {
  *   flags         0 or TMOTIF_EXTRACT_HALVING, TMOTIF_EXTRACT_OPTIMUM and/or
  *                 TMOTIF_PREPROCESS_STATIC;
  *   timestamps    NULL, or the EC-PathMotif tuple T = (j_1, ..., j_{k-1}) of
- *                 Sec. 6.3 (caller-owned host array of k-1 strictly increasing
+ *                 Sec. 7.3 (caller-owned host array of k-1 strictly increasing
  *                 times >= 1; INVALID otherwise): the path's l-th arc must have
  *                 time j_l.  Only arcs whose time is in T (and in the window)
  *                 are used; a temporal path of k-1 arcs with strictly
  *                 increasing times from a set of k-1 values uses them all in
- *                 order, so this is exactly the EC recurrence of Sec. 6.3.
+ *                 order, so this is exactly the EC recurrence of Sec. 7.3.
  *                 Applies to decide, extract, batch and server requests. */
 typedef struct {
     uint32_t k;
@@ -161,17 +161,17 @@ int tmotif_create_graph(const tmotif_graph_desc *desc, tmotif_graph_t *out);
 void tmotif_destroy_graph(tmotif_graph_t g);
 int tmotif_graph_get_info(tmotif_graph_t g, tmotif_graph_info *info);
 
-/* Decide PathMotif (Lemma 5.5 on eq. gen-polynomial:3, Lemma 5.4 time and
+/* Decide PathMotif (Lemma 6.5 on eq. gen-polynomial:3, Lemma 6.4 time and
  * O(m L) space per lane batch of L points).  Errors: INVALID (bad multiset
  * colour, start/end out of range, repeats 0, bad point range), UNSUPPORTED
  * (k outside [2, TMOTIF_KMAX]), OOM, CUDA. */
 int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out);
 
-/* Extract one matching temporal path (Sec. 5.9): verts receives k vertex ids
+/* Extract one matching temporal path (Sec. 6.9): verts receives k vertex ids
  * in path order and times the k-1 arc timestamps (caller-owned).  found = 0
  * when no path exists.  Two procedures, both deterministic given the seed:
  *   by localisation (default; the paper's second approach, with the sieve of
- *     Sec. 5.7 localised to arcs): level 1 runs the sieve of the query with
+ *     Sec. 6.7 localised to arcs): level 1 runs the sieve of the query with
  *     per-arc sums at the last layer and takes the first arc (a1 -> b1, t1)
  *     in (dst, time, src) order whose sum is nonzero -- a matching path ends
  *     with it; level j asks for a path on the remaining colours ending at
@@ -187,7 +187,7 @@ int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out)
  * Errors as tmotif_decide. */
 int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uint32_t *times, int *found);
 
-/* Optimum timestamp (Sec. 5.8): *t_opt = the least t' such that the query
+/* Optimum timestamp (Sec. 6.8): *t_opt = the least t' such that the query
  * restricted to arcs with t_min <= time <= t' is YES, found by binary search
  * with O(log t) decisions (each with the query's seed and repeats):
  * lo = max(t_min, 1), hi = t_max (0: the largest time); no path when hi is
@@ -195,13 +195,13 @@ int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uin
  * mid + 1 on NO.  *found = 0 when no path exists.  Errors as tmotif_decide. */
 int tmotif_optimum_time(tmotif_graph_t g, const tmotif_query *q, uint32_t *t_opt, int *found);
 
-/* Vertex-localised sieve (Sec. 5.7): per_vertex[u] (caller-owned, n values)
+/* Vertex-localised sieve (Sec. 6.7): per_vertex[u] (caller-owned, n values)
  * receives Q_u = sum over the 2^k points of P_{u,k,t}(z^A) -- nonzero exactly
  * when (w.h.p.) a matching temporal path ends at u; out receives the whole
  * decision (first repeat; repeats are ignored).  Errors as tmotif_decide. */
 int tmotif_localize(tmotif_graph_t g, const tmotif_query *q, uint64_t *per_vertex, tmotif_decision *out);
 
-/* Static preprocessing sieve (Sec. 7.1 (ii), static generating function
+/* Static preprocessing sieve (Sec. 8.1 (ii), static generating function
  * eq. gen-polynomial:1).  The temporal arcs are merged into the static graph
  * E_s = {(a, b) : some arc a -> b}; per_vertex[u] (caller-owned, n values, or
  * NULL) receives Q_u = sum over the 2^k points A of

@@ -108,7 +108,7 @@ def _ptr(a):
 
 
 # --------------------------------------------------------------------------
-# GF(2^64) and coefficients (Sec. 5.5 / Lemma 5.5)
+# GF(2^64) and coefficients (Sec. 6.5 / Lemma 6.5)
 # --------------------------------------------------------------------------
 def gf_mul(a: int, b: int) -> int:
     """Product in GF(2^64) = GF(2)[x]/(x^64 + x^4 + x^3 + x + 1)."""
@@ -154,7 +154,7 @@ def coef_w(qs: int, d: int, j: int) -> int:
 
 
 def coef_y(qs: int, a: int, b: int, t: int, p: int) -> int:
-    """y for arc a->b at time t used at walk position p (Sec. 5.3)."""
+    """y for arc a->b at time t used at walk position p (Sec. 6.3)."""
     return _load().or_coef_y(qs, a, b, t, p)
 
 
@@ -177,7 +177,7 @@ def vertex_x(qs, k, multiset, num_colors, color_u, u, point):
 # Graphs
 # --------------------------------------------------------------------------
 def canon(n, src, dst, time, undirected=False):
-    """Canonical arc set (Sec. 3: E^tau is a set; undirected = two arcs;
+    """Canonical arc set (Sec. 4: E^tau is a set; undirected = two arcs;
     self-loops dropped), sorted by (time, src, dst)."""
     src, dst, time = _u32(src), _u32(dst), _u32(time)
     m = len(src)
@@ -214,7 +214,7 @@ class Problem:
 
 def sieve_points(pb: Problem, qs: int, p_begin=0, p_end=None, nthreads=0):
     """Q^A for points [p_begin, p_end): eq. gen-polynomial:3 with the time index
-    rolled, sieve substitution of Lemma 5.5."""
+    rolled, sieve substitution of Lemma 6.5."""
     if p_end is None:
         p_end = 1 << pb.k
     out = np.zeros(p_end - p_begin, np.uint64)
@@ -235,7 +235,7 @@ def literal_table(pb: Problem, qs: int, point: int, T: int):
 
 
 def brute_points(pb: Problem, qs: int, p_begin=0, p_end=None):
-    """Per-point sums of walk monomials (walk enumeration, Sec. 5.3)."""
+    """Per-point sums of walk monomials (walk enumeration, Sec. 6.3)."""
     if p_end is None:
         p_end = 1 << pb.k
     out = np.zeros(p_end - p_begin, np.uint64)
@@ -255,7 +255,7 @@ def brute_det(pb: Problem, qs: int):
 
 
 def count_paths(pb: Problem, limit=0):
-    """Exhaustive temporal DFS (Sec. 8.1 baseline): number of matching temporal
+    """Exhaustive temporal DFS (Sec. 9.1 baseline): number of matching temporal
     paths (stops at `limit` if > 0) and the first one found."""
     fv = np.zeros(KMAX, np.uint32)
     ft = np.zeros(KMAX, np.uint32)
@@ -267,7 +267,7 @@ def count_paths(pb: Problem, limit=0):
 
 def decide(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
            t_min=0, t_max=0, seed=1, repeats=1, point_begin=0, point_end=0, alive=None, nthreads=0):
-    """Decision (Lemma 5.5): returns (found, sieve_sum, per_point) from the raw
+    """Decision (Lemma 6.5): returns (found, sieve_sum, per_point) from the raw
     edge list.  per_point covers [point_begin, point_end) (0,0 = all 2^k)."""
     src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
     npts = (1 << k) if point_end == 0 else point_end - point_begin
@@ -285,7 +285,7 @@ def decide(n, src, dst, time, color, num_colors, k, multiset, *, undirected=Fals
 
 def decide_ec(n, src, dst, time, color, num_colors, k, multiset, timestamps, *, undirected=False, start=ANY,
               end=ANY, t_min=0, t_max=0, seed=1, repeats=1, point_begin=0, point_end=0, alive=None, nthreads=0):
-    """EC-PathMotif decision (Sec. 6.3): the path's arc times must equal the
+    """EC-PathMotif decision (Sec. 7.3): the path's arc times must equal the
     strictly increasing tuple `timestamps` (k-1 entries).  Returns (found,
     sieve_sum, per_point) like decide()."""
     src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
@@ -307,7 +307,7 @@ def decide_ec(n, src, dst, time, color, num_colors, k, multiset, timestamps, *, 
 
 def static_through(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
                    seed=1, alive=None, nthreads=0):
-    """Static preprocessing sieve (Sec. 7.1 (ii)): per-vertex sums Q_u over
+    """Static preprocessing sieve (Sec. 8.1 (ii)): per-vertex sums Q_u over
     the merged static graph; Q_u != 0 iff u lies on a static path with
     colours M (w.h.p.).  Returns n uint64 values."""
     src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
@@ -340,7 +340,7 @@ def decide_preprocessed(n, src, dst, time, color, num_colors, k, multiset, *, un
                         end=ANY, t_min=0, t_max=0, seed=1, repeats=1, point_begin=0, point_end=0, alive=None,
                         timestamps=None, nthreads=0):
     """Decision after the static preprocessing sieve: vertices with Q_u = 0
-    are removed (Sec. 7.1 (ii)), then the temporal sieve runs on the rest.
+    are removed (Sec. 8.1 (ii)), then the temporal sieve runs on the rest.
     Returns (found, sieve_sum, per_point, keep_mask)."""
     qv = static_through(n, src, dst, time, color, num_colors, k, multiset, undirected=undirected, start=start,
                         end=end, seed=seed, alive=alive, nthreads=nthreads)
@@ -358,7 +358,7 @@ def decide_preprocessed(n, src, dst, time, color, num_colors, k, multiset, *, un
 
 def extract(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
             t_min=0, t_max=0, seed=1, repeats=1, nthreads=0):
-    """Extraction by self-reducibility + temporal DFS (Sec. 5.9).  Returns
+    """Extraction by self-reducibility + temporal DFS (Sec. 6.9).  Returns
     (found, verts[k], times[k-1], probes)."""
     src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
     verts = np.zeros(KMAX, np.uint32)
@@ -384,7 +384,7 @@ def brute_arc_det(pb: Problem, qs: int):
 
 
 def arc_sums(pb: Problem, qs: int):
-    """Arc-localised sieve (Sec. 5.7 localisation, split by the last arc):
+    """Arc-localised sieve (Sec. 6.7 localisation, split by the last arc):
     S_e = sum over points of the last-layer term of eq. gen-polynomial:3 that
     arc e contributes.  Arcs of pb must be canonical (sorted by time)."""
     out = np.zeros(max(pb.m, 1), np.uint64)
@@ -397,7 +397,7 @@ def arc_sums(pb: Problem, qs: int):
 def extract_localized(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
                       t_min=0, t_max=0, seed=1, repeats=1):
     """Extraction by localisation: k-1 arc-localised sieves on shrinking
-    problems, the path built backwards from its last arc (Sec. 5.9, second
+    problems, the path built backwards from its last arc (Sec. 6.9, second
     approach).  Returns (found, verts[k], times[k-1])."""
     src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
     verts = np.zeros(KMAX, np.uint32)
@@ -413,7 +413,7 @@ def extract_localized(n, src, dst, time, color, num_colors, k, multiset, *, undi
 
 def optimum_time(n, src, dst, time, color, num_colors, k, multiset, *, undirected=False, start=ANY, end=ANY,
                  t_min=0, t_max=0, seed=1, repeats=1, nthreads=0):
-    """Optimum timestamp (Sec. 5.8): least t' with a matching path using only
+    """Optimum timestamp (Sec. 6.8): least t' with a matching path using only
     arcs in [t_min, t'], by binary search.  Returns (found, t_opt)."""
     src, dst, time, color, ms = _u32(src), _u32(dst), _u32(time), _u32(color), _u32(multiset)
     t = u32(0)

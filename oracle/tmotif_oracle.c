@@ -11,21 +11,21 @@
  * Everything here is written for a reader to check against the paper by eye:
  *   - GF(2^64) arithmetic is the textbook shift-and-add ("Russian peasant")
  *     product with interleaved reduction modulo f(x) = x^64 + x^4 + x^3 + x + 1.
- *   - The generating function follows eq. (gen-polynomial:3) of Sec. 5.4:
+ *   - The generating function follows eq. (gen-polynomial:3) of Sec. 6.4:
  *       P_{u,1,i} = x_u,
  *       P_{u,l,i} = x_u * sum_{v in N_i(u)} y_{uv,l-1,i} P_{v,l-1,i-1} + P_{u,l,i-1}.
  *     or_sieve_points() evaluates it with the time index rolled (one array per
  *     walk length, lengths updated in decreasing order inside each time step so
  *     that P_{.,l-1,i-1} is read before it is overwritten); or_literal_table()
  *     fills the full table P_{u,l,i} exactly as printed, for tiny graphs.
- *   - The sieve variables follow Lemma 5.5 (constrained multilinear sieving,
+ *   - The sieve variables follow Lemma 6.5 (constrained multilinear sieving,
  *     eq. motif:1): z_{i,j} = sum_{d in S_{c(i)}} v_{i,d} w_{d,j},
  *     z_i^A = sum_{j in A} z_{i,j}; Q = sum_{A subset of L} P_{k,t}(z^A, y).
  *   - or_brute_points() and or_brute_det() evaluate the same sums from the
- *     walk definitions (Sec. 5.3) without the recurrence.
+ *     walk definitions (Sec. 6.3) without the recurrence.
  *   - or_count_paths() is the exhaustive temporal DFS of the experimental
- *     baseline (Sec. 8.1): ground truth for the decision.
- *   - or_extract() is extraction by self-reducibility (Sec. 5.9) with the
+ *     baseline (Sec. 9.1): ground truth for the decision.
+ *   - or_extract() is extraction by self-reducibility (Sec. 6.9) with the
  *     halving group test and a temporal DFS on the survivors.
  *
  * Points the paper leaves open are read as follows (the GPU library makes
@@ -117,19 +117,19 @@ u64 or_query_seed(u64 seed, u32 r) { return or_fmix64(seed + (u64)(r + 1) * OR_G
 /* seed of the i-th extraction probe (i >= 1). */
 u64 or_probe_seed(u64 seed, u32 i) { return or_fmix64(seed ^ ((u64)i * OR_PROBE)); }
 
-/* v_{u,d}: vertex u, slot d (Lemma 5.5). */
+/* v_{u,d}: vertex u, slot d (Lemma 6.5). */
 u64 or_coef_v(u64 qs, u32 u, u32 d)
 {
     return or_fmix64(or_fmix64(qs ^ OR_TAG_V) ^ (((u64)u << 8) | d));
 }
 
-/* w_{d,j}: slot d, label j (Lemma 5.5). */
+/* w_{d,j}: slot d, label j (Lemma 6.5). */
 u64 or_coef_w(u64 qs, u32 d, u32 j)
 {
     return or_fmix64(or_fmix64(qs ^ OR_TAG_W) ^ (((u64)d << 8) | j));
 }
 
-/* y_{ab,p,t}: the arc a->b at time t used at walk position p (Sec. 5.3). */
+/* y_{ab,p,t}: the arc a->b at time t used at walk position p (Sec. 6.3). */
 u64 or_coef_y(u64 qs, u32 a, u32 b, u32 t, u32 p)
 {
     u64 h = or_fmix64(or_fmix64(qs ^ OR_TAG_Y) ^ (((u64)a << 32) | b));
@@ -172,7 +172,7 @@ u64 or_vertex_x(u64 qs, u32 k, const u32 *slot_begin, const u32 *slot_count, u32
 }
 
 /* ------------------------------------------------------------------------ */
-/* Temporal edge set.  E^tau is a set of triples (u,v,j), j >= 1 (Sec. 3):   */
+/* Temporal edge set.  E^tau is a set of triples (u,v,j), j >= 1 (Sec. 4):   */
 /* undirected edges become two arcs, self-loops are dropped and identical    */
 /* arcs are kept once.  Output is sorted by (time, src, dst).                */
 /* ------------------------------------------------------------------------ */
@@ -336,7 +336,7 @@ int or_sieve_points(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *tim
 
 /* ------------------------------------------------------------------------ */
 /* Literal table: P_{u,l,i} for u in [n], l in [1,k], i in [0,T], exactly as */
-/* printed in eq. (gen-polynomial:3), loops l > i > u (Sec. 7).  One point.   */
+/* printed in eq. (gen-polynomial:3), loops l > i > u (Sec. 8).  One point.   */
 /* table has n*(k+1)*(T+1) entries, index (u*(k+1) + l)*(T+1) + i.           */
 /* Returns Q^A = sum_{u end-ok} P_{u,k,T}.                                   */
 /* ------------------------------------------------------------------------ */
@@ -380,7 +380,7 @@ int or_literal_table(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *ti
 }
 
 /* ------------------------------------------------------------------------ */
-/* Walk enumeration (Sec. 5.3 definitions, no recurrence).                   */
+/* Walk enumeration (Sec. 6.3 definitions, no recurrence).                   */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const or_problem *P;
@@ -488,7 +488,7 @@ static void or_walk_all(or_enum *E)
 }
 
 /* Per-point values by summing every temporal walk's monomial
- * x_{u_1} y_1 x_{u_2} ... y_{k-1} x_{u_k} at the point (Sec. 5.3-5.4).
+ * x_{u_1} y_1 x_{u_2} ... y_{k-1} x_{u_k} at the point (Sec. 6.3-6.4).
  * Exponential: tiny graphs only.  Returns the number of walks, -1 on error. */
 i64 or_brute_points(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32 *color,
                     u32 num_colors, const uint8_t *alive, u32 k, const u32 *multiset, u32 start, u32 end,
@@ -514,7 +514,7 @@ i64 or_brute_points(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *tim
 
 /* Whole-sieve value Q = sum over all 2^k points, from the identity
  * sum_{A subset of L} prod_r z_{u_r}^A = det(Z) in characteristic 2, where
- * Z[r][j] = z_{u_r,j} (Lemmas 5.3 and 5.5): Q = sum_walks (prod y) det(Z_walk).
+ * Z[r][j] = z_{u_r,j} (Lemmas 6.3 and 6.5): Q = sum_walks (prod y) det(Z_walk).
  * Returns the number of walks, -1 on error. */
 i64 or_brute_det(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32 *color,
                  u32 num_colors, const uint8_t *alive, u32 k, const u32 *multiset, u32 start, u32 end,
@@ -562,8 +562,8 @@ i64 or_brute_arc_det(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *ti
 /* b may end the path, S_e = sum over all 2^k points A of the last-layer term */
 /* of eq. (gen-polynomial:3) that e contributes,                             */
 /*     x_b^A * y_{ba,k-1,t} * P_{a,k-1,t-1}(z^A),                            */
-/* i.e. the sieve of Lemma 5.5 applied to the walks whose last arc is e (the */
-/* vertex-localised sieve of Sec. 5.7, split further by the last arc).  The  */
+/* i.e. the sieve of Lemma 6.5 applied to the walks whose last arc is e (the */
+/* vertex-localised sieve of Sec. 6.7, split further by the last arc).  The  */
 /* sum of S_e over the arcs into b is the vertex-localised value Q_b.        */
 /* Arcs must be canonical (sorted by time).  arc_out has m entries.          */
 /* ------------------------------------------------------------------------ */
@@ -607,7 +607,7 @@ int or_arc_sums(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, c
 }
 
 /* ------------------------------------------------------------------------ */
-/* Extraction by localisation (Sec. 5.9, second approach, with the sieve     */
+/* Extraction by localisation (Sec. 6.9, second approach, with the sieve     */
 /* localised to arcs).  Level 1 runs the arc-localised sieve on the query   */
 /* and takes the first arc (a1 -> b1, t1) in (dst, time, src) order whose    */
 /* value is nonzero: some matching path ends with it.  Level j >= 2 asks for */
@@ -671,7 +671,7 @@ int or_extract_localized(u32 n, u64 m, const u32 *src, const u32 *dst, const u32
 }
 
 /* ------------------------------------------------------------------------ */
-/* Exhaustive temporal DFS (Sec. 8.1 baseline): counts temporal paths whose  */
+/* Exhaustive temporal DFS (Sec. 9.1 baseline): counts temporal paths whose  */
 /* vertex colours equal the multiset (distinct vertices, strictly increasing */
 /* times, window, start/end).  Stops after `limit` paths when limit > 0.     */
 /* ------------------------------------------------------------------------ */
@@ -779,7 +779,7 @@ i64 or_min_last_time(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *ti
 }
 
 /* ------------------------------------------------------------------------ */
-/* Decision (Lemma 5.5 + Lemma 5.4): for each repeat r, Q_r = sum over all  */
+/* Decision (Lemma 6.5 + Lemma 6.4): for each repeat r, Q_r = sum over all  */
 /* 2^k points; found = OR_r (Q_r != 0).  per_point (optional) receives the   */
 /* repeat-0 values on [p_begin, p_end) (p_end = 0 means all 2^k points).    */
 /* Input is the caller's edge list; canonicalised here.                      */
@@ -847,7 +847,7 @@ int or_decide(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int
 }
 
 /* ------------------------------------------------------------------------ */
-/* Static preprocessing sieve (Sec. 7.1 (ii) with eq. gen-polynomial:1).     */
+/* Static preprocessing sieve (Sec. 8.1 (ii) with eq. gen-polynomial:1).     */
 /* The temporal graph is merged into the static graph                        */
 /*   E_s = {(a, b) : some canonical arc a -> b, at any time}.                */
 /* A vertex is kept iff it lies on at least one static path whose colours   */
@@ -862,7 +862,7 @@ int or_decide(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, int
 /* a whole walk of k vertices with u at position r; the arc from position p */
 /* to p+1 carries yf before u and yb from u on.  Q_u = sum_A Q_u^A is       */
 /* non-zero (up to the sieve's one-sided error) iff such a walk is a path   */
-/* with colours M (Lemmas 5.2-5.5 applied to each vertex's terms).          */
+/* with colours M (Lemmas 6.2-6.5 applied to each vertex's terms).          */
 /*   yf(a->b, p) = mix64(mix64(kf ^ (a<<32 | b)) ^ p), kf = mix64(qs ^ 0x4444..44) */
 /*   yb(a->b, p) = mix64(mix64(kb ^ (a<<32 | b)) ^ p), kb = mix64(qs ^ 0x5555..55) */
 /* ------------------------------------------------------------------------ */
@@ -1091,7 +1091,7 @@ i64 or_static_brute(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *tim
 }
 
 /* ------------------------------------------------------------------------ */
-/* EC-PathMotif (Sec. 6.3): the path's arc times must equal the tuple        */
+/* EC-PathMotif (Sec. 7.3): the path's arc times must equal the tuple        */
 /* T = (j_1, ..., j_{k-1}), j_1 < ... < j_{k-1}.  The recurrence there keeps */
 /* one value per vertex and walk length, with no "stay" term:               */
 /*   P_{u,1} = x_u,                                                          */
@@ -1196,7 +1196,7 @@ int or_decide_ec(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *time, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Optimum timestamp (Sec. 5.8): the least t' for which the query restricted */
+/* Optimum timestamp (Sec. 6.8): the least t' for which the query restricted */
 /* to arcs with times in [t_min, t'] is YES, by binary search over t' with   */
 /* O(log t) decisions (each with the query's seed and repeats):             */
 /* lo = max(t_min, 1), hi = t_max (or the largest time); if hi is NO there   */
@@ -1247,7 +1247,7 @@ int or_optimum_time(u32 n, u64 m, const u32 *src, const u32 *dst, const u32 *tim
 }
 
 /* ------------------------------------------------------------------------ */
-/* Extraction by self-reducibility (Sec. 5.9): candidates R = vertices whose */
+/* Extraction by self-reducibility (Sec. 6.9): candidates R = vertices whose */
 /* colour is in the multiset, ascending id.  shrink(block): if the block is  */
 /* not all that is left and the problem with the block removed is still YES */
 /* (probe i uses seed or_probe_seed(seed, i)), the block is removed; else a  */

@@ -6,9 +6,9 @@ package loads the in-tree library and raises if it has not been built; there
 is no CPU fallback.
 
 Method: Thejaswi, Gionis, Lauri, "Finding path motifs in large temporal graphs
-using algebraic fingerprints" -- the constrained multilinear sieve (Lemma 5.5)
+using algebraic fingerprints" -- the constrained multilinear sieve (Lemma 6.5)
 over the temporal-walk generating function (eq. gen-polynomial:3) in GF(2^64),
-and extraction by self-reducibility (Sec. 5.9).
+and extraction by self-reducibility (Sec. 6.9).
 """
 from __future__ import annotations
 
@@ -184,7 +184,7 @@ def tmotif_decide(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_
                   repeats=1, point_begin=0, point_end=0, per_point=True, timestamps=None,
                   preprocess=False) -> Decision:
     """PathMotif decision; with `timestamps` (k-1 strictly increasing times)
-    the EC-PathMotif decision of Sec. 6.3; with `preprocess` the static
+    the EC-PathMotif decision of Sec. 7.3; with `preprocess` the static
     preprocessing sieve first (TMOTIF_PREPROCESS_STATIC)."""
     q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end,
                      TMOTIF_PREPROCESS_STATIC if preprocess else 0, timestamps)
@@ -199,7 +199,7 @@ def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t
                    repeats=1, method="localized", optimum=False, timestamps=None, preprocess=False):
     """method: "localized" (default) or "halving" (TMOTIF_EXTRACT_HALVING);
     optimum: extract a path with the least latest time (TMOTIF_EXTRACT_OPTIMUM);
-    timestamps: the EC-PathMotif tuple (Sec. 6.3), or None."""
+    timestamps: the EC-PathMotif tuple (Sec. 7.3), or None."""
     flags = (TMOTIF_EXTRACT_HALVING if method == "halving" else 0) | (TMOTIF_EXTRACT_OPTIMUM if optimum else 0)
     flags |= TMOTIF_PREPROCESS_STATIC if preprocess else 0
     q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags, timestamps)
@@ -212,7 +212,7 @@ def tmotif_extract(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t
 
 def tmotif_optimum_time(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, t_min=0, t_max=0, seed=1,
                         repeats=1, timestamps=None, preprocess=False):
-    """Optimum timestamp (Sec. 5.8): (found, least t' with a path in [t_min, t'])."""
+    """Optimum timestamp (Sec. 6.8): (found, least t' with a path in [t_min, t'])."""
     q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0,
                      TMOTIF_PREPROCESS_STATIC if preprocess else 0, timestamps)
     t = C.c_uint32(0)
@@ -233,7 +233,7 @@ def tmotif_localize(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, 
 
 
 def tmotif_static_sieve(g: Graph, k, multiset, *, start=TMOTIF_ANY, end=TMOTIF_ANY, seed=1):
-    """Static preprocessing sieve (Sec. 7.1 (ii)): (per-vertex Q_u, number of
+    """Static preprocessing sieve (Sec. 8.1 (ii)): (per-vertex Q_u, number of
     kept vertices); Q_u != 0 iff u lies on a static path with colours M."""
     q, keep = _query(k, multiset, start, end, 0, 0, seed, 1, 0, 0)
     qv = np.zeros(max(g.n, 1), np.uint64)

@@ -195,7 +195,7 @@ void Profiler::destroy()
 
 // ---------------------------------------------------------------------------
 // Graph residency: validate, orient, drop self-loops, merge duplicates, sort
-// arcs by (dst, time, src), upload.  E^tau is a set of triples (Sec. 3).
+// arcs by (dst, time, src), upload.  E^tau is a set of triples (Sec. 4).
 // ---------------------------------------------------------------------------
 struct HArc {
     u32 dst, time, src;
@@ -395,7 +395,7 @@ int tmotif_graph_get_info(tmotif_graph_t g, tmotif_graph_info *info)
 namespace {
 
 // With TMOTIF_PREPROCESS_STATIC: the static sieve's kept vertices and the
-// graph of the arcs among them (same vertex ids; Sec. 7.1 (ii) rebuilds the
+// graph of the arcs among them (same vertex ids; Sec. 8.1 (ii) rebuilds the
 // temporal graph on those vertices).  Otherwise the graph itself.
 struct Prepared {
     Graph *g = nullptr;

@@ -1,4 +1,4 @@
-// extract.cu -- extraction of a matching temporal path (Sec. 5.9).
+// extract.cu -- extraction of a matching temporal path (Sec. 6.9).
 //
 // Step (i), self-reducibility with halving: the candidate set R holds the
 // vertices whose colour is in M, in ascending id.  shrink(block) removes the
@@ -239,7 +239,7 @@ Status extract_path(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *f
 }
 
 // ---------------------------------------------------------------------------
-// Extraction by localisation (Sec. 5.9, second approach, localised to arcs).
+// Extraction by localisation (Sec. 6.9, second approach, localised to arcs).
 // Level 1: the arc-localised sieve of the query; its first nonzero arc
 // (a1 -> b1, t1) in (dst, time, src) order ends a matching path.  Level j:
 // a path on the remaining colours ending at a_{j-1}, every time below

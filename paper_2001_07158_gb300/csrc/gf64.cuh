@@ -2,7 +2,7 @@
 //
 // Field: GF(2)[x] / (x^64 + x^4 + x^3 + x + 1), polynomial basis, bit i of a
 // 64-bit word is the coefficient of x^i.  Addition is XOR.  The paper fixes
-// only the field size (b = 64, Sec. 5.5 and Sec. 7); the modulus is the
+// only the field size (b = 64, Sec. 6.5 and Sec. 8); the modulus is the
 // standard pentanomial for this size.
 //
 // Multiplication (carry-less product then reduction) is built from 32-bit

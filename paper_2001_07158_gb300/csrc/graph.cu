@@ -1,6 +1,6 @@
 // graph.cu -- graph residency built on the device.
 //
-// E^tau is a set of triples (u, v, j), j >= 1 (Sec. 3).  The build uploads the
+// E^tau is a set of triples (u, v, j), j >= 1 (Sec. 4).  The build uploads the
 // caller's edge arrays and, on the device: validates them, turns each edge
 // into one arc (two for undirected input) packed as a 64-bit key
 // dst | time | src (bit widths from n and the largest timestamp), marks

@@ -250,7 +250,7 @@ void release_graph_arrays(Graph *g);
 // subgraph).  Uses workspace w on stream st.
 Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_t *d_alive, Graph *sub);
 
-// Extraction (Sec. 5.9) as a state machine: next_probe() gives the next
+// Extraction (Sec. 6.9) as a state machine: next_probe() gives the next
 // decision to run (the first one is the query itself, the rest mask the
 // vertices with alive[u] == 0), result() takes its answer.  When
 // next_probe() returns false, stage is SHRUNK (run extract_finish) or
@@ -307,10 +307,10 @@ struct LocalizedExtract {
 // is nonzero; *best = NONE when there is none, else (*a -> *b, *t).
 Status sieve_first_arc(Graph &g, const QuerySpec &q, u32 repeat, const uint8_t *d_alive, u32 *best, u32 *a, u32 *b,
                        u32 *t);
-// Per-vertex localised values Q_u (Sec. 5.7) for every vertex: XOR over the
+// Per-vertex localised values Q_u (Sec. 6.7) for every vertex: XOR over the
 // arc sums of the arcs into u.  per_vertex (host) has n entries.
 Status sieve_localize(Graph &g, const QuerySpec &q, u64 *per_vertex, int *found, u64 *sieve_sum, double *ms);
-// Optimum timestamp by binary search over the window's upper end (Sec. 5.8).
+// Optimum timestamp by binary search over the window's upper end (Sec. 6.8).
 Status optimum_time(Graph &g, const QuerySpec &q, u32 *t_opt, int *found);
 // Extraction by localisation (k-1 arc-localised sieves, path built backwards).
 Status extract_localized(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *found);
@@ -321,7 +321,7 @@ Status build_graph(const tmotif_graph_desc *d, Graph *g);
 Status radix_sort_u64(cudaStream_t st, u64 *a, u64 *b, u64 N, int bits, u32 *d_scratch, u64 **sorted,
                       u64 *launches);
 
-// Static preprocessing sieve (Sec. 7.1 (ii)): the static graph of g (built
+// Static preprocessing sieve (Sec. 8.1 (ii)): the static graph of g (built
 // once), then per-vertex sums Q_u (device, n u64) for the query: nonzero iff
 // u lies on a static path with colours M.  kept_pairs (optional) receives
 // the number of static pairs among the query's vertices.

@@ -2,12 +2,12 @@
 //
 // For one query the device runs, per lane batch of L sieve points:
 //   1. prep (once per query): keep the arcs whose endpoints carry a query
-//      colour and whose time is in the window (Sec. 7.1 preprocessing (i):
+//      colour and whose time is in the window (Sec. 8.1 preprocessing (i):
 //      vertices whose colour is not in M contribute x_u = 0), compact them in
 //      (dst, time, src) order, find for every arc e = (a -> b, t) the last
 //      in-arc of a with time < t ("pos"), and number the distinct pos values
 //      ("checkpoints": the only prefix values any later arc reads);
-//   2. coefficients x_u^A = sum_{d in S_c(u)} v_{u,d} W_d^A (Lemma 5.5,
+//   2. coefficients x_u^A = sum_{d in S_c(u)} v_{u,d} W_d^A (Lemma 6.5,
 //      eq. motif:1) for every lane;
 //   3. layers l = 2..k of eq. (gen-polynomial:3), edge-centric: for arc e into
 //      b, H_l[e] = y_{e,l-1} * P_{a,l-1,t(e)-1}; P_{b,l,i} is x_b times the XOR
@@ -56,7 +56,7 @@ __global__ void k_active_list(u32 n, const u32 *act, u32 *list)
 }
 
 // Arc e is kept iff both endpoints are flagged, its time lies in the window
-// and, for EC-PathMotif (Sec. 6.3), its time is one of the tuple's.
+// and, for EC-PathMotif (Sec. 7.3), its time is one of the tuple's.
 __global__ void k_keep(u64 m, const u32 *src, const u32 *dst, const u32 *time, const uint8_t *vflag, ArcFilter f,
                        u32 *keep)
 {
@@ -98,7 +98,7 @@ __global__ void k_segments(u64 mf, const u32 *f_dst, u32 *seg_lo, u32 *seg_hi)
 }
 
 // pos[e] = last in-arc of src(e) with time < time(e) (strictly increasing times,
-// Sec. 3), or NONE; marks that arc as a checkpoint.
+// Sec. 4), or NONE; marks that arc as a checkpoint.
 __global__ void k_pos(u64 mf, const u32 *f_src, const u32 *f_time, const u32 *seg_lo, const u32 *seg_hi,
                       u32 *pos, u32 *mark)
 {
@@ -132,7 +132,7 @@ __global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in,
 }
 
 // ---------------------------------------------------------------------------
-// Coefficients (Lemma 5.5, eq. motif:1)
+// Coefficients (Lemma 6.5, eq. motif:1)
 // ---------------------------------------------------------------------------
 // W_d^A = sum_{j in A} w_{d,j} for slots d < k and lanes of the batch.
 __global__ void k_wtab(u32 k, u32 L, u64 p0, QueryKeys keys, u64 *wtab)
@@ -457,7 +457,7 @@ Status job_prep(Job &j)
     TM_CUDA(cudaMemcpyAsync(w.slot_count.p, sc.data(), g.num_colors * 4, cudaMemcpyHostToDevice, st));
     u32 *d_cnt = w.counters.as<u32>();
 
-    // filter arcs (Sec. 7.1 (i): colours outside M, masked vertices, window)
+    // filter arcs (Sec. 8.1 (i): colours outside M, masked vertices, window)
     cudaEvent_t pa = nullptr;
     TM_TRY(j.prof->begin(st, &pa));
     TM_TRY(w.vflag.reserve(std::max<u64>(n, 1)));

@@ -1,4 +1,4 @@
-// static.cu -- static-graph preprocessing sieve (Sec. 7.1 (ii), with the
+// static.cu -- static-graph preprocessing sieve (Sec. 8.1 (ii), with the
 // static generating function eq. gen-polynomial:1).
 //
 // The temporal graph is merged into the static graph E_s = {(a, b) : some arc

@@ -1,7 +1,7 @@
 """Sharding one decision's sieve points across ranks (one process per GPU).
 
-The 2^k sieve evaluations of Lemma 5.5 are independent (the paper vectorises
-over them, Sec. 7), so rank r of W evaluates a contiguous range of points with
+The 2^k sieve evaluations of Lemma 6.5 are independent (the paper vectorises
+over them, Sec. 8), so rank r of W evaluates a contiguous range of points with
 ``tmotif_decide(..., point_begin, point_end)`` on its own replica of the graph.
 The per-point sums are combined by XOR.  Collective libraries offer no XOR
 reduction, so the exchange is one all-gather of 8 bytes per point followed by

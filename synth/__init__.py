@@ -3,7 +3,7 @@
 These generators stand in for the paper's datasets (KONECT/SNAP graphs and
 transport feeds, Sec. 8) with the shapes its experiments use: configuration-
 model style power-law out-degrees, uniform timestamps, uniform or Zipf vertex
-colours, planted matching paths (Sec. 8.2-8.3).  They hold none of the sieve's
+colours, planted matching paths (Sec. 9.3 and 10.1).  They hold none of the sieve's
 arithmetic: both the GPU library and the CPU oracle receive the plain arrays
 they return.
 """
@@ -129,7 +129,7 @@ def tour_graph(n, avg_deg, t_max, num_colors, seed, name="tour"):
 def plant_paths(g: Graph, multiset, count, seed, t_max=None):
     """Plant `count` temporal paths whose colours equal `multiset`: pick
     distinct vertices with the needed colours and add arcs between
-    consecutive ones at strictly increasing random times (Sec. 8.3 planted
+    consecutive ones at strictly increasing random times (Sec. 10.1 planted
     solutions).  Returns the new graph and the planted (verts, times)."""
     r = _rng(seed)
     k = len(multiset)

@@ -1,8 +1,8 @@
 """GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
 
 GF(2^64) arithmetic is exact, so every comparison is bit-exact: each per-point
-sieve sum Q^A, each decision and each extracted path (Lemma 5.5 sieve over
-eq. gen-polynomial:3; extraction of Sec. 5.9).
+sieve sum Q^A, each decision and each extracted path (Lemma 6.5 sieve over
+eq. gen-polynomial:3; extraction of Sec. 6.9).
 """
 import random
 
@@ -216,7 +216,7 @@ def test_device_graph_build_matches_canonical_set(tm):
 
 
 # ---------------------------------------------------------------------------
-# Extraction (Sec. 5.9): same deterministic procedure -> the same path
+# Extraction (Sec. 6.9): same deterministic procedure -> the same path
 # ---------------------------------------------------------------------------
 def test_extraction_matches_oracle(tm):
     g, q = synth.config1_tiny()
@@ -295,7 +295,7 @@ def test_vertex_localized_sieve_matches_oracle(tm):
 
 
 # ---------------------------------------------------------------------------
-# EC-PathMotif (Sec. 6.3): the path's arc times are a given tuple T
+# EC-PathMotif (Sec. 7.3): the path's arc times are a given tuple T
 # ---------------------------------------------------------------------------
 def _ec_both(tm, G, g, k, ms, T, **kw):
     d = tm.tmotif_decide(G, k, ms, timestamps=T, **kw)

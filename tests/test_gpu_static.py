@@ -1,4 +1,4 @@
-"""GPU parity of the static preprocessing sieve (Sec. 7.1 (ii)).
+"""GPU parity of the static preprocessing sieve (Sec. 8.1 (ii)).
 
 Bit-exact against the oracle: the per-vertex sums Q_u, the per-point sums of
 the decision on the preprocessed graph, and the extracted paths (both

@@ -1,10 +1,10 @@
-"""Pins for the oracle's EC-PathMotif sieve (Sec. 6.3).
+"""Pins for the oracle's EC-PathMotif sieve (Sec. 7.3).
 
 EC-PathMotif fixes the arc times of the path to a strictly increasing tuple
 T = (j_1, ..., j_{k-1}).  The oracle evaluates the paper's EC recurrence (one
 value per vertex and walk length, layer l using only arcs at time j_{l-1}).
 It is checked against things fixed independently of that recurrence:
-enumeration of the temporal walks whose arc times are exactly T (Sec. 5.3),
+enumeration of the temporal walks whose arc times are exactly T (Sec. 6.3),
 exhaustive DFS for the decision, and the reduction of Lemma ectemppath:1
 (a static k-path exists iff the temporal graph with every edge present at
 times 1..k-1 has an EC path with T = (1, ..., k-1)).

@@ -1,6 +1,6 @@
 """Pins for the oracle's GF(2^64) arithmetic and random coefficients.
 
-The field is GF(2)[x]/(f), f = x^64 + x^4 + x^3 + x + 1 (Sec. 5.5 leaves b and f
+The field is GF(2)[x]/(f), f = x^64 + x^4 + x^3 + x + 1 (Sec. 6.5 leaves b and f
 open; b = 64 follows the paper's footnote and experiments).  Every check here
 is against mathematics that holds independently of the oracle: an independent
 Python polynomial product, field axioms, Fermat/Frobenius identities and

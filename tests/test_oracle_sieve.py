@@ -2,11 +2,11 @@
 
 Each check compares the oracle with something fixed independently of it:
 the polynomials printed in the paper's worked example (Fig.
-tempwalk-encoding-demo, Sec. 5.4), direct enumeration of temporal walks
-(Sec. 5.3), the determinant form of the sieve sum in characteristic 2
-(Lemmas 5.3/5.5), cancellation of walks that repeat a vertex (Lemma 5.1),
-exhaustive temporal DFS (the Sec. 8.1 baseline) and the k-path reduction of
-Lemma 4.1.
+tempwalk-encoding-demo, Sec. 6.4), direct enumeration of temporal walks
+(Sec. 6.3), the determinant form of the sieve sum in characteristic 2
+(Lemmas 6.3/6.5), cancellation of walks that repeat a vertex (Lemma 6.1),
+exhaustive temporal DFS (the Sec. 9.1 baseline) and the k-path reduction of
+Lemma 5.1.
 """
 import itertools
 import os
@@ -152,7 +152,7 @@ def test_dp_equals_enumeration_on_config1_brute_instance(oracle_mod):
 # Cancellation and one-sidedness
 # ---------------------------------------------------------------------------
 def test_repeated_vertex_walk_cancels(oracle_mod):
-    # a->b at 1, b->a at 2: the only 3-vertex walk is a,b,a (Lemma 5.1).
+    # a->b at 1, b->a at 2: the only 3-vertex walk is a,b,a (Lemma 6.1).
     n, src, dst, time = 2, [0, 1], [1, 0], [1, 2]
     color = [0, 1]
     pb = problem(n, src, dst, time, color, False, 3, [0, 1, 0], num_colors=2)
@@ -179,7 +179,7 @@ def test_duplicate_arc_cancels_without_dedupe(oracle_mod):
 
 
 def test_equal_times_are_not_consecutive(oracle_mod):
-    # Strictly increasing times (Sec. 3): a->b and b->c both at time 4 form no path.
+    # Strictly increasing times (Sec. 4): a->b and b->c both at time 4 form no path.
     f, q, _ = oracle.decide(3, [0, 1], [1, 2], [4, 4], [0, 1, 2], 3, 3, [0, 1, 2], seed=5)
     assert not f and q == 0
     f, q, _ = oracle.decide(3, [0, 1], [1, 2], [4, 5], [0, 1, 2], 3, 3, [0, 1, 2], seed=5)
@@ -239,7 +239,7 @@ def _static_kpath(n, edges, k):
 
 @pytest.mark.parametrize("trial", range(20))
 def test_ktemppath_reduction(oracle_mod, trial):
-    # Lemma 4.1: a static graph has a k-path iff the temporal graph with every
+    # Lemma 5.1: a static graph has a k-path iff the temporal graph with every
     # edge present at times 1..k-1 has a temporal path on k vertices; with a
     # single colour, PathMotif with M = {1^k} is k-TempPath.
     rng = random.Random(9000 + trial)
@@ -272,7 +272,7 @@ def test_point_range_matches_full(oracle_mod):
 
 
 # ---------------------------------------------------------------------------
-# Extraction (Sec. 5.9)
+# Extraction (Sec. 6.9)
 # ---------------------------------------------------------------------------
 def verify_path(n, src, dst, time, color, undirected, k, ms, verts, times, start=ANY, end=ANY, t_min=0, t_max=0):
     arcs = set(zip(src, dst, time))
@@ -323,7 +323,7 @@ def test_extraction_on_config1(oracle_mod):
 
 def test_time_window_bounds_are_inclusive(oracle_mod):
     # Path 0 -(3)-> 1 -(7)-> 2: the window [t_min, t_max] keeps arcs with
-    # t_min <= t <= t_max (the optimum-timestamp search of Sec. 5.8 asks for
+    # t_min <= t <= t_max (the optimum-timestamp search of Sec. 6.8 asks for
     # walks ending at latest time t').
     n, src, dst, time, color = 3, [0, 1], [1, 2], [3, 7], [0, 1, 2]
     for seed in range(1, 30):
@@ -336,7 +336,7 @@ def test_time_window_bounds_are_inclusive(oracle_mod):
 
 
 # ---------------------------------------------------------------------------
-# Localised sieve and extraction by localisation (Sec. 5.7, Sec. 5.9)
+# Localised sieve and extraction by localisation (Sec. 6.7, Sec. 6.9)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("trial", range(30))
 def test_arc_sums_equal_walk_enumeration(oracle_mod, trial):
@@ -389,7 +389,7 @@ def test_localized_extraction_on_config1(oracle_mod):
 
 
 # ---------------------------------------------------------------------------
-# Optimum timestamp (Sec. 5.8)
+# Optimum timestamp (Sec. 6.8)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("trial", range(40))
 def test_optimum_time_equals_brute_force(oracle_mod, trial):

@@ -1,10 +1,10 @@
-"""Pins for the oracle's static preprocessing sieve (Sec. 7.1 (ii)).
+"""Pins for the oracle's static preprocessing sieve (Sec. 8.1 (ii)).
 
 The temporal graph is merged into a static graph, and a vertex is kept iff it
 lies on some static path whose colours are M.  The oracle's forward/backward
 recurrence over eq. gen-polynomial:1 is checked against enumeration of the
 static walks (per-point monomials and the determinant identity of Lemmas
-5.3/5.5), against a direct search for the vertices on static matching paths,
+6.3/6.5), against a direct search for the vertices on static matching paths,
 and for soundness: removing the other vertices never changes a decision, and
 the preprocessed per-point values equal the temporal sieve on the graph
 restricted to the searched vertex set.
