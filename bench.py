@@ -37,23 +37,34 @@ UNIT = "edge-steps/s"
 WORKLOAD = ("power-law out-degree 2.1, n=1e6, m=1e7 (+50 planted arcs), t in [1,1000], 16 colours Zipf(1.0); "
             "PathMotif k=6 with one colour twice, 64 sieve points, GF(2^64)")
 
-# GB300 integer issue limit: 152 SMs x 4 sub-partitions x 32 lanes (one warp
-# instruction per sub-partition per clock) x 2070 MHz maximum SM clock.  A
-# single integer pipe (ALU: LOP3/SHF/IADD, or FMA-heavy: IMAD) sustains half of
-# it; a throughput probe measured 58-60 lanes/SM/clk for each alone.
-INT_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
+# Speed of light of the layer kernel, from GB300 unit counts at the maximum SM
+# clock (152 SMs, 2070 MHz) and per-product costs measured by ncu on the
+# library's register-resident probe (tmotif_gf_probe methods 0-2; see
+# profiles/gf_product_probe_instruction_counts.md).  A launch's lower-bound
+# time is the largest of three pipe times for its work:
+#   shared memory, 1 wavefront (128 B) per clock per SM: a table product
+#     reads 16 eight-byte entries (1 wavefront); a table build writes 2 KB
+#     (16 wavefronts);
+#   ALU pipe, 64 lanes per clock per SM: 47.1 ALU instructions per table
+#     product plus 1216 per table build (fitted to the probe at 64 and 128
+#     lanes per table: 66.1 and 56.6 per product), 92.6 per register product
+#     (probe counts less about 3-4 of probe loop work);
+#   FMA pipe: 9.28 sub-partition cycles per register product (4 per SM).
+SMS = 152
+SM_HZ = 2.070e9
+ALU_PER_REG, ALU_PER_TAB, ALU_PER_BUILD = 92.6, 47.1, 1216.0
+WF_PER_TAB, WF_PER_BUILD = 1.0, 16.0
+FMA_CYC_PER_REG = 9.28
 
-# Instructions per GF(2^64) product for the two forms the layer kernel uses,
-# from ncu smsp__inst_executed of the library's throughput probe
-# (tmotif_gf_probe) divided by its products:
-#   register multiply (Karatsuba over three 32x32 carry-less products with
-#   holes, plus the reduction) -- used for the x-products;
-#   shared nibble table of a multiplier common to 64 lanes (build amortised)
-#   -- used for the y-products.
-# (probe instructions per product, less about 4 of loop overhead; see
-# profiles/gf_product_probe_instruction_counts.md)
-OPS_PER_GF_MUL = 207.7
-OPS_PER_TABLE_MUL = 127.7
+
+def layer_bound_s(reg, tab, builds):
+    """Lower-bound seconds of one layer launch with `reg` register products,
+    `tab` table products and `builds` table builds."""
+    t_smem = (tab * WF_PER_TAB + builds * WF_PER_BUILD) / (SMS * SM_HZ)
+    t_alu = (reg * ALU_PER_REG + tab * ALU_PER_TAB + builds * ALU_PER_BUILD) / (SMS * 64 * SM_HZ)
+    t_fma = reg * FMA_CYC_PER_REG / (SMS * 4 * SM_HZ)
+    return max(t_smem, t_alu, t_fma), {"smem": t_smem, "alu": t_alu, "fma": t_fma}
+
 
 # DRAM traffic of one layer launch from an ncu capture, valid only for the
 # layer-kernel source it was taken on (source_sha() below, first 16 hex).
@@ -271,8 +282,17 @@ def serving_benchmark(tm, stream, requests=128, load=0.7, seed=8):
         return {"queries_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3)}
 
+    by_k = {}
+    for kk in sorted(set(int(q.k) for q, _ in reqs)):
+        idx = [i for i, (q, _) in enumerate(reqs) if q.k == kk]
+        by_k[kk] = {"n": len(idx), "service_ms": float(np.mean([service[i] for i in idx]) * 1e3),
+                    "plain_p50_ms": float(np.percentile(lat_plain[idx], 50) * 1e3),
+                    "served_p50_ms": float(np.percentile(lat_served[idx], 50) * 1e3),
+                    "plain_max_ms": float(np.max(lat_plain[idx]) * 1e3),
+                    "served_max_ms": float(np.max(lat_served[idx]) * 1e3)}
     return {"workload": "power-law n=2e6 m=2e7 t<=1000 16 colours; requests k~U{3..10}, 30% extract",
             "requests": len(reqs), "arrival_rate_per_s": rate, "plain_capacity_per_s": capacity,
+            "by_k": by_k,
             "plain": summary(lat_plain, done_plain), "served": summary(lat_served, done_at),
             "saturated_queries_per_s": {"plain": capacity, "served": len(reqs) / t_sat},
             "results_match": bool(match)}
@@ -364,22 +384,28 @@ def run_ours(args):
     value = world * work_units * args.steps / (total_ms / 1e3)
 
     # roofline of the dominant kernel (the layer kernel), from the library's
-    # CUDA events around every layer launch during the timed region
+    # CUDA events around every layer launch during the timed region: achieved
+    # GF(2^64) products per second against the speed-of-light rate of the
+    # same product mix (layer_bound_s)
     nl = max(stats["layer_launches"], 1)
     layer_ms = stats["layer_ms"] / nl
     muls = stats["layer_gf_muls"] / nl
     tmuls = stats["layer_table_muls"] / nl
-    ops = tmuls * OPS_PER_TABLE_MUL + (muls - tmuls) * OPS_PER_GF_MUL
-    achieved = ops / (layer_ms / 1e3) / 1e12
+    builds = stats["layer_table_builds"] / nl
+    t_min, pipes = layer_bound_s(muls - tmuls, tmuls, builds)
+    achieved = muls / (layer_ms / 1e3) / 1e9
+    peak = muls / t_min / 1e9
     sha = source_sha()
     traffic = LAYER_TRAFFIC["bytes_per_launch"] if LAYER_TRAFFIC["source_sha"] == sha else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": INT_PEAK_TOPS, "unit": "Tinstr/s",
-                "frac": achieved / INT_PEAK_TOPS, "traffic": traffic,
-                "kernel": "k_layer (eq. gen-polynomial:3 layer)", "layer_ms_per_launch": layer_ms,
-                "gf_muls_per_launch": muls, "table_muls_per_launch": tmuls,
-                "instr_per_product": {"register": OPS_PER_GF_MUL, "table": OPS_PER_TABLE_MUL},
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G GF(2^64) products/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_layer (eq. gen-polynomial:3 layer)",
+                "model": "integer/shared-memory pipes from unit counts at 2070 MHz; binding pipe: "
+                         + max(pipes, key=pipes.get),
+                "pipe_ms": {k: v * 1e3 for k, v in pipes.items()}, "layer_ms_per_launch": layer_ms,
+                "gf_muls_per_launch": muls, "table_muls_per_launch": tmuls, "table_builds_per_launch": builds,
                 "algorithmic_bytes_per_launch": stats["layer_bytes"] / nl,
-                "achieved_gbs": stats["layer_bytes"] / nl / (layer_ms / 1e3) / 1e9,
+                "achieved_hbm_gbs": stats["layer_bytes"] / nl / (layer_ms / 1e3) / 1e9,
                 "layer_share_of_step": stats["layer_ms"] / total_ms if total_ms else None}
 
     # end to end through the C ABI with host buffers: upload + build the graph,

@@ -152,6 +152,7 @@ typedef struct {
     uint64_t layer_bytes;      /* algorithmic bytes of the layer kernels    */
     uint64_t layer_gf_muls;    /* GF(2^64) products in the layer kernels    */
     uint64_t layer_table_muls; /* ... of which by a shared multiplier table  */
+    uint64_t layer_table_builds; /* shared tables built (one per arc and table layer) */
 } tmotif_stats;
 
 /* Build the resident graph: validate, orient, drop self-loops, merge
@@ -241,6 +242,16 @@ void tmotif_server_destroy(tmotif_server_t s);
 /* Profiling counters for a graph (see tmotif_stats).  set_profiling(g, 1)
  * enables per-kernel events and clears the counters. */
 int tmotif_set_profiling(tmotif_graph_t g, int on);
+
+/* Launch shape of the generating-function layer kernel for lane width L (a
+ * power of two in [4, 128]) on graph g: arcs per team chunk (64, 128 or 256)
+ * and the register-shape variant (0 = the compiler's budget, 1 = at most 64
+ * registers per thread, 2 = at most 128; only 0 at L < 16 and L = 128).  The library's autotuner picks it on the first
+ * decision that needs it, by timing every candidate on one layer; set pins
+ * it (results never depend on it), get reads it (NOT_FOUND when none is set
+ * yet).  Errors: INVALID for a bad L, chunk or variant. */
+int tmotif_set_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t chunk, uint32_t variant);
+int tmotif_get_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t *chunk, uint32_t *variant);
 int tmotif_get_stats(tmotif_graph_t g, tmotif_stats *out);
 
 /* Diagnostic: out[i] = a[i] * b[i] in GF(2^64) computed by the device
@@ -251,8 +262,10 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
  * kernel uses, on register-resident data (no memory traffic), 8 blocks of 256
  * threads per SM: method 0 = register multiply (Karatsuba over 32x32
  * carry-less products with holes); method 1 = a warp builds the 16 x 16 nibble
- * table of one multiplier in shared memory and applies it to 64 lanes.  Runs
- * `iters` rounds; ms receives the device time, products the products done. */
+ * table of one multiplier in shared memory and applies it to 64 lanes (2 per
+ * thread); method 2 = the same table applied to 128 lanes (4 per thread).
+ * Runs `iters` rounds; ms receives the device time, products the products
+ * done.  INVALID for another method or iters = 0. */
 int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products);
 
 /* Decision without any memory allocation.  The paper has no counterpart: this

@@ -61,7 +61,8 @@ class _Stats(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("layer_launches", C.c_uint64), ("layer_ms", C.c_double),
                 ("prep_ms", C.c_double), ("coef_ms", C.c_double), ("other_ms", C.c_double),
                 ("layer_arc_lanes", C.c_uint64), ("layer_cp_lanes", C.c_uint64), ("layer_bytes", C.c_uint64),
-                ("layer_gf_muls", C.c_uint64), ("layer_table_muls", C.c_uint64)]
+                ("layer_gf_muls", C.c_uint64), ("layer_table_muls", C.c_uint64),
+                ("layer_table_builds", C.c_uint64)]
 
 
 def _load():
@@ -84,6 +85,8 @@ def _load():
         "tmotif_poll": (C.c_int, [P, C.c_uint64, C.POINTER(_Decision), P, P, C.POINTER(C.c_int)]),
         "tmotif_server_destroy": (None, [P]),
         "tmotif_set_profiling": (C.c_int, [P, C.c_int]),
+        "tmotif_set_layer_shape": (C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32]),
+        "tmotif_get_layer_shape": (C.c_int, [P, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
         "tmotif_get_stats": (C.c_int, [P, C.POINTER(_Stats)]),
         "tmotif_gf_mul_batch": (C.c_int, [P, P, P, C.c_uint64]),
         "tmotif_gf_probe": (C.c_int, [C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
@@ -268,6 +271,22 @@ def tmotif_decide_batch(graphs, queries):
 
 def tmotif_set_profiling(g: Graph, on=True):
     _check(_lib.tmotif_set_profiling(g.handle, int(bool(on))))
+
+
+def tmotif_set_layer_shape(g: Graph, L: int, chunk: int, variant: int = 0):
+    """Pin the layer kernel's launch shape for lane width L (results never
+    depend on it; the autotuner picks one when none is set)."""
+    _check(_lib.tmotif_set_layer_shape(g.handle, L, chunk, variant))
+
+
+def tmotif_get_layer_shape(g: Graph, L: int):
+    """(chunk, variant) for lane width L, or None when none is set yet."""
+    c, v = C.c_uint32(0), C.c_uint32(0)
+    rc = _lib.tmotif_get_layer_shape(g.handle, L, C.byref(c), C.byref(v))
+    if rc == 6:
+        return None
+    _check(rc)
+    return int(c.value), int(v.value)
 
 
 def tmotif_get_stats(g: Graph) -> dict:

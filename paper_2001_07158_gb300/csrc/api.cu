@@ -578,6 +578,32 @@ int tmotif_set_profiling(tmotif_graph_t g, int on)
     return TMOTIF_OK;
 }
 
+static bool valid_shape(uint32_t L, uint32_t chunk, uint32_t variant)
+{
+    const bool pow2 = L >= 4 && L <= 128 && (L & (L - 1)) == 0;
+    const bool ch = chunk == 64 || chunk == 128 || chunk == 256;
+    const bool var = variant == 0 || (variant <= 2 && L >= 16 && L <= 64);
+    return pow2 && ch && var;
+}
+
+int tmotif_set_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t chunk, uint32_t variant)
+{
+    if (!g) return fail(TMOTIF_ERR_INVALID, "null graph").code;
+    if (!valid_shape(L, chunk, variant)) return fail(TMOTIF_ERR_INVALID, "bad layer shape").code;
+    g->layer_tune[L] = {chunk, variant};
+    return TMOTIF_OK;
+}
+
+int tmotif_get_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t *chunk, uint32_t *variant)
+{
+    if (!g || !chunk || !variant) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    auto it = g->layer_tune.find(L);
+    if (it == g->layer_tune.end()) return fail(TMOTIF_ERR_NOT_FOUND, "no layer shape for this lane width").code;
+    *chunk = it->second.first;
+    *variant = it->second.second;
+    return TMOTIF_OK;
+}
+
 int tmotif_get_stats(tmotif_graph_t g, tmotif_stats *out)
 {
     if (!g || !out) return fail(TMOTIF_ERR_INVALID, "null argument").code;
@@ -593,7 +619,7 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
 
 int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products)
 {
-    if (!ms || !products || (method != 0 && method != 1) || iters == 0)
+    if (!ms || !products || method < 0 || method > 2 || iters == 0)
         return fail(TMOTIF_ERR_INVALID, "bad probe arguments").code;
     return gf_probe(method, iters, ms, (u64 *)products).code;
 }

@@ -101,15 +101,38 @@ __device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthr
     }
 }
 
+// Lookup side.  The table must start on a 2 KB boundary of shared memory, so
+// that its shared address has bits 0..10 clear: the address of entry b of row
+// i is then (address | (b' << 3)) + 128 i, where b' = b ^ 2(i & 7) is the
+// swizzled column.  XORing s once with 0xECA86420ECA86420 (nibble i of the
+// constant is 2(i & 7)) swizzles all sixteen nibbles at once, so each lookup
+// costs a shift and one three-input logic op for its address, and the row
+// offset rides in the load's immediate.
+#define TM_LDS64(out, addr, off) asm volatile("ld.shared.b64 %0, [%1+" #off "];" : "=l"(out) : "r"(addr))
+
 __device__ __forceinline__ u64 gf_table_mul(const u64 *tab, u64 s)
 {
-    const u32 lo = (u32)s, hi = (u32)(s >> 32);
-    u64 r = 0;
-#pragma unroll
-    for (int i = 0; i < 8; i++) r ^= tab[i * 16 + (((lo >> (4 * i)) & 15u) ^ (u32)((i & 7) << 1))];
-#pragma unroll
-    for (int i = 0; i < 8; i++) r ^= tab[(i + 8) * 16 + (((hi >> (4 * i)) & 15u) ^ (u32)(((i + 8) & 7) << 1))];
-    return r;
+    const u32 ta = (u32)__cvta_generic_to_shared(tab);
+    const u64 sw = s ^ 0xECA86420ECA86420ull;
+    const u32 lo = (u32)sw, hi = (u32)(sw >> 32);
+    u64 v0, v1, v2, v3, v4, v5, v6, v7, v8, v9, v10, v11, v12, v13, v14, v15;
+    TM_LDS64(v0, ((lo << 3) & 0x78u) | ta, 0);
+    TM_LDS64(v1, ((lo >> 1) & 0x78u) | ta, 128);
+    TM_LDS64(v2, ((lo >> 5) & 0x78u) | ta, 256);
+    TM_LDS64(v3, ((lo >> 9) & 0x78u) | ta, 384);
+    TM_LDS64(v4, ((lo >> 13) & 0x78u) | ta, 512);
+    TM_LDS64(v5, ((lo >> 17) & 0x78u) | ta, 640);
+    TM_LDS64(v6, ((lo >> 21) & 0x78u) | ta, 768);
+    TM_LDS64(v7, ((lo >> 25) & 0x78u) | ta, 896);
+    TM_LDS64(v8, ((hi << 3) & 0x78u) | ta, 1024);
+    TM_LDS64(v9, ((hi >> 1) & 0x78u) | ta, 1152);
+    TM_LDS64(v10, ((hi >> 5) & 0x78u) | ta, 1280);
+    TM_LDS64(v11, ((hi >> 9) & 0x78u) | ta, 1408);
+    TM_LDS64(v12, ((hi >> 13) & 0x78u) | ta, 1536);
+    TM_LDS64(v13, ((hi >> 17) & 0x78u) | ta, 1664);
+    TM_LDS64(v14, ((hi >> 21) & 0x78u) | ta, 1792);
+    TM_LDS64(v15, ((hi >> 25) & 0x78u) | ta, 1920);
+    return ((v0 ^ v1 ^ v2) ^ (v3 ^ v4 ^ v5)) ^ ((v6 ^ v7 ^ v8) ^ (v9 ^ v10 ^ v11)) ^ ((v12 ^ v13 ^ v14) ^ v15);
 }
 
 // ---------------------------------------------------------------------------

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -135,6 +136,9 @@ struct Graph {
     u64 m_static = 0;
     u32 *s_in = nullptr, *s_out = nullptr;
     StaticWork sw;
+    // layer-kernel launch shape per lane width, chosen by the autotuner on the
+    // first decision that needs it: (arcs per team chunk, kernel variant)
+    std::map<u32, std::pair<u32, u32>> layer_tune;
 };
 
 // Arc filter of a query, passed by value to the filter kernel: the time
@@ -197,6 +201,7 @@ struct Job {
     // sizes known after prep
     u64 mf = 0, ncp = 0, n_act = 0;
     u32 L = 0, T = 0, lane_groups = 0, chunk = 128;
+    u32 variant = 0;      // layer kernel shape (see the autotuner)
     u64 n_chunks = 0;
     // progress
     u32 r = 0;            // repeat

@@ -154,48 +154,53 @@ __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L,
                                               const u32 *slot_begin, const u32 *slot_count, QueryKeys keys,
                                               const u64 *wtab, u64 *x)
 {
-    __shared__ __align__(128) u64 tabs[8][256];
+    __shared__ __align__(2048) u64 tabs[8][256];  // tables on 2 KB boundaries
     u64 *tab = tabs[threadIdx.x >> 5];
     const int tt = threadIdx.x & 31;
     const u64 v = (u64)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (v >= n_act) return;  // whole warp leaves together
     const u32 u = list[v], c = color[u];
     const u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
-    u64 s0 = 0, s1 = 0;
+    u64 s[4] = {0, 0, 0, 0};  // lanes tt, tt + 32, tt + 64, tt + 96 (L <= 128)
     for (u32 d = d0; d < d1; d++) {
         __syncwarp();
         gf_table_build(tab, coef_v(keys, u, d), tt, 32);
         __syncwarp();
-        if ((u32)tt < L) s0 ^= gf_table_mul(tab, wtab[(u64)d * L + tt]);
-        if ((u32)tt + 32 < L) s1 ^= gf_table_mul(tab, wtab[(u64)d * L + tt + 32]);
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if ((u32)tt + 32 * i < L) s[i] ^= gf_table_mul(tab, wtab[(u64)d * L + tt + 32 * i]);
     }
-    if ((u32)tt < L) x[(u64)u * L + tt] = s0;
-    if ((u32)tt + 32 < L) x[(u64)u * L + tt + 32] = s1;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        if ((u32)tt + 32 * i < L) x[(u64)u * L + tt + 32 * i] = s[i];
 }
 
 // ---------------------------------------------------------------------------
 // Layer kernel: eq. (gen-polynomial:3), one walk length per job per launch.
 // ---------------------------------------------------------------------------
-// A team of T threads owns 2T consecutive lanes (16 bytes per thread) of one
-// job and walks one chunk of whole in-segments in arc order.  Segments are
-// never split, so a running XOR is the prefix of eq. (3)'s stay term.  With
-// TAB the team builds, per arc, the nibble table of y_{e,l-1} in shared memory
-// and every lane's y-product is 16 table loads; x-products (one per
-// checkpoint and per segment at the last layer) use the register multiply.
-// One launch can carry many jobs (njobs > 0: the team's job is found in the
-// prefix of team counts); njobs = 0 means the single job in `one`.  At the
-// last layer every team writes its lanes' sums to the job's partial array.
-template <int T, bool TAB>
+// A team of T threads owns T * LPT consecutive lanes (LPT = 2 or 4 lanes, 16
+// or 32 bytes, per thread) of one job and walks one chunk of whole
+// in-segments in arc order.  Segments are never split, so a running XOR is
+// the prefix of eq. (3)'s stay term.  With TAB the team builds, per arc, the
+// nibble table of y_{e,l-1} in shared memory and every lane's y-product is 16
+// table loads; x-products (one per checkpoint and per segment at the last
+// layer) use the register multiply.  One launch can carry many jobs
+// (njobs > 0: the team's job is found in the prefix of team counts); njobs =
+// 0 means the single job in `one`.  At the last layer every team writes its
+// lanes' sums to the job's partial array.
+template <int T, bool TAB, int LPT>
 __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *tab)
 {
     const int tt = threadIdx.x % T;
     const u32 team_mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (((threadIdx.x & 31) / T) * T));
     const u64 chunk = team / p.lane_groups;
     if (chunk >= p.n_chunks) return;
-    const u32 lane0 = (u32)(team % p.lane_groups) * (2 * T) + 2 * tt;
+    const u32 lane0 = (u32)(team % p.lane_groups) * (LPT * T) + LPT * tt;
     const u64 Lw = p.L;
     const bool last = (p.ell == p.k);
-    u64 q0 = 0, q1 = 0;
+    u64 q[LPT], xc[LPT], acc[LPT];
+#pragma unroll
+    for (int i = 0; i < LPT; i++) q[i] = xc[i] = acc[i] = 0;
 
     const u64 b0 = chunk * p.chunk;
     const u64 b1 = min(b0 + p.chunk, p.m_f);
@@ -204,7 +209,6 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
     if (b1 < p.m_f && p.dst[b1] == p.dst[b1 - 1]) stop = p.seg_hi[p.dst[b1]];
 
     u32 cur = NONE;
-    u64 xc0 = 0, xc1 = 0, acc0 = 0, acc1 = 0;
     for (u64 base = begin; base < stop; base += T) {
         const u64 e = base + tt;
         u32 s = 0, d = NONE, ci = NONE, co = NONE;
@@ -226,76 +230,90 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
             const u64 yj = __shfl_sync(team_mask, y, j, T);
             if (dj != cur) {
                 if (last && cur != NONE && (p.end == NONE || cur == p.end)) {
-                    q0 ^= gf_mul(xc0, acc0);
-                    q1 ^= gf_mul(xc1, acc1);
+#pragma unroll
+                    for (int i = 0; i < LPT; i++) q[i] ^= gf_mul(xc[i], acc[i]);
                 }
                 cur = dj;
-                acc0 = acc1 = 0;
-                const ulonglong2 xv = *(const ulonglong2 *)(p.x + (u64)dj * Lw + lane0);
-                xc0 = xv.x;
-                xc1 = xv.y;
-            }
-            bool have = false;
-            ulonglong2 in;
-            if (p.ell == 2) {
-                if (p.start == NONE || sj == p.start) {
-                    in = *(const ulonglong2 *)(p.x + (u64)sj * Lw + lane0);
-                    have = true;
+#pragma unroll
+                for (int i = 0; i < LPT; i += 2) {
+                    const ulonglong2 xv = *(const ulonglong2 *)(p.x + (u64)dj * Lw + lane0 + i);
+                    xc[i] = xv.x;
+                    xc[i + 1] = xv.y;
+                    acc[i] = acc[i + 1] = 0;
                 }
-            } else if (cij != NONE) {
-                in = *(const ulonglong2 *)(p.Cin + (u64)cij * Lw + lane0);
-                have = true;
             }
-            if (have) {  // uniform across the team
-                u64 h0, h1;
+            const u64 *row = nullptr;
+            if (p.ell == 2) {
+                if (p.start == NONE || sj == p.start) row = p.x + (u64)sj * Lw + lane0;
+            } else if (cij != NONE) {
+                row = p.Cin + (u64)cij * Lw + lane0;
+            }
+            if (row) {  // uniform across the team
+                u64 in[LPT], h[LPT];
+#pragma unroll
+                for (int i = 0; i < LPT; i += 2) {
+                    const ulonglong2 v = *(const ulonglong2 *)(row + i);
+                    in[i] = v.x;
+                    in[i + 1] = v.y;
+                }
                 if (TAB) {
                     __syncwarp(team_mask);  // earlier lookups are done
                     gf_table_build(tab, yj, tt, T);
                     __syncwarp(team_mask);  // table complete
-                    h0 = gf_table_mul(tab, in.x);
-                    h1 = gf_table_mul(tab, in.y);
+#pragma unroll
+                    for (int i = 0; i < LPT; i++) h[i] = gf_table_mul(tab, in[i]);
                 } else {
-                    h0 = gf_mul(yj, in.x);
-                    h1 = gf_mul(yj, in.y);
+#pragma unroll
+                    for (int i = 0; i < LPT; i++) h[i] = gf_mul(yj, in[i]);
                 }
-                acc0 ^= h0;
-                acc1 ^= h1;
+#pragma unroll
+                for (int i = 0; i < LPT; i++) acc[i] ^= h[i];
                 if (last && p.arc_sum && (p.end == NONE || dj == p.end)) {
                     // this arc's last-layer term, summed over the lanes
-                    u64 v = gf_mul(xc0, h0) ^ gf_mul(xc1, h1);
+                    u64 v = 0;
+#pragma unroll
+                    for (int i = 0; i < LPT; i++) v ^= gf_mul(xc[i], h[i]);
 #pragma unroll
                     for (int o = T / 2; o > 0; o >>= 1) v ^= __shfl_xor_sync(team_mask, v, o, T);
                     if (tt == 0) p.arc_sum[base + j] ^= v;
                 }
             }
             if (coj != NONE) {
-                ulonglong2 o;
-                o.x = gf_mul(xc0, acc0);
-                o.y = gf_mul(xc1, acc1);
-                *(ulonglong2 *)(p.Cout + (u64)coj * Lw + lane0) = o;
+#pragma unroll
+                for (int i = 0; i < LPT; i += 2) {
+                    ulonglong2 o;
+                    o.x = gf_mul(xc[i], acc[i]);
+                    o.y = gf_mul(xc[i + 1], acc[i + 1]);
+                    *(ulonglong2 *)(p.Cout + (u64)coj * Lw + lane0 + i) = o;
+                }
             }
         }
     }
     if (last) {
         if (cur != NONE && (p.end == NONE || cur == p.end)) {
-            q0 ^= gf_mul(xc0, acc0);
-            q1 ^= gf_mul(xc1, acc1);
+#pragma unroll
+            for (int i = 0; i < LPT; i++) q[i] ^= gf_mul(xc[i], acc[i]);
         }
-        *(ulonglong2 *)(p.partial + chunk * Lw + lane0) = make_ulonglong2(q0, q1);
+#pragma unroll
+        for (int i = 0; i < LPT; i += 2)
+            *(ulonglong2 *)(p.partial + chunk * Lw + lane0 + i) = make_ulonglong2(q[i], q[i + 1]);
     }
 }
 
 // MULTI = false: the single job in `one` (read from parameter space);
 // MULTI = true: the team's job is found in the prefix of team counts.
-template <int T, bool TAB, bool MULTI>
-__global__ void __launch_bounds__(256) k_layer(LayerParams one, const LayerParams *__restrict__ jobs,
-                                               const u64 *__restrict__ team_prefix, u32 njobs)
+template <int T, bool TAB, bool MULTI, int LPT>
+__device__ __forceinline__ void layer_kernel(const LayerParams &one, const LayerParams *__restrict__ jobs,
+                                             const u64 *__restrict__ team_prefix, u32 njobs)
 {
     extern __shared__ __align__(16) u64 smem[];
-    u64 *tab = smem + (size_t)(threadIdx.x / T) * 256;
+    // team tables of 2 KB each, starting on a 2 KB boundary of shared memory
+    // (the launch adds 2 KB of slack for the rounding)
+    const u32 sa = (u32)__cvta_generic_to_shared(smem);
+    u64 *tab = smem + (((2048u - (sa & 2047u)) & 2047u) >> 3) + (size_t)(threadIdx.x / T) * 256;
     const u64 team = (u64)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
     if (!MULTI) {
-        layer_team<T, TAB>(one, team, tab);
+        layer_team<T, TAB, LPT>(one, team, tab);
         return;
     }
     if (team >= team_prefix[njobs]) return;
@@ -305,7 +323,24 @@ __global__ void __launch_bounds__(256) k_layer(LayerParams one, const LayerParam
         if (team_prefix[mid] <= team) lo = mid;
         else hi = mid;
     }
-    layer_team<T, TAB>(jobs[lo], team - team_prefix[lo], tab);
+    layer_team<T, TAB, LPT>(jobs[lo], team - team_prefix[lo], tab);
+}
+
+// k_layer: the compiler's own register budget for 256-thread blocks;
+// k_layer_mb: the blocks of 256 threads per SM the allocation must allow
+// (2: up to 128 registers per thread, 4: 64).  These are the register shapes
+// the autotuner picks from.
+template <int T, bool TAB, bool MULTI, int LPT>
+__global__ void __launch_bounds__(256) k_layer(LayerParams one, const LayerParams *__restrict__ jobs,
+                                               const u64 *__restrict__ team_prefix, u32 njobs)
+{
+    layer_kernel<T, TAB, MULTI, LPT>(one, jobs, team_prefix, njobs);
+}
+
+template <int T, bool TAB, int LPT, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_layer_mb(LayerParams one)
+{
+    layer_kernel<T, TAB, false, LPT>(one, nullptr, nullptr, 0);
 }
 
 // out[lane] = XOR over chunks of partial[chunk * L + lane]; blockDim.x = L,
@@ -336,27 +371,36 @@ __global__ void k_gf_mul(const u64 *a, const u64 *b, u64 *out, u64 n)
 template <int METHOD>
 __global__ void __launch_bounds__(256) k_gf_probe(u32 iters, u64 seed, u64 *sink)
 {
-    __shared__ __align__(16) u64 tabs[8][256];
+    __shared__ __align__(2048) u64 tabs[8][256];  // tables on 2 KB boundaries
     u64 *tab = tabs[threadIdx.x >> 5];
     const int tt = threadIdx.x & 31;
-    u64 a0 = mix64(seed + blockIdx.x * 256 + threadIdx.x), a1 = mix64(a0), y = mix64(seed ^ blockIdx.x);
-    u64 acc0 = 0, acc1 = 0;
+    constexpr int LPT = METHOD == 2 ? 4 : 2;  // lanes per thread
+    u64 a[LPT], acc[LPT];
+    a[0] = mix64(seed + blockIdx.x * 256 + threadIdx.x);
+#pragma unroll
+    for (int i = 1; i < LPT; i++) a[i] = mix64(a[i - 1]);
+#pragma unroll
+    for (int i = 0; i < LPT; i++) acc[i] = 0;
+    u64 y = mix64(seed ^ blockIdx.x);
     for (u32 it = 0; it < iters; it++) {
         if (METHOD == 0) {
-            acc0 ^= gf_mul(y, a0);
-            acc1 ^= gf_mul(y, a1);
+#pragma unroll
+            for (int i = 0; i < LPT; i++) acc[i] ^= gf_mul(y, a[i]);
         } else {
             __syncwarp();
             gf_table_build(tab, y, tt, 32);
             __syncwarp();
-            acc0 ^= gf_table_mul(tab, a0);
-            acc1 ^= gf_table_mul(tab, a1);
+#pragma unroll
+            for (int i = 0; i < LPT; i++) acc[i] ^= gf_table_mul(tab, a[i]);
         }
-        a0 += acc1;
-        a1 ^= acc0;
+#pragma unroll
+        for (int i = 0; i < LPT; i++) a[i] += acc[(i + 1) % LPT];
         y += TM_GOLDEN;
     }
-    if ((acc0 ^ acc1) == 0x5151ull) sink[0] = acc0;
+    u64 r = 0;
+#pragma unroll
+    for (int i = 0; i < LPT; i++) r ^= acc[i];
+    if (r == 0x5151ull) sink[0] = r;
 }
 
 Status gf_probe(int method, u32 iters, double *ms, u64 *products)
@@ -370,11 +414,13 @@ Status gf_probe(int method, u32 iters, double *ms, u64 *products)
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    if (method == 0) k_gf_probe<0><<<blocks, 256>>>(4, 1, sink);
-    else k_gf_probe<1><<<blocks, 256>>>(4, 1, sink);
-    cudaEventRecord(a);
-    if (method == 0) k_gf_probe<0><<<blocks, 256>>>(iters, 7, sink);
-    else k_gf_probe<1><<<blocks, 256>>>(iters, 7, sink);
+    for (int pass = 0; pass < 2; pass++) {  // warm-up launch, then the timed one
+        if (pass == 1) cudaEventRecord(a);
+        const u32 n = pass ? iters : 4;
+        if (method == 0) k_gf_probe<0><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
+        else if (method == 1) k_gf_probe<1><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
+        else k_gf_probe<2><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
+    }
     cudaEventRecord(b);
     cudaError_t e = cudaEventSynchronize(b);
     float f = 0;
@@ -385,7 +431,7 @@ Status gf_probe(int method, u32 iters, double *ms, u64 *products)
     if (e != cudaSuccess) return cuda_fail(e, "gf_probe");
     TM_CUDA(cudaGetLastError());
     *ms = f;
-    *products = (u64)blocks * 256 * 2 * iters;
+    *products = (u64)blocks * 256 * (method == 2 ? 4 : 2) * iters;
     return Status();
 }
 
@@ -411,8 +457,9 @@ Status gf_mul_batch(const u64 *a, const u64 *b, u64 *out, u64 n)
 // ---------------------------------------------------------------------------
 static inline unsigned grid_for(u64 items, int threads) { return (unsigned)((items + threads - 1) / threads); }
 
-static const u32 LANES_MAX = 64;  // lanes per batch (one warp owns 64 lanes)
-static const u32 CHUNK = 128;     // arcs per team chunk (whole in-segments)
+static const u32 LANES_MAX = 128;  // lanes per batch (one warp owns up to 128 lanes)
+static const u32 CHUNK = 128;     // arcs per team chunk (whole in-segments), untuned
+static const u32 CHUNK_MIN = 64;  // smallest chunk the autotuner tries (partials sized for it)
 static const size_t PIN_BYTES = 64 + LANES_MAX * 8;
 
 static Status ensure_pinned(Workspace &w, size_t bytes = PIN_BYTES)
@@ -431,7 +478,7 @@ size_t job_bytes(const Job &j)
     const u64 n = j.g->n, m = j.mf ? j.mf : j.g->m, L = j.L ? j.L : LANES_MAX;
     const u64 ncp = j.mf ? j.ncp : m;
     return (size_t)(n * (1 + 8) + (j.g->m + 1) * 4 + m * 28 + n * L * 8 + 2 * ncp * L * 8 +
-                    ((m + CHUNK - 1) / CHUNK) * L * 8 + 4096);
+                    ((m + CHUNK_MIN - 1) / CHUNK_MIN) * L * 8 + 4096);
 }
 
 Status job_prep(Job &j)
@@ -530,20 +577,28 @@ Status job_prep(Job &j)
         size_t room = 0;
         TM_TRY(device_headroom(&room));
         room += w.x.bytes + w.C0.bytes + w.C1.bytes + w.partial.bytes;
-        const u64 per_lane = ((u64)n + 2 * std::max<u64>(j.ncp, 1) + (j.mf + CHUNK - 1) / CHUNK) * 8;
+        const u64 per_lane = ((u64)n + 2 * std::max<u64>(j.ncp, 1) + (j.mf + CHUNK_MIN - 1) / CHUNK_MIN) * 8;
         while (L > 4 && per_lane * L > room / 10 * 9) L >>= 1;
     }
     j.L = L;
-    j.T = L / 2 > 32 ? 32 : L / 2;
-    j.lane_groups = L / (2 * j.T);
+    j.T = L / 2 > 32 ? 32 : L / 2;  // 2 lanes per thread, 4 at L = 128
+    j.lane_groups = 1;
     j.chunk = CHUNK;
-    j.n_chunks = (j.mf + CHUNK - 1) / CHUNK;
+    j.variant = 0;
+    {  // the launch shape the autotuner chose for this graph and lane width
+        auto it = g.layer_tune.find(L);
+        if (it != g.layer_tune.end()) {
+            j.chunk = it->second.first;
+            j.variant = it->second.second;
+        }
+    }
+    j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
     TM_TRY(w.x.reserve((u64)n * L * 8));
     TM_TRY(w.C0.reserve(std::max<u64>(j.ncp, 1) * L * 8));
     TM_TRY(w.C1.reserve(std::max<u64>(j.ncp, 1) * L * 8));
     TM_TRY(w.out.reserve(L * 8));
     TM_TRY(w.wtab.reserve((u64)q.k * L * 8));
-    TM_TRY(w.partial.reserve(j.n_chunks * L * 8));
+    TM_TRY(w.partial.reserve(((j.mf + CHUNK_MIN - 1) / CHUNK_MIN) * L * 8));
     if (j.localize) {
         TM_TRY(w.arc_sum.reserve(j.mf * 8));
         TM_CUDA(cudaMemsetAsync(w.arc_sum.p, 0, j.mf * 8, st));
@@ -604,37 +659,65 @@ LayerParams job_layer_params(const Job &j)
     return lp;
 }
 
-template <int T, bool TAB>
+// One launch of the layer kernel.  MINB = 0: k_layer (single- or multi-job);
+// MINB > 0: k_layer_mb with that register bound (single-job only).
+template <int T, bool TAB, int LPT, int MINB>
 static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const LayerParams *jobs,
                              const u64 *prefix, u32 njobs, u64 teams)
 {
     const int threads = 256;
     const u64 teams_per_block = threads / T;
     const unsigned blocks = (unsigned)((teams + teams_per_block - 1) / teams_per_block);
-    const size_t smem = TAB ? teams_per_block * 256 * 8 : 16;
+    const size_t smem = TAB ? teams_per_block * 256 * 8 + 2048 : 16;
     static bool attr_set = false;
     if (!attr_set) {
-        TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     160 * 1024));
-        TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     160 * 1024));
+        if constexpr (MINB == 0) {
+            TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB, false, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         160 * 1024));
+            TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB, true, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         160 * 1024));
+        } else {
+            TM_CUDA(cudaFuncSetAttribute(k_layer_mb<T, TAB, LPT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         160 * 1024));
+        }
         attr_set = true;
     }
     if (!blocks) return Status();
-    if (njobs == 0) k_layer<T, TAB, false><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
-    else k_layer<T, TAB, true><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
+    if constexpr (MINB == 0) {
+        if (njobs == 0) k_layer<T, TAB, false, LPT><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
+        else k_layer<T, TAB, true, LPT><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
+    } else {
+        if (njobs != 0) return fail(TMOTIF_ERR_UNSUPPORTED, "multi-job launches use the default kernel form");
+        k_layer_mb<T, TAB, LPT, MINB><<<blocks, threads, smem, st>>>(one);
+    }
     return Status();
 }
 
-static Status launch_layer_class(cudaStream_t st, u32 T, const LayerParams &one, const LayerParams *jobs,
-                                 const u64 *prefix, u32 njobs, u64 teams)
+// One kernel form per lane width L (the launch class): L = T * LPT.  The
+// register shape is the variant of the table forms at 2 lanes per thread:
+// 0 = the compiler's budget, 1 = 4 blocks per SM, 2 = 2; other forms and
+// multi-job launches have only variant 0.
+template <int T, bool TAB, int LPT>
+static Status launch_layer_v(cudaStream_t st, u32 variant, const LayerParams &one, const LayerParams *jobs,
+                             const u64 *prefix, u32 njobs, u64 teams)
 {
-    switch (T) {
-        case 2: return launch_layer_t<2, false>(st, one, jobs, prefix, njobs, teams);
-        case 4: return launch_layer_t<4, false>(st, one, jobs, prefix, njobs, teams);
-        case 8: return launch_layer_t<8, true>(st, one, jobs, prefix, njobs, teams);
-        case 16: return launch_layer_t<16, true>(st, one, jobs, prefix, njobs, teams);
-        default: return launch_layer_t<32, true>(st, one, jobs, prefix, njobs, teams);
+    if constexpr (TAB && LPT == 2) {
+        if (njobs == 0 && variant == 1) return launch_layer_t<T, TAB, LPT, 4>(st, one, jobs, prefix, njobs, teams);
+        if (njobs == 0 && variant == 2) return launch_layer_t<T, TAB, LPT, 2>(st, one, jobs, prefix, njobs, teams);
+    }
+    return launch_layer_t<T, TAB, LPT, 0>(st, one, jobs, prefix, njobs, teams);
+}
+
+static Status launch_layer_class(cudaStream_t st, u32 L, u32 variant, const LayerParams &one,
+                                 const LayerParams *jobs, const u64 *prefix, u32 njobs, u64 teams)
+{
+    switch (L) {
+        case 4: return launch_layer_v<2, false, 2>(st, variant, one, jobs, prefix, njobs, teams);
+        case 8: return launch_layer_v<4, false, 2>(st, variant, one, jobs, prefix, njobs, teams);
+        case 16: return launch_layer_v<8, true, 2>(st, variant, one, jobs, prefix, njobs, teams);
+        case 32: return launch_layer_v<16, true, 2>(st, variant, one, jobs, prefix, njobs, teams);
+        case 64: return launch_layer_v<32, true, 2>(st, variant, one, jobs, prefix, njobs, teams);
+        default: return launch_layer_v<32, true, 4>(st, variant, one, jobs, prefix, njobs, teams);
     }
 }
 
@@ -648,7 +731,10 @@ static void count_layer(Profiler *prof, const Job &j)
     const u64 writes = (j.ell < k) ? j.ncp : 0;
     prof->stats.layer_bytes += (j.mf + writes) * L * 8;
     prof->stats.layer_gf_muls += (j.mf + writes) * L;
-    if (j.T >= 8) prof->stats.layer_table_muls += j.mf * L;
+    if (j.T >= 8) {
+        prof->stats.layer_table_muls += j.mf * L;
+        prof->stats.layer_table_builds += j.mf;
+    }
 }
 
 Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &dev_params, void *host_params,
@@ -659,7 +745,8 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         const Job &j = *jobs[0];
         cudaEvent_t la = nullptr;
         TM_TRY(prof->begin(st, &la));
-        TM_TRY(launch_layer_class(st, j.T, job_layer_params(j), nullptr, nullptr, 0, j.n_chunks * j.lane_groups));
+        TM_TRY(launch_layer_class(st, j.L, j.variant, job_layer_params(j), nullptr, nullptr, 0,
+                                  j.n_chunks * j.lane_groups));
         TM_CUDA(cudaGetLastError());
         TM_TRY(prof->end(st, la, FAM_LAYER));
         prof->stats.launches++;
@@ -667,13 +754,13 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         count_layer(prof, j);
         return Status();
     }
-    // group by lane-width class; per class: job table + team prefix
-    const u32 classes[5] = {2, 4, 8, 16, 32};
+    // group by lane width; per class: job table + team prefix
+    const u32 classes[6] = {4, 8, 16, 32, 64, 128};
     size_t off = 0;
-    for (u32 T : classes) {
+    for (u32 Lc : classes) {
         std::vector<const Job *> cls;
         for (const Job *j : jobs)
-            if (j->T == T) cls.push_back(j);
+            if (j->L == Lc) cls.push_back(j);
         if (cls.empty()) continue;
         const size_t need = cls.size() * sizeof(LayerParams) + (cls.size() + 1) * sizeof(u64);
         const size_t at = (off + 255) & ~(size_t)255;
@@ -693,7 +780,7 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         TM_CUDA(cudaMemcpyAsync(dbase, (char *)host_params + at, need, cudaMemcpyHostToDevice, st));
         cudaEvent_t la = nullptr;
         TM_TRY(prof->begin(st, &la));
-        TM_TRY(launch_layer_class(st, T, hp[0], (const LayerParams *)dbase,
+        TM_TRY(launch_layer_class(st, Lc, 0, hp[0], (const LayerParams *)dbase,
                                   (const u64 *)(dbase + cls.size() * sizeof(LayerParams)), (u32)cls.size(), teams));
         TM_CUDA(cudaGetLastError());
         TM_TRY(prof->end(st, la, FAM_LAYER));
@@ -702,6 +789,69 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         off = at + need;
     }
     return Status();
+}
+
+// Autotuner of the layer kernel's launch shape.  On the first lane batch of
+// a decision whose (graph, lane width) has no entry yet, layer 3 is launched
+// for every candidate -- arcs per team chunk in {64, 128, 256} x register
+// shape {compiler's budget, 4 blocks per SM, 2 blocks per SM} (table forms at
+// 2 lanes per thread, L = 16..64) -- twice, each
+// launch timed by CUDA events on the job's stream.  The fastest shape (least
+// of its two times) is kept for the graph and used by every later job on it
+// with that lane width; the layer then runs once more in that shape, whose
+// output (checkpoints, or at the last layer the per-chunk partial sums that
+// the readout reduces) the rest of the decision uses.
+static Status tune_layer(Job &j)
+{
+    struct Cand {
+        u32 chunk, variant;
+        float ms;
+    };
+    std::vector<Cand> cands;
+    for (u32 c : {64u, 128u, 256u})
+        for (u32 v = 0; v < ((j.L >= 16 && j.L <= 64) ? 3u : 1u); v++) cands.push_back({c, v, 1e30f});
+    const size_t nl = 2 * cands.size();
+    std::vector<cudaEvent_t> ev(nl + 1, nullptr);
+    Status st;
+    for (auto &e : ev) {
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) st = cuda_fail(err, "tuner events");
+    }
+    if (st.ok()) st = [&]() -> Status {
+        TM_CUDA(cudaEventRecord(ev[0], j.st));
+        for (size_t i = 0; i < nl; i++) {
+            const Cand &c = cands[i % cands.size()];
+            j.chunk = c.chunk;
+            j.variant = c.variant;
+            j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
+            TM_TRY(launch_layer_class(j.st, j.L, j.variant, job_layer_params(j), nullptr, nullptr, 0,
+                                      j.n_chunks * j.lane_groups));
+            TM_CUDA(cudaGetLastError());
+            TM_CUDA(cudaEventRecord(ev[i + 1], j.st));
+            j.prof->stats.launches++;
+        }
+        TM_CUDA(cudaEventSynchronize(ev[nl]));
+        for (size_t i = 0; i < nl; i++) {
+            float ms = 0;
+            TM_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+            Cand &c = cands[i % cands.size()];
+            c.ms = std::min(c.ms, ms);
+        }
+        return Status();
+    }();
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+    TM_TRY(st);
+    const Cand *best = &cands[0];
+    for (const Cand &c : cands)
+        if (c.ms < best->ms) best = &c;
+    j.g->layer_tune[j.L] = {best->chunk, best->variant};
+    j.chunk = best->chunk;
+    j.variant = best->variant;
+    j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
+    std::vector<Job *> one{&j};
+    DevBuf unused;
+    return launch_layers(j.st, one, unused, nullptr, 0, j.prof);
 }
 
 Status job_readout_enqueue(Job &j)
@@ -759,12 +909,16 @@ Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *f
         const u64 total = nb * q.repeats;
         TM_TRY(ensure_pinned(g.ws, 64 + total * j.L * 8));
         j.multi_slot = true;
+        const bool tune = q.k >= 3 && g.layer_tune.find(j.L) == g.layer_tune.end();
         for (u64 b = 0; b < total; b++) {
             j.r = (u32)(b / nb);
             j.p0 = q.p_begin + (b % nb) * j.L;
             j.batch_seq = b;
             TM_TRY(job_batch_begin(j));
-            for (; j.ell <= q.k; j.ell++) TM_TRY(launch_layers(j.st, one, unused, nullptr, 0, j.prof));
+            for (; j.ell <= q.k; j.ell++) {
+                if (tune && b == 0 && j.ell == 3) TM_TRY(tune_layer(j));
+                else TM_TRY(launch_layers(j.st, one, unused, nullptr, 0, j.prof));
+            }
             TM_TRY(job_readout_enqueue(j));
         }
         TM_CUDA(cudaStreamSynchronize(j.st));

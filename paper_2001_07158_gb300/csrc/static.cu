@@ -105,7 +105,7 @@ template <bool TAB>
 __global__ void __launch_bounds__(256) k_static_layer(u64 M, const u32 *own, const u32 *oth, u32 L, const u64 *In,
                                                       u64 *Out, u64 key, u32 p, int fwd, int base, u32 only)
 {
-    __shared__ __align__(128) u64 tabs[TAB ? 8 : 1][TAB ? 256 : 1];
+    __shared__ __align__(2048) u64 tabs[TAB ? 8 : 1][TAB ? 256 : 1];  // tables on 2 KB boundaries
     u64 *tab = tabs[TAB ? (threadIdx.x >> 5) : 0];
     const int tt = threadIdx.x & 31;
     const u64 w = (u64)blockIdx.x * 8 + (threadIdx.x >> 5);

@@ -136,6 +136,29 @@ def test_lane_batches_and_point_ranges(tm):
         assert np.array_equal(sub.per_point, o[2][37:hi])
 
 
+def test_layer_shapes_give_identical_results(tm):
+    # every launch shape the autotuner can pick (arcs per chunk x register
+    # bound) gives the same per-point sums; the tuner's pick is one of them
+    g = synth.powerlaw_graph(3000, 40000, 300, 4, seed=71)
+    for k, L in ((4, 16), (5, 32), (6, 64), (7, 128)):
+        ms = [i % 4 for i in range(k)]
+        G = gpu_graph(tm, g)
+        assert tm.tmotif_get_layer_shape(G, L) is None
+        tuned = tm.tmotif_decide(G, k, ms, seed=9)
+        chunk, variant = tm.tmotif_get_layer_shape(G, L)
+        assert chunk in (64, 128, 256) and variant in ((0, 1, 2) if 16 <= L <= 64 else (0,))
+        ref = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, seed=9)
+        assert_same(tuned, ref)
+        for c in (64, 128, 256):
+            for v in ((0, 1, 2) if 16 <= L <= 64 else (0,)):
+                tm.tmotif_set_layer_shape(G, L, c, v)
+                d = tm.tmotif_decide(G, k, ms, seed=9)
+                assert np.array_equal(d.per_point, tuned.per_point), (L, c, v)
+        with pytest.raises(tm.TmotifError):
+            tm.tmotif_set_layer_shape(G, L, 100, 0)
+        G.close()
+
+
 def test_edge_cases(tm):
     # empty edge set, only self-loops, duplicated input edges, absent colours,
     # k larger than the vertex count
