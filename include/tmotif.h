@@ -263,7 +263,8 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
  * threads per SM: method 0 = register multiply (Karatsuba over 32x32
  * carry-less products with holes); method 1 = a warp builds the 16 x 16 nibble
  * table of one multiplier in shared memory and applies it to 64 lanes (2 per
- * thread); method 2 = the same table applied to 128 lanes (4 per thread).
+ * thread); method 2 = the same table applied to 128 lanes (4 per thread);
+ * method 3 = method 1 with the lookup's nibble shifts done by multiplies.
  * Runs `iters` rounds; ms receives the device time, products the products
  * done.  INVALID for another method or iters = 0. */
 int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products);

@@ -619,7 +619,7 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
 
 int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products)
 {
-    if (!ms || !products || method < 0 || method > 2 || iters == 0)
+    if (!ms || !products || method < 0 || method > 3 || iters == 0)
         return fail(TMOTIF_ERR_INVALID, "bad probe arguments").code;
     return gf_probe(method, iters, ms, (u64 *)products).code;
 }

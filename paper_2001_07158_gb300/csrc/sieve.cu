@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(256) k_gf_probe(u32 iters, u64 seed, u64 *sink
     u64 *tab = tabs[threadIdx.x >> 5];
     const int tt = threadIdx.x & 31;
     constexpr int LPT = METHOD == 2 ? 4 : 2;  // lanes per thread
+    const NibbleMuls nm = nibble_muls((u32)(iters != 0));
     u64 a[LPT], acc[LPT];
     a[0] = mix64(seed + blockIdx.x * 256 + threadIdx.x);
 #pragma unroll
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(256) k_gf_probe(u32 iters, u64 seed, u64 *sink
             gf_table_build(tab, y, tt, 32);
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < LPT; i++) acc[i] ^= gf_table_mul(tab, a[i]);
+            for (int i = 0; i < LPT; i++) acc[i] ^= METHOD == 3 ? gf_table_mul_m(tab, a[i], nm) : gf_table_mul(tab, a[i]);
         }
 #pragma unroll
         for (int i = 0; i < LPT; i++) a[i] += acc[(i + 1) % LPT];
@@ -419,7 +420,8 @@ Status gf_probe(int method, u32 iters, double *ms, u64 *products)
         const u32 n = pass ? iters : 4;
         if (method == 0) k_gf_probe<0><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
         else if (method == 1) k_gf_probe<1><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
-        else k_gf_probe<2><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
+        else if (method == 2) k_gf_probe<2><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
+        else k_gf_probe<3><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
     }
     cudaEventRecord(b);
     cudaError_t e = cudaEventSynchronize(b);
