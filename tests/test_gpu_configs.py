@@ -1,0 +1,136 @@
+"""GPU parity at the sizes of the batched, large and serving workloads.
+
+Bit-exact against the oracle wherever the oracle finishes in seconds:
+- large graphs (n = 10^7 with m = 5*10^8 at k = 5, and m = 10^8 at k = 10):
+  every point (k = 5) or a ragged sample of points (k = 10) of a decision
+  restricted to a narrow time window, which the oracle evaluates on the arcs
+  of that window (arcs outside the window are not used, Sec. 6.8); at the
+  full window, properties that hold at any size: a point range equals the
+  matching slice of the whole decision (a different lane width and launch
+  shape), and extraction returns a valid path;
+- batched small graphs: a sample of the batch checked point by point;
+- the serving graph: requests in the server's mix equal the same requests
+  alone, and a sample of them equals the oracle.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2001_07158_gb300 as tm
+
+    return tm
+
+
+def window_arcs(g, t_min, t_max):
+    sel = (g.time >= t_min) & (g.time <= t_max)
+    return g.src[sel], g.dst[sel], g.time[sel]
+
+
+def check_path(g, k, ms, v, t, arcs=None):
+    assert len(set(v.tolist())) == k
+    assert sorted(g.color[v].tolist()) == sorted(int(c) for c in ms)
+    for r in range(k - 1):
+        if r:
+            assert t[r] > t[r - 1]
+        if arcs is not None:
+            assert (int(v[r]), int(v[r + 1]), int(t[r])) in arcs
+
+
+@pytest.mark.parametrize("m,k,seed,points", [(500_000_000, 5, 5, None), (100_000_000, 10, 6, (0, 1, 333, 511, 1022))])
+def test_large_graph(tm, m, k, seed, points):
+    g, q = synth.config4_large(m=m, n=10_000_000, k=k, seed=seed)
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors)
+    info = tm.tmotif_graph_get_info(G)
+    assert info["m_arcs"] <= m
+    # narrow window: every point (k=5) or sampled points (k=10) against the oracle
+    t0, t1 = 5000, 5000 + 4 * k
+    d = tm.tmotif_decide(G, k, q.multiset, seed=q.seed, t_min=t0, t_max=t1)
+    ws, wd, wt = window_arcs(g, t0, t1)
+    ranges = [(0, 1 << k)] if points is None else [(p, p + 1) for p in points]
+    for lo, hi in ranges:
+        _, _, pp = oracle.decide(g.n, ws, wd, wt, g.color, g.num_colors, k, q.multiset, seed=q.seed, t_min=t0,
+                                 t_max=t1, point_begin=lo, point_end=hi, nthreads=min(16, hi - lo))
+        assert np.array_equal(d.per_point[lo:hi], pp), (lo, hi)
+    # full window: a point range equals the slice of the whole decision
+    full = tm.tmotif_decide(G, k, q.multiset, seed=q.seed)
+    lo, hi = (3, 11) if k == 5 else (100, 108)
+    part = tm.tmotif_decide(G, k, q.multiset, seed=q.seed, point_begin=lo, point_end=hi)
+    assert np.array_equal(part.per_point, full.per_point[lo:hi])
+    assert full.found
+    f, v, t = tm.tmotif_extract(G, k, q.multiset, seed=q.seed)
+    assert f
+    check_path(g, k, q.multiset, v, t)
+    for r in range(k - 1):  # the arcs exist (searched in the arrays, not a set of 10^8)
+        hit = (g.src == v[r]) & (g.dst == v[r + 1]) & (g.time == t[r])
+        assert hit.any()
+    G.close()
+
+
+def test_batched_tour_graphs_sample_against_oracle(tm):
+    items = synth.config3_batch(num_graphs=400)
+    graphs = [tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors) for g, _ in items]
+    queries = [{"k": q.k, "multiset": q.multiset, "seed": q.seed} for _, q in items]
+    res = tm.tmotif_decide_batch(graphs, queries)
+    rng = random.Random(5)
+    for i in rng.sample(range(len(items)), 8):
+        g, q = items[i]
+        f, s, pp = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed)
+        assert res[i].found == f and res[i].sieve_sum == s and np.array_equal(res[i].per_point, pp), i
+    for i in rng.sample(range(len(items)), 40):
+        alone = tm.tmotif_decide(graphs[i], **queries[i])
+        assert np.array_equal(alone.per_point, res[i].per_point)
+    for G in graphs:
+        G.close()
+
+
+def test_serving_graph_mix_equals_alone_and_oracle(tm):
+    import time
+
+    g, reqs = synth.config5_serving(requests=24)
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors)
+    srv = tm.tmotif_server_create(0)
+    tickets = [tm.tmotif_submit(srv, G, q.k, q.multiset, is_extract=ex, seed=q.seed) for q, ex in reqs]
+    out = [None] * len(reqs)
+    t0 = time.time()
+    while any(o is None for o in out):
+        for i, t in enumerate(tickets):
+            if out[i] is None:
+                out[i] = tm.tmotif_poll(srv, t, reqs[i][0].k)
+        assert time.time() - t0 < 600
+        time.sleep(0.001)
+    srv.close()
+    arcs = None
+    for (q, ex), (dec, v, t) in zip(reqs, out):
+        if ex:
+            f, va, ta = tm.tmotif_extract(G, q.k, q.multiset, seed=q.seed)
+            assert dec.found == f
+            if f:
+                assert np.array_equal(v, va) and np.array_equal(t, ta)
+                check_path(g, q.k, q.multiset, v, t, arcs)
+        else:
+            alone = tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed)
+            assert dec.found == alone.found and dec.sieve_sum == alone.sieve_sum
+    # two small requests against the oracle, every point
+    small = [(q, ex) for q, ex in reqs if q.k <= 4 and not ex][:2]
+    for q, _ in small:
+        d = tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed)
+        f, s, pp = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed,
+                                 nthreads=16)
+        assert d.found == f and d.sieve_sum == s and np.array_equal(d.per_point, pp)
+    G.close()
