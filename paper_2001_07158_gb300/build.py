@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtmotif.so")
-SOURCES = ["api.cu", "graph.cu", "sieve.cu", "static.cu", "extract.cu", "serve.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "graph.cu", "sieve.cu", "static.cu", "pack.cu", "extract.cu", "serve.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

@@ -172,6 +172,14 @@ struct QuerySpec {
 
 Status parse_query(const Graph &g, const tmotif_query *q, QuerySpec *out);
 
+// One query of a packed many-graph batch, as the device reads it (pack.cu):
+// its graph's first vertex in the packed numbering, k, start/end (packed ids
+// or NONE), the y key of the current repeat and the first lane-sum slot.
+struct PackJob {
+    u64 ky;
+    u32 vbase, k, start, end;
+};
+
 // Parameters of one job's layer step (eq. gen-polynomial:3), as the layer
 // kernel reads them.
 struct LayerParams {
@@ -185,6 +193,10 @@ struct LayerParams {
     u64 n_chunks;
     u64 ky;
     u32 L, lane_groups, chunk, ell, k, start, end, T;
+    // packed batches only: vertex -> job, the jobs, per (job, lane) sums
+    const u32 *jv = nullptr;
+    const PackJob *pjobs = nullptr;
+    u64 *pout = nullptr;
 };
 
 // One decision in flight: its query, its device workspace and its progress
@@ -321,6 +333,13 @@ Status optimum_time(Graph &g, const QuerySpec &q, u32 *t_opt, int *found);
 Status extract_localized(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *found);
 
 Status build_graph(const tmotif_graph_desc *d, Graph *g);
+
+// Packed many-graph batch (pack.cu): every query's per-point values on its
+// graph, identical to deciding each alone; vals[i] receives 2^k values.
+// Queries must be pack_eligible (one repeat, all points, no preprocessing).
+bool pack_eligible(const QuerySpec &q);
+Status pack_decide(Graph *const *graphs, const QuerySpec *specs, size_t count, cudaStream_t st,
+                   std::vector<std::vector<u64>> *vals, u64 *launches);
 // Stable LSD radix sort of N 64-bit keys on their low `bits` bits; a and b
 // hold N keys each, *sorted points at the one with the result.
 Status radix_sort_u64(cudaStream_t st, u64 *a, u64 *b, u64 N, int bits, u32 *d_scratch, u64 **sorted,

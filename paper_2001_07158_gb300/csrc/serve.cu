@@ -237,6 +237,36 @@ extern "C" int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_qu
                 return fail(TMOTIF_ERR_INVALID, "graphs of one batch must share a stream").code;
         }
         cudaStream_t st = graphs[0]->stream;
+        bool packable = count > 1;
+        for (uint32_t i = 0; i < count && packable; i++) packable = pack_eligible(specs[i]);
+        if (packable) {
+            // many graphs, one pass: the packed form (pack.cu)
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+            std::vector<std::vector<u64>> vals;
+            std::vector<Graph *> gp(graphs, graphs + count);
+            u64 launches = 0;
+            Status ps = pack_decide(gp.data(), specs.data(), count, st, &vals, &launches);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (!ps.ok()) return ps.code;
+            for (uint32_t i = 0; i < count; i++) {
+                u64 sum = 0;
+                for (u64 v : vals[i]) sum ^= v;
+                out[i].found = sum != 0;
+                out[i].sieve_sum = sum;
+                out[i].ms = ms;
+                if (out[i].per_point) std::memcpy(out[i].per_point, vals[i].data(), vals[i].size() * sizeof(u64));
+            }
+            graphs[0]->prof.stats.launches += launches;
+            return TMOTIF_OK;
+        }
         Scheduler sched(st, default_budget());
         Status s = sched.init();
         if (!s.ok()) return s.code;

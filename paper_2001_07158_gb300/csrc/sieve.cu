@@ -21,6 +21,7 @@
 
 #include "gf64.cuh"
 #include "internal.h"
+#include "layer.cuh"
 #include "scan.cuh"
 
 namespace tmo {
@@ -177,129 +178,6 @@ __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L,
 
 // ---------------------------------------------------------------------------
 // Layer kernel: eq. (gen-polynomial:3), one walk length per job per launch.
-// ---------------------------------------------------------------------------
-// A team of T threads owns T * LPT consecutive lanes (LPT = 2 or 4 lanes, 16
-// or 32 bytes, per thread) of one job and walks one chunk of whole
-// in-segments in arc order.  Segments are never split, so a running XOR is
-// the prefix of eq. (3)'s stay term.  With TAB the team builds, per arc, the
-// nibble table of y_{e,l-1} in shared memory and every lane's y-product is 16
-// table loads; x-products (one per checkpoint and per segment at the last
-// layer) use the register multiply.  One launch can carry many jobs
-// (njobs > 0: the team's job is found in the prefix of team counts); njobs =
-// 0 means the single job in `one`.  At the last layer every team writes its
-// lanes' sums to the job's partial array.
-template <int T, bool TAB, int LPT>
-__device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *tab)
-{
-    const int tt = threadIdx.x % T;
-    const u32 team_mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (((threadIdx.x & 31) / T) * T));
-    const u64 chunk = team / p.lane_groups;
-    if (chunk >= p.n_chunks) return;
-    const u32 lane0 = (u32)(team % p.lane_groups) * (LPT * T) + LPT * tt;
-    const u64 Lw = p.L;
-    const bool last = (p.ell == p.k);
-    u64 q[LPT], xc[LPT], acc[LPT];
-#pragma unroll
-    for (int i = 0; i < LPT; i++) q[i] = xc[i] = acc[i] = 0;
-
-    const u64 b0 = chunk * p.chunk;
-    const u64 b1 = min(b0 + p.chunk, p.m_f);
-    u64 begin = b0, stop = b1;
-    if (b0 > 0 && p.dst[b0] == p.dst[b0 - 1]) begin = p.seg_hi[p.dst[b0]];
-    if (b1 < p.m_f && p.dst[b1] == p.dst[b1 - 1]) stop = p.seg_hi[p.dst[b1]];
-
-    u32 cur = NONE;
-    for (u64 base = begin; base < stop; base += T) {
-        const u64 e = base + tt;
-        u32 s = 0, d = NONE, ci = NONE, co = NONE;
-        u64 y = 0;
-        if (e < stop) {
-            s = p.src[e];
-            d = p.dst[e];
-            const u32 t = p.time[e];
-            if (p.ell > 2) ci = p.cp_in[e];
-            if (!last) co = p.cp_out[e];
-            y = coef_y(mix64(p.ky ^ (((u64)s << 32) | d)), t, p.ell - 1);
-        }
-        const int cnt = (int)min((u64)T, stop - base);
-        for (int j = 0; j < cnt; j++) {
-            const u32 dj = __shfl_sync(team_mask, d, j, T);
-            const u32 sj = __shfl_sync(team_mask, s, j, T);
-            const u32 cij = __shfl_sync(team_mask, ci, j, T);
-            const u32 coj = __shfl_sync(team_mask, co, j, T);
-            const u64 yj = __shfl_sync(team_mask, y, j, T);
-            if (dj != cur) {
-                if (last && cur != NONE && (p.end == NONE || cur == p.end)) {
-#pragma unroll
-                    for (int i = 0; i < LPT; i++) q[i] ^= gf_mul(xc[i], acc[i]);
-                }
-                cur = dj;
-#pragma unroll
-                for (int i = 0; i < LPT; i += 2) {
-                    const ulonglong2 xv = *(const ulonglong2 *)(p.x + (u64)dj * Lw + lane0 + i);
-                    xc[i] = xv.x;
-                    xc[i + 1] = xv.y;
-                    acc[i] = acc[i + 1] = 0;
-                }
-            }
-            const u64 *row = nullptr;
-            if (p.ell == 2) {
-                if (p.start == NONE || sj == p.start) row = p.x + (u64)sj * Lw + lane0;
-            } else if (cij != NONE) {
-                row = p.Cin + (u64)cij * Lw + lane0;
-            }
-            if (row) {  // uniform across the team
-                u64 in[LPT], h[LPT];
-#pragma unroll
-                for (int i = 0; i < LPT; i += 2) {
-                    const ulonglong2 v = *(const ulonglong2 *)(row + i);
-                    in[i] = v.x;
-                    in[i + 1] = v.y;
-                }
-                if (TAB) {
-                    __syncwarp(team_mask);  // earlier lookups are done
-                    gf_table_build(tab, yj, tt, T);
-                    __syncwarp(team_mask);  // table complete
-#pragma unroll
-                    for (int i = 0; i < LPT; i++) h[i] = gf_table_mul(tab, in[i]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < LPT; i++) h[i] = gf_mul(yj, in[i]);
-                }
-#pragma unroll
-                for (int i = 0; i < LPT; i++) acc[i] ^= h[i];
-                if (last && p.arc_sum && (p.end == NONE || dj == p.end)) {
-                    // this arc's last-layer term, summed over the lanes
-                    u64 v = 0;
-#pragma unroll
-                    for (int i = 0; i < LPT; i++) v ^= gf_mul(xc[i], h[i]);
-#pragma unroll
-                    for (int o = T / 2; o > 0; o >>= 1) v ^= __shfl_xor_sync(team_mask, v, o, T);
-                    if (tt == 0) p.arc_sum[base + j] ^= v;
-                }
-            }
-            if (coj != NONE) {
-#pragma unroll
-                for (int i = 0; i < LPT; i += 2) {
-                    ulonglong2 o;
-                    o.x = gf_mul(xc[i], acc[i]);
-                    o.y = gf_mul(xc[i + 1], acc[i + 1]);
-                    *(ulonglong2 *)(p.Cout + (u64)coj * Lw + lane0 + i) = o;
-                }
-            }
-        }
-    }
-    if (last) {
-        if (cur != NONE && (p.end == NONE || cur == p.end)) {
-#pragma unroll
-            for (int i = 0; i < LPT; i++) q[i] ^= gf_mul(xc[i], acc[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < LPT; i += 2)
-            *(ulonglong2 *)(p.partial + chunk * Lw + lane0 + i) = make_ulonglong2(q[i], q[i + 1]);
-    }
-}
-
 // MULTI = false: the single job in `one` (read from parameter space);
 // MULTI = true: the team's job is found in the prefix of team counts.
 template <int T, bool TAB, bool MULTI, int LPT>
@@ -313,7 +191,7 @@ __device__ __forceinline__ void layer_kernel(const LayerParams &one, const Layer
     u64 *tab = smem + (((2048u - (sa & 2047u)) & 2047u) >> 3) + (size_t)(threadIdx.x / T) * 256;
     const u64 team = (u64)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
     if (!MULTI) {
-        layer_team<T, TAB, LPT>(one, team, tab);
+        layer_team<T, TAB, LPT, false>(one, team, tab);
         return;
     }
     if (team >= team_prefix[njobs]) return;
@@ -323,7 +201,7 @@ __device__ __forceinline__ void layer_kernel(const LayerParams &one, const Layer
         if (team_prefix[mid] <= team) lo = mid;
         else hi = mid;
     }
-    layer_team<T, TAB, LPT>(jobs[lo], team - team_prefix[lo], tab);
+    layer_team<T, TAB, LPT, false>(jobs[lo], team - team_prefix[lo], tab);
 }
 
 // k_layer: the compiler's own register budget for 256-thread blocks;
@@ -794,7 +672,8 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
 }
 
 // Autotuner of the layer kernel's launch shape.  On the first lane batch of
-// a decision whose (graph, lane width) has no entry yet, layer 3 is launched
+// a decision whose (graph, lane width) has no entry yet and whose layers
+// hold at least 2^22 arc-lanes, layer 3 is launched
 // for every candidate -- arcs per team chunk in {64, 128, 256} x register
 // shape {compiler's budget, 4 blocks per SM, 2 blocks per SM} (table forms at
 // 2 lanes per thread, L = 16..64) -- twice, each
@@ -911,7 +790,9 @@ Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *f
         const u64 total = nb * q.repeats;
         TM_TRY(ensure_pinned(g.ws, 64 + total * j.L * 8));
         j.multi_slot = true;
-        const bool tune = q.k >= 3 && g.layer_tune.find(j.L) == g.layer_tune.end();
+        // tune only where a layer is long enough for the shape to matter
+        // (at least 2^22 arc-lanes, tens of microseconds)
+        const bool tune = q.k >= 3 && j.mf * j.L >= (1ull << 22) && g.layer_tune.find(j.L) == g.layer_tune.end();
         for (u64 b = 0; b < total; b++) {
             j.r = (u32)(b / nb);
             j.p0 = q.p_begin + (b % nb) * j.L;

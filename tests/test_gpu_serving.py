@@ -44,11 +44,29 @@ def small_graphs(tm, count, seed):
 
 
 def test_batch_equals_individual_decisions(tm):
+    # packed form (every query one repeat over all points): windows, start and
+    # end vertices and EC timestamp tuples mixed in
     items = small_graphs(tm, 60, seed=3)
+    rng = random.Random(33)
+    for i, (G, q) in enumerate(items):
+        if i % 5 == 1:
+            q["start"] = rng.randrange(G.n)
+        if i % 5 == 2:
+            q["end"] = rng.randrange(G.n)
+        if i % 7 == 3:
+            q["timestamps"] = sorted(rng.sample(range(1, 289), q["k"] - 1))
+            q["t_max"] = 0
     graphs = [G for G, _ in items]
     queries = [q for _, q in items]
     res = tm.tmotif_decide_batch(graphs, queries)
     for (G, q), r in zip(items, res):
+        alone = tm.tmotif_decide(G, **q)
+        assert r.found == alone.found and r.sieve_sum == alone.sieve_sum
+        assert np.array_equal(r.per_point, alone.per_point)
+    # scheduler form (a query with two repeats takes the batch off the packed path)
+    queries[0] = dict(queries[0], repeats=2)
+    res = tm.tmotif_decide_batch(graphs[:20], queries[:20])
+    for G, q, r in zip(graphs[:20], queries[:20], res):
         alone = tm.tmotif_decide(G, **q)
         assert r.found == alone.found and r.sieve_sum == alone.sieve_sum
         assert np.array_equal(r.per_point, alone.per_point)
