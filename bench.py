@@ -67,10 +67,10 @@ def layer_bound_s(reg, tab, builds):
 
 
 # DRAM traffic of one layer launch from an ncu capture, valid only for the
-# layer-kernel source it was taken on (source_sha() below, first 16 hex).
-# (layer l = 4 launch of a cfg2 decision, full size, one-pass dram counters;
-# profiles/k_layer_cfg2_dram_full.md)
-LAYER_TRAFFIC = {"source_sha": "d9351bd1902886f9", "bytes_per_launch": 1137230080 + 399884544}
+# layer-kernel sources it was taken on (source_sha() below, first 16 hex):
+# a timed-decision layer of the default workload, full size, one-pass dram
+# counters (profiles/k_layer_mid_n1e6_m1e7_k6_dram.md)
+LAYER_TRAFFIC = {"source_sha": "1fc937ff4d3c99bb", "bytes_per_launch": 1120302336 + 399874048}
 
 
 def parse_args():
@@ -82,7 +82,7 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
-    p.add_argument("--serving-requests", type=int, default=32)
+    p.add_argument("--serving-requests", type=int, default=256)
     p.add_argument("--scale", type=float, default=1.0,
                    help="scale n and m of the workload (profiling captures of a smaller case)")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="mid",
@@ -99,9 +99,10 @@ def dist_env():
 
 
 def source_sha():
-    """Hash of the sources the layer kernel is compiled from."""
+    """Hash of the layer kernel's device code (its team body and the GF(2^64)
+    products it calls)."""
     h = hashlib.sha256()
-    for f in ("sieve.cu", "gf64.cuh"):
+    for f in ("layer.cuh", "gf64.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2001_07158_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -396,7 +397,8 @@ def run_ours(args):
     achieved = muls / (layer_ms / 1e3) / 1e9
     peak = muls / t_min / 1e9
     sha = source_sha()
-    traffic = LAYER_TRAFFIC["bytes_per_launch"] if LAYER_TRAFFIC["source_sha"] == sha else None
+    traffic = (LAYER_TRAFFIC["bytes_per_launch"]
+               if LAYER_TRAFFIC["source_sha"] == sha and args.workload == "mid" and args.scale == 1.0 else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G GF(2^64) products/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_layer (eq. gen-polynomial:3 layer)",

@@ -237,6 +237,9 @@ struct Job {
 // host; readout_finish (after the stream is synchronised): accumulate and
 // move on to the next batch, repeat, or finish.
 Status job_prep(Job &j);
+// A launch shape the autotuner found on this device for lane width L and a
+// layer of about mf arcs (same floor(log2)), if any.
+bool tuned_shape(u32 L, u64 mf, std::pair<u32, u32> *shape);
 Status job_batch_begin(Job &j);
 LayerParams job_layer_params(const Job &j);
 Status job_readout_enqueue(Job &j);

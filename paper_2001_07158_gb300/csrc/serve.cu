@@ -80,7 +80,13 @@ struct SJob {
 
 class Scheduler {
 public:
-    Scheduler(cudaStream_t st, size_t budget) : st_(st), budget_(budget) {}
+    // st: the stream of the shared layer launches; prep_st: the stream of
+    // job preparation (filter, checkpoints, masks), so that jobs admitted
+    // while layers run are prepared beside them (the same stream when equal)
+    Scheduler(cudaStream_t st, size_t budget, cudaStream_t prep_st = nullptr)
+        : st_(st), prep_st_(prep_st ? prep_st : st), budget_(budget)
+    {
+    }
     ~Scheduler()
     {
         for (auto &d : dev_params_) d.release();
@@ -97,23 +103,30 @@ public:
 
     // room for one more job: within the memory budget, and the job tables
     // of one layer launch stay inside a slot
-    bool fits(size_t bytes) const { return in_use_ + bytes <= budget_ && active_.size() < kMaxActive; }
+    bool fits(size_t bytes) const
+    {
+        return in_use_ + bytes <= budget_ && active_.size() + staged_.size() < kMaxActive;
+    }
     size_t in_use() const { return in_use_; }
     size_t budget() const { return budget_; }
-    bool idle() const { return active_.empty(); }
+    bool idle() const { return active_.empty() && staged_.empty(); }
     size_t active() const { return active_.size(); }
 
-    // Admit a job whose query/graph/mask are set; runs its prep.  On return
-    // the job is active, or finished (nothing kept) and appended to done.
+    // Admit a job whose query/graph/mask are set; runs its prep on the prep
+    // stream (which the prep synchronises).  On return the job is staged to
+    // join the active jobs at the end of the current step (or at once when
+    // no step is running), or finished (nothing kept) and appended to done.
     Status admit(std::unique_ptr<SJob> sj, size_t reserved, std::vector<std::unique_ptr<SJob>> *done)
     {
         sj->reserved = reserved;
         in_use_ += reserved;
-        sj->ws.set_stream(st_);
+        sj->ws.set_stream(prep_st_);
         sj->job.ws = &sj->ws;
-        sj->job.st = st_;
+        sj->job.st = prep_st_;
         sj->job.prof = &prof;
         Status s = job_prep(sj->job);
+        sj->ws.set_stream(st_);
+        sj->job.st = st_;
         if (!s.ok()) {
             in_use_ -= reserved;
             return s;
@@ -122,6 +135,8 @@ public:
         if (sj->job.done) {
             in_use_ -= sj->reserved;
             done->push_back(std::move(sj));
+        } else if (in_step_) {
+            staged_.push_back(std::move(sj));
         } else {
             active_.push_back(std::move(sj));
         }
@@ -131,9 +146,9 @@ public:
     // Upload a probe mask into a job's workspace before admission.
     Status set_mask(SJob &sj, const std::vector<uint8_t> &alive)
     {
-        sj.ws.set_stream(st_);
+        sj.ws.set_stream(prep_st_);
         TM_TRY(sj.ws.alive.reserve(std::max<size_t>(alive.size(), 1)));
-        TM_CUDA(cudaMemcpyAsync(sj.ws.alive.p, alive.data(), alive.size(), cudaMemcpyHostToDevice, st_));
+        TM_CUDA(cudaMemcpyAsync(sj.ws.alive.p, alive.data(), alive.size(), cudaMemcpyHostToDevice, prep_st_));
         sj.job.d_alive = sj.ws.alive.as<uint8_t>();
         return Status();
     }
@@ -142,9 +157,14 @@ public:
     // a lane batch, one shared layer launch per lane-width class per layer)
     // until some job finishes its lane batch; then read out, sync once, and
     // retire finished jobs.  At most kMaxLayersPerSync layers are enqueued
-    // before the host looks again (to admit new work).
-    Status step(std::vector<std::unique_ptr<SJob>> *done)
+    // before the host looks again (to admit new work).  `overlap` (may be
+    // empty) runs after the launches are enqueued and before the sync: jobs
+    // it admits are prepared while the layers run and join after the step.
+    template <class F>
+    Status step(std::vector<std::unique_ptr<SJob>> *done, F &&overlap)
     {
+        for (auto &sj : staged_) active_.push_back(std::move(sj));
+        staged_.clear();
         if (active_.empty()) return Status();
         for (int rounds = 0; rounds < kMaxLayersPerSync; rounds++) {
             std::vector<Job *> layer;
@@ -168,7 +188,11 @@ public:
             }
             if (readout) break;
         }
+        in_step_ = true;
+        Status os = overlap();
+        in_step_ = false;
         TM_CUDA(cudaStreamSynchronize(st_));
+        TM_TRY(os);
         TM_TRY(prof.collect());
         steps++;
         std::vector<std::unique_ptr<SJob>> keep;
@@ -185,7 +209,13 @@ public:
             keep.push_back(std::move(sj));
         }
         active_.swap(keep);
+        for (auto &sj : staged_) active_.push_back(std::move(sj));
+        staged_.clear();
         return Status();
+    }
+    Status step(std::vector<std::unique_ptr<SJob>> *done)
+    {
+        return step(done, [] { return Status(); });
     }
 
     Profiler prof;
@@ -197,10 +227,11 @@ private:
     static const int kMaxLayersPerSync = 8;
     static const size_t kSlotBytes = 1 << 20;
     static const size_t kMaxActive = 4096;  // x (LayerParams + prefix) < kSlotBytes
-    cudaStream_t st_;
+    cudaStream_t st_, prep_st_;
     size_t budget_;
     size_t in_use_ = 0;
-    std::vector<std::unique_ptr<SJob>> active_;
+    bool in_step_ = false;
+    std::vector<std::unique_ptr<SJob>> active_, staged_;
     DevBuf dev_params_[kMaxLayersPerSync];
     void *host_params_ = nullptr;
 };
@@ -344,7 +375,7 @@ struct Request {
 struct tmotif_server {
     size_t budget = 0;
     int device = 0;
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr, prep_st = nullptr;  // layer launches; job preparation
     std::unique_ptr<Scheduler> sched;
     Workspace finish_ws;  // arc gathering for extraction's final DFS
     std::thread worker;
@@ -402,7 +433,7 @@ struct tmotif_server {
         if (!r->ex.next_probe(&pq)) return false;
         sj->job.q = pq;
         if (r->ex.stage == ExtractState::PROBING) {
-            Status s = r->ex.maybe_compact(*r->g, finish_ws, st);
+            Status s = r->ex.maybe_compact(*r->g, finish_ws, prep_st);
             if (s.ok()) s = sched->set_mask(*sj, r->ex.alive);
             if (!s.ok()) {
                 complete(r, s);
@@ -429,7 +460,7 @@ struct tmotif_server {
         }
         Status s;
         if (r->ex.stage == ExtractState::SHRUNK)
-            s = extract_finish(*r->ex.current(*r->g), finish_ws, st, sched->prof, r->ex, r->verts.data(),
+            s = extract_finish(*r->ex.current(*r->g), finish_ws, prep_st, sched->prof, r->ex, r->verts.data(),
                                r->times.data(), &r->found);
         else
             r->found = 0;
@@ -441,20 +472,19 @@ struct tmotif_server {
         cudaSetDevice(device);
         std::deque<std::pair<Request *, std::unique_ptr<SJob>>> waiting;  // admission queue (FIFO)
         std::vector<std::unique_ptr<SJob>> done;
-        while (!stop.load()) {
-            {
-                std::unique_lock<std::mutex> lock(mu);
-                if (pending.empty() && waiting.empty() && sched->idle())
-                    cv.wait_for(lock, std::chrono::milliseconds(2));
-                while (!pending.empty()) {
-                    Request *r = pending.front();
-                    pending.pop_front();
-                    waiting.push_back({r, nullptr});
-                }
+        auto take_pending = [&]() {
+            std::lock_guard<std::mutex> lock(mu);
+            while (!pending.empty()) {
+                Request *r = pending.front();
+                pending.pop_front();
+                waiting.push_back({r, nullptr});
             }
-            // admit in arrival order while the memory budget allows; a large
-            // request waits for the large slot, and smaller ones behind it
-            // may go first
+        };
+        // admit in arrival order while the memory budget allows; a large
+        // request waits for the large slot, and smaller ones behind it may
+        // go first
+        auto admit_waiting = [&]() {
+            take_pending();
             for (auto it = waiting.begin(); it != waiting.end();) {
                 Request *r = it->first;
                 std::unique_ptr<SJob> &sj = it->second;
@@ -474,8 +504,21 @@ struct tmotif_server {
                 it = waiting.erase(it);
                 if (!s.ok()) complete(r, s);
             }
+        };
+        while (!stop.load()) {
+            {
+                std::unique_lock<std::mutex> lock(mu);
+                if (pending.empty() && waiting.empty() && sched->idle())
+                    cv.wait_for(lock, std::chrono::milliseconds(2));
+            }
+            if (sched->idle()) admit_waiting();
             if (!sched->idle()) {
-                Status s = sched->step(&done);
+                // jobs admitted while this step's layers run are prepared
+                // beside them (prep stream) and join after the step
+                Status s = sched->step(&done, [&] {
+                    admit_waiting();
+                    return Status();
+                });
                 if (!s.ok()) {  // fail every request in flight
                     std::lock_guard<std::mutex> lock(mu);
                     for (auto &kv : reqs)
@@ -538,11 +581,12 @@ extern "C" int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *ou
         if (cudaGetDevice(&s->device) != cudaSuccess) return fail(TMOTIF_ERR_CUDA, "no CUDA device").code;
         s->budget = hbm_budget_bytes ? hbm_budget_bytes : default_budget();
         cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->prep_st, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "server stream").code;
-        s->sched = std::make_unique<Scheduler>(s->st, s->budget);
+        s->sched = std::make_unique<Scheduler>(s->st, s->budget, s->prep_st);
         Status st = s->sched->init();
         if (!st.ok()) return st.code;
-        s->finish_ws.set_stream(s->st);
+        s->finish_ws.set_stream(s->prep_st);
         tmotif_server *raw = s.get();
         s->worker = std::thread([raw] { raw->run(); });
         *out = s.release();
@@ -618,9 +662,11 @@ extern "C" void tmotif_server_destroy(tmotif_server_t s)
     if (s->worker.joinable()) s->worker.join();
     s->sched.reset();
     s->finish_ws.release();
-    if (s->st) {
-        cudaStreamSynchronize(s->st);
-        cudaStreamDestroy(s->st);
-    }
+    s->reqs.clear();  // extraction subgraphs free on the prep stream
+    for (cudaStream_t st : {s->st, s->prep_st})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
     delete s;
 }

@@ -18,6 +18,8 @@
 // reads x directly.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <tuple>
 
 #include "gf64.cuh"
 #include "internal.h"
@@ -465,11 +467,17 @@ Status job_prep(Job &j)
     j.lane_groups = 1;
     j.chunk = CHUNK;
     j.variant = 0;
-    {  // the launch shape the autotuner chose for this graph and lane width
+    {  // the launch shape pinned or tuned for this graph and lane width, else
+       // one tuned on this device for a layer of about the same size
         auto it = g.layer_tune.find(L);
+        std::pair<u32, u32> shape;
         if (it != g.layer_tune.end()) {
             j.chunk = it->second.first;
             j.variant = it->second.second;
+        } else if (tuned_shape(L, j.mf, &shape)) {
+            g.layer_tune[L] = shape;
+            j.chunk = shape.first;
+            j.variant = shape.second;
         }
     }
     j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
@@ -671,6 +679,29 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
     return Status();
 }
 
+// Shapes the autotuner found, per device, lane width and layer size class
+// (floor(log2(arcs))), shared by every graph of the process.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, u32, u32>, std::pair<u32, u32>> g_tuned;
+
+static std::tuple<int, u32, u32> tune_key(u32 L, u64 mf)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    u32 b = 0;
+    while ((mf >> (b + 1)) != 0) b++;
+    return {dev, L, b};
+}
+
+bool tuned_shape(u32 L, u64 mf, std::pair<u32, u32> *shape)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(tune_key(L, mf));
+    if (it == g_tuned.end()) return false;
+    *shape = it->second;
+    return true;
+}
+
 // Autotuner of the layer kernel's launch shape.  On the first lane batch of
 // a decision whose (graph, lane width) has no entry yet and whose layers
 // hold at least 2^22 arc-lanes, layer 3 is launched
@@ -727,6 +758,10 @@ static Status tune_layer(Job &j)
     for (const Cand &c : cands)
         if (c.ms < best->ms) best = &c;
     j.g->layer_tune[j.L] = {best->chunk, best->variant};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[tune_key(j.L, j.mf)] = {best->chunk, best->variant};
+    }
     j.chunk = best->chunk;
     j.variant = best->variant;
     j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
