@@ -245,8 +245,9 @@ int tmotif_set_profiling(tmotif_graph_t g, int on);
 
 /* Launch shape of the generating-function layer kernel for lane width L (a
  * power of two in [4, 128]) on graph g: arcs per team chunk (64, 128 or 256)
- * and the register-shape variant (0 = the compiler's budget, 1 = at most 64
- * registers per thread, 2 = at most 128; only 0 at L < 16 and L = 128).  The library's autotuner picks it on the first
+ * and the kernel variant (0 = the default form; 1 = at most 64 registers per
+ * thread, 2 = at most 128, for L = 16 and 64; 3 = 16-thread teams at 2 lanes
+ * per thread instead of the default warp team at one lane, for L = 32).  The library's autotuner picks it on the first
  * decision that needs it, by timing every candidate on one layer; set pins
  * it (results never depend on it), get reads it (NOT_FOUND when none is set
  * yet).  Errors: INVALID for a bad L, chunk or variant. */

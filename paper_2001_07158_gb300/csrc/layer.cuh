@@ -8,8 +8,8 @@
 namespace tmo {
 
 // ---------------------------------------------------------------------------
-// A team of T threads owns T * LPT consecutive lanes (LPT = 2 or 4 lanes, 16
-// or 32 bytes, per thread) of one job and walks one chunk of whole
+// A team of T threads owns T * LPT consecutive lanes (LPT = 1, 2 or 4 lanes,
+// 8, 16 or 32 bytes, per thread) of one job and walks one chunk of whole
 // in-segments in arc order.  Segments are never split, so a running XOR is
 // the prefix of eq. (3)'s stay term.  With TAB the team builds, per arc, the
 // nibble table of y_{e,l-1} in shared memory and every lane's y-product is 16
@@ -101,12 +101,17 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
                 } else {
                     seg_end_ok = p.end == NONE || dj == p.end;
                 }
+                if constexpr (LPT == 1) {
+                    xc[0] = p.x[(u64)dj * Lw + lane0];
+                    acc[0] = 0;
+                } else {
 #pragma unroll
-                for (int i = 0; i < LPT; i += 2) {
-                    const ulonglong2 xv = *(const ulonglong2 *)(p.x + (u64)dj * Lw + lane0 + i);
-                    xc[i] = xv.x;
-                    xc[i + 1] = xv.y;
-                    acc[i] = acc[i + 1] = 0;
+                    for (int i = 0; i < LPT; i += 2) {
+                        const ulonglong2 xv = *(const ulonglong2 *)(p.x + (u64)dj * Lw + lane0 + i);
+                        xc[i] = xv.x;
+                        xc[i + 1] = xv.y;
+                        acc[i] = acc[i + 1] = 0;
+                    }
                 }
             }
             if (PACKED && !seg_live) continue;  // past this job's last layer (uniform in the team)
@@ -118,11 +123,15 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
             }
             if (row) {  // uniform across the team
                 u64 in[LPT], h[LPT];
+                if constexpr (LPT == 1) {
+                    in[0] = row[0];
+                } else {
 #pragma unroll
-                for (int i = 0; i < LPT; i += 2) {
-                    const ulonglong2 v = *(const ulonglong2 *)(row + i);
-                    in[i] = v.x;
-                    in[i + 1] = v.y;
+                    for (int i = 0; i < LPT; i += 2) {
+                        const ulonglong2 v = *(const ulonglong2 *)(row + i);
+                        in[i] = v.x;
+                        in[i + 1] = v.y;
+                    }
                 }
                 if (TAB) {
                     __syncwarp(team_mask);  // earlier lookups are done
@@ -147,21 +156,29 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
                 }
             }
             if (coj != NONE) {
+                if constexpr (LPT == 1) {
+                    p.Cout[(u64)coj * Lw + lane0] = gf_mul(xc[0], acc[0]);
+                } else {
 #pragma unroll
-                for (int i = 0; i < LPT; i += 2) {
-                    ulonglong2 o;
-                    o.x = gf_mul(xc[i], acc[i]);
-                    o.y = gf_mul(xc[i + 1], acc[i + 1]);
-                    *(ulonglong2 *)(p.Cout + (u64)coj * Lw + lane0 + i) = o;
+                    for (int i = 0; i < LPT; i += 2) {
+                        ulonglong2 o;
+                        o.x = gf_mul(xc[i], acc[i]);
+                        o.y = gf_mul(xc[i + 1], acc[i + 1]);
+                        *(ulonglong2 *)(p.Cout + (u64)coj * Lw + lane0 + i) = o;
+                    }
                 }
             }
         }
     }
     finish_segment();
     if (!PACKED && last) {
+        if constexpr (LPT == 1) {
+            p.partial[chunk * Lw + lane0] = q[0];
+        } else {
 #pragma unroll
-        for (int i = 0; i < LPT; i += 2)
-            *(ulonglong2 *)(p.partial + chunk * Lw + lane0 + i) = make_ulonglong2(q[i], q[i + 1]);
+            for (int i = 0; i < LPT; i += 2)
+                *(ulonglong2 *)(p.partial + chunk * Lw + lane0 + i) = make_ulonglong2(q[i], q[i + 1]);
+        }
     }
 }
 

@@ -583,13 +583,16 @@ static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const Laye
 
 // One kernel form per lane width L (the launch class): L = T * LPT.  The
 // register shape is the variant of the table forms at 2 lanes per thread:
-// 0 = the compiler's budget, 1 = 4 blocks per SM, 2 = 2; other forms and
-// multi-job launches have only variant 0.
+// 0 = the compiler's budget, 1 = 4 blocks per SM, 2 = 2.  At L = 32 the
+// default team is a whole warp at one lane per thread, which keeps the warp
+// convergent (two 16-thread teams would walk different arcs); variant 3 is
+// the 16-thread team at 2 lanes per thread.  Other forms and multi-job
+// launches have only variant 0.
 template <int T, bool TAB, int LPT>
 static Status launch_layer_v(cudaStream_t st, u32 variant, const LayerParams &one, const LayerParams *jobs,
                              const u64 *prefix, u32 njobs, u64 teams)
 {
-    if constexpr (TAB && LPT == 2) {
+    if constexpr (TAB && LPT == 2 && T != 16) {  // T = 16 only as the L = 32 variant 3
         if (njobs == 0 && variant == 1) return launch_layer_t<T, TAB, LPT, 4>(st, one, jobs, prefix, njobs, teams);
         if (njobs == 0 && variant == 2) return launch_layer_t<T, TAB, LPT, 2>(st, one, jobs, prefix, njobs, teams);
     }
@@ -603,7 +606,9 @@ static Status launch_layer_class(cudaStream_t st, u32 L, u32 variant, const Laye
         case 4: return launch_layer_v<2, false, 2>(st, variant, one, jobs, prefix, njobs, teams);
         case 8: return launch_layer_v<4, false, 2>(st, variant, one, jobs, prefix, njobs, teams);
         case 16: return launch_layer_v<8, true, 2>(st, variant, one, jobs, prefix, njobs, teams);
-        case 32: return launch_layer_v<16, true, 2>(st, variant, one, jobs, prefix, njobs, teams);
+        case 32:
+            if (variant == 3 && njobs == 0) return launch_layer_t<16, true, 2, 0>(st, one, jobs, prefix, njobs, teams);
+            return launch_layer_v<32, true, 1>(st, variant, one, jobs, prefix, njobs, teams);
         case 64: return launch_layer_v<32, true, 2>(st, variant, one, jobs, prefix, njobs, teams);
         default: return launch_layer_v<32, true, 4>(st, variant, one, jobs, prefix, njobs, teams);
     }
@@ -707,7 +712,8 @@ bool tuned_shape(u32 L, u64 mf, std::pair<u32, u32> *shape)
 // hold at least 2^22 arc-lanes, layer 3 is launched
 // for every candidate -- arcs per team chunk in {64, 128, 256} x register
 // shape {compiler's budget, 4 blocks per SM, 2 blocks per SM} (table forms at
-// 2 lanes per thread, L = 16..64) -- twice, each
+// 2 lanes per thread, L = 16 and 64; at L = 32 the one-lane warp team and
+// the two-lane 16-thread team) -- twice, each
 // launch timed by CUDA events on the job's stream.  The fastest shape (least
 // of its two times) is kept for the graph and used by every later job on it
 // with that lane width; the layer then runs once more in that shape, whose
@@ -721,7 +727,8 @@ static Status tune_layer(Job &j)
     };
     std::vector<Cand> cands;
     for (u32 c : {64u, 128u, 256u})
-        for (u32 v = 0; v < ((j.L >= 16 && j.L <= 64) ? 3u : 1u); v++) cands.push_back({c, v, 1e30f});
+        for (u32 v = 0; v < (j.L == 32 ? 4u : ((j.L == 16 || j.L == 64) ? 3u : 1u)); v++)
+            if (!(j.L == 32 && (v == 1 || v == 2))) cands.push_back({c, v, 1e30f});
     const size_t nl = 2 * cands.size();
     std::vector<cudaEvent_t> ev(nl + 1, nullptr);
     Status st;
