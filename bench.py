@@ -334,8 +334,9 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(local)  # before the process group, so each rank's NCCL uses its own GPU
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     if args.workload == "batch":

@@ -28,12 +28,6 @@
 
 namespace tmo {
 
-// In-place exclusive scan of a[0..N); writes the total to d_total (device u32).
-static Status exclusive_scan(Graph &g, u32 *a, u64 N, u32 *d_total)
-{
-    return exclusive_scan_on(g.stream, g.ws.block_sums, a, N, d_total, (u64 *)&g.prof.stats.launches);
-}
-
 // ---------------------------------------------------------------------------
 // Per-query preparation
 // ---------------------------------------------------------------------------
