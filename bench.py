@@ -88,7 +88,7 @@ def parse_args():
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="mid",
                    help="mid: the default decision (n=1e6, m=1e7, k=6); large5 / large10: power-law "
                         "n=1e7 with m=5e8, k=5 / m=1e8, k=10; batch: 10,000 small tour graphs in one "
-                        "batched call (k in 5..8)")
+                        "batched call (k in 5..8); transit: a timetable graph for --preprocess")
     p.add_argument("--preprocess", action="store_true", help="static preprocessing sieve before each decision")
     return p.parse_args()
 
@@ -165,6 +165,8 @@ WORKLOADS = {
                "1024 points",
     "batch": "10,000 tour-style graphs, n~U[100,5000], avg out-degree 8, t in [1,288], 12 colours; "
              "k~U{5..8}; one batched call",
+    "transit": "timetable graph: 100,000 stops, 10,000 routes of 10-39 stops x 100 trips (2.4e7 arcs over "
+               "2.4e5 static pairs), t in [1,1440], 12 colours; PathMotif k=8, 256 points",
 }
 
 
@@ -175,6 +177,8 @@ def workload(scale=1.0, name="mid"):
         return synth.config4_large(m=int(500_000_000 * scale), n=int(10_000_000 * scale), k=5, seed=5)
     if name == "large10":
         return synth.config4_large(m=int(100_000_000 * scale), n=int(10_000_000 * scale), k=10, seed=6)
+    if name == "transit":
+        return synth.config_transit(n_stops=int(100_000 * scale), routes=int(10_000 * scale))
     if scale == 1.0:
         return synth.config2_mid()
     return synth.config2_mid(n=int(1_000_000 * scale), m=int(10_000_000 * scale))

@@ -406,6 +406,26 @@ struct Prepared {
     double ms = 0;
 };
 
+// Add the statistics of work done on a preprocessed subgraph to its parent.
+void merge_stats(Graph &g, const Prepared &p)
+{
+    if (!p.sub) return;
+    const tmotif_stats &b = p.sub->prof.stats;
+    tmotif_stats &a = g.prof.stats;
+    a.launches += b.launches;
+    a.layer_launches += b.layer_launches;
+    a.layer_ms += b.layer_ms;
+    a.prep_ms += b.prep_ms;
+    a.coef_ms += b.coef_ms;
+    a.other_ms += b.other_ms;
+    a.layer_arc_lanes += b.layer_arc_lanes;
+    a.layer_cp_lanes += b.layer_cp_lanes;
+    a.layer_bytes += b.layer_bytes;
+    a.layer_gf_muls += b.layer_gf_muls;
+    a.layer_table_muls += b.layer_table_muls;
+    a.layer_table_builds += b.layer_table_builds;
+}
+
 Status prepare(Graph &g, const QuerySpec &q, Prepared *p)
 {
     p->g = &g;
@@ -419,6 +439,7 @@ Status prepare(Graph &g, const QuerySpec &q, Prepared *p)
     TM_TRY(static_mask(g, q, nullptr, g.sw.mask.as<uint8_t>(), nullptr));
     p->sub.reset(new Graph());
     TM_TRY(make_subgraph(g, g.ws, g.stream, g.sw.mask.as<uint8_t>(), p->sub.get()));
+    p->sub->prof.on = g.prof.on;  // its work is reported in g's statistics
     TM_CUDA(cudaEventRecord(e1, g.stream));
     TM_CUDA(cudaEventSynchronize(e1));
     float f = 0;
@@ -448,6 +469,7 @@ int tmotif_decide(tmotif_graph_t g, const tmotif_query *q, tmotif_decision *out)
         u64 sum = 0;
         double ms = 0;
         s = sieve_decide(*pre.g, qs, nullptr, &found, &sum, (u64 *)out->per_point, &ms);
+        merge_stats(*g, pre);
         if (!s.ok()) return s.code;
         out->found = found;
         out->sieve_sum = sum;
@@ -478,6 +500,7 @@ int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uin
             if (!s.ok()) return s.code;
             if (!any) {
                 *found = 0;
+                merge_stats(*g, pre);
                 return TMOTIF_OK;
             }
             qs.t_max = t_opt;
@@ -488,6 +511,7 @@ int tmotif_extract(tmotif_graph_t g, const tmotif_query *q, uint32_t *verts, uin
         } else {
             s = extract_localized(G, qs, verts, times, found);
         }
+        merge_stats(*g, pre);
         return s.code;
     } catch (const std::bad_alloc &) {
         return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
@@ -506,7 +530,9 @@ int tmotif_optimum_time(tmotif_graph_t g, const tmotif_query *q, uint32_t *t_opt
         Prepared pre;
         s = prepare(*g, qs, &pre);
         if (!s.ok()) return s.code;
-        return optimum_time(*pre.g, qs, t_opt, found).code;
+        s = optimum_time(*pre.g, qs, t_opt, found);
+        merge_stats(*g, pre);
+        return s.code;
     } catch (const std::bad_alloc &) {
         return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
     }
@@ -528,6 +554,7 @@ int tmotif_localize(tmotif_graph_t g, const tmotif_query *q, uint64_t *per_verte
         u64 sum = 0;
         double ms = 0;
         s = sieve_localize(*pre.g, qs, (u64 *)per_vertex, &found, &sum, &ms);
+        merge_stats(*g, pre);
         if (!s.ok()) return s.code;
         out->found = found;
         out->sieve_sum = sum;

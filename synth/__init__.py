@@ -1,7 +1,7 @@
 """Seeded synthetic temporal graphs and motif queries.
 
 These generators stand in for the paper's datasets (KONECT/SNAP graphs and
-transport feeds, Sec. 8) with the shapes its experiments use: configuration-
+transport feeds, Sec. 9) with the shapes its experiments use: configuration-
 model style power-law out-degrees, uniform timestamps, uniform or Zipf vertex
 colours, planted matching paths (Sec. 9.3 and 10.1).  They hold none of the sieve's
 arithmetic: both the GPU library and the CPU oracle receive the plain arrays
@@ -124,6 +124,41 @@ def tour_graph(n, avg_deg, t_max, num_colors, seed, name="tour"):
     time = np.concatenate(times)[:m_target].astype(np.uint32)
     color = r.integers(0, num_colors, n, dtype=np.uint32)
     return Graph(n, src, dst, time, color, num_colors, False, name)
+
+
+def transit_graph(n_stops, routes, trips, num_colors, seed, t_max=1440, name="transit"):
+    """Timetable-style graph (the paper's transport feeds, Sec. 9.3): each
+    route visits 10-39 distinct random stops with 1-5 minutes between stops;
+    each of its `trips` departures (uniform over the day) adds one arc per hop,
+    so every static (stop, stop) pair repeats at many times."""
+    r = _rng(seed)
+    length = r.integers(10, 40, routes)                          # stops per route
+    first = np.cumsum(length) - length
+    stops = np.concatenate([r.choice(n_stops, int(L), replace=False) for L in length]).astype(np.uint32)
+    route_of = np.repeat(np.arange(routes), length)
+    hop = r.integers(1, 6, int(length.sum()))                      # minutes from the previous stop
+    hop[first] = 0
+    offs = np.cumsum(hop)
+    offs = offs - offs[first][route_of]                            # minutes since the route's first stop
+    span = offs[first + length - 1]                                # route duration
+    has_next = np.arange(len(stops)) + 1 < (first + length)[route_of]
+    a = np.flatnonzero(has_next)                                   # hop a -> a + 1 of its route
+    dep = r.integers(1, np.maximum(2, t_max - span), (trips, routes))  # departure per trip and route
+    t = dep[:, route_of[a]] + offs[a + 1][None, :]
+    src = np.broadcast_to(stops[a], t.shape).reshape(-1).astype(np.uint32)
+    dst = np.broadcast_to(stops[a + 1], t.shape).reshape(-1).astype(np.uint32)
+    time = t.reshape(-1).astype(np.uint32)
+    color = r.integers(0, num_colors, n_stops, dtype=np.uint32)
+    return Graph(n_stops, src, dst, time, color, num_colors, False, name)
+
+
+def config_transit(n_stops=100_000, routes=10_000, trips=100, k=8, seed=12):
+    """Timetable graph (100,000 stops, 10,000 routes of 10-39 stops, 100 trips
+    each: about 2.4e7 arcs over about 2.4e5 static pairs), 12 colours, and a
+    k = 8 query (seed 12)."""
+    g = transit_graph(n_stops, routes, trips, 12, seed=seed, name=f"transit-{n_stops}x{routes}x{trips}")
+    q = Query(k, draw_multiset(k, 12, seed=seed), seed=seed)
+    return g, q
 
 
 def plant_paths(g: Graph, multiset, count, seed, t_max=None):
