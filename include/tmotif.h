@@ -237,6 +237,11 @@ int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *out);
 int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_query *q, int is_extract, uint64_t *ticket);
 int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *out, uint32_t *verts, uint32_t *times,
                 int *done);
+/* Blocking form of tmotif_poll: waits at most timeout_ms for the request to
+ * finish.  TIMEOUT when it has not (the request stays pending and can be
+ * polled or waited for again); otherwise as tmotif_poll with done = 1. */
+int tmotif_wait(tmotif_server_t s, uint64_t ticket, uint32_t timeout_ms, tmotif_decision *out, uint32_t *verts,
+                uint32_t *times);
 void tmotif_server_destroy(tmotif_server_t s);
 
 /* Profiling counters for a graph (see tmotif_stats).  set_profiling(g, 1)

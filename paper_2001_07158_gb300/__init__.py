@@ -83,6 +83,7 @@ def _load():
         "tmotif_server_create": (C.c_int, [C.c_size_t, C.POINTER(P)]),
         "tmotif_submit": (C.c_int, [P, P, C.POINTER(_Query), C.c_int, C.POINTER(C.c_uint64)]),
         "tmotif_poll": (C.c_int, [P, C.c_uint64, C.POINTER(_Decision), P, P, C.POINTER(C.c_int)]),
+        "tmotif_wait": (C.c_int, [P, C.c_uint64, C.c_uint32, C.POINTER(_Decision), P, P]),
         "tmotif_server_destroy": (None, [P]),
         "tmotif_set_profiling": (C.c_int, [P, C.c_int]),
         "tmotif_set_layer_shape": (C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32]),
@@ -380,6 +381,16 @@ def tmotif_poll(s: Server, ticket: int, k: int):
     _check(_lib.tmotif_poll(s.handle, ticket, C.byref(d), verts.ctypes.data, times.ctypes.data, C.byref(done)))
     if not done.value:
         return None
+    return Decision(bool(d.found), int(d.sieve_sum), None, float(d.ms)), verts[:k], times[:k - 1]
+
+
+def tmotif_wait(s: Server, ticket: int, k: int, timeout_ms: int):
+    """Block until the request finishes (raises TmotifError TIMEOUT = 4 after
+    timeout_ms, the request staying pending); returns what tmotif_poll does."""
+    d = _Decision(0, 0, None, 0.0)
+    verts = np.zeros(max(k, 1), np.uint32)
+    times = np.zeros(max(k, 1), np.uint32)
+    _check(_lib.tmotif_wait(s.handle, ticket, int(timeout_ms), C.byref(d), verts.ctypes.data, times.ctypes.data))
     return Decision(bool(d.found), int(d.sieve_sum), None, float(d.ms)), verts[:k], times[:k - 1]
 
 

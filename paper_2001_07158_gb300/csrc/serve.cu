@@ -381,6 +381,7 @@ struct tmotif_server {
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv;
+    std::condition_variable done_cv;  // a request finished (tmotif_wait)
     std::deque<Request *> pending;           // submitted, not yet admitted
     std::map<u64, std::unique_ptr<Request>> reqs;
     std::atomic<bool> stop{false};
@@ -397,6 +398,7 @@ struct tmotif_server {
         }
         r->ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
         r->done = true;
+        done_cv.notify_all();
     }
 
     // Make the next job of a request (its decision, or its next probe).
@@ -526,6 +528,7 @@ struct tmotif_server {
                             kv.second->code = s.code;
                             kv.second->done = true;
                         }
+                    done_cv.notify_all();
                     return;
                 }
             }
@@ -629,16 +632,11 @@ extern "C" int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_q
     }
 }
 
-extern "C" int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *out, uint32_t *verts,
-                           uint32_t *times, int *done)
+// Hand out a finished request's result and forget it (s->mu held).
+static int take_result(tmotif_server_t s, std::map<u64, std::unique_ptr<Request>>::iterator it,
+                       tmotif_decision *out, uint32_t *verts, uint32_t *times)
 {
-    if (!s || !done) return fail(TMOTIF_ERR_INVALID, "null argument").code;
-    std::lock_guard<std::mutex> lock(s->mu);
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) return fail(TMOTIF_ERR_NOT_FOUND, "unknown ticket").code;
     Request *r = it->second.get();
-    *done = r->done ? 1 : 0;
-    if (!r->done) return TMOTIF_OK;
     const int code = r->code;
     if (code != TMOTIF_OK) set_error(r->err);
     if (out) {
@@ -652,6 +650,31 @@ extern "C" int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *
     }
     s->reqs.erase(it);
     return code;
+}
+
+extern "C" int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *out, uint32_t *verts,
+                           uint32_t *times, int *done)
+{
+    if (!s || !done) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(TMOTIF_ERR_NOT_FOUND, "unknown ticket").code;
+    *done = it->second->done ? 1 : 0;
+    if (!*done) return TMOTIF_OK;
+    return take_result(s, it, out, verts, times);
+}
+
+extern "C" int tmotif_wait(tmotif_server_t s, uint64_t ticket, uint32_t timeout_ms, tmotif_decision *out,
+                           uint32_t *verts, uint32_t *times)
+{
+    if (!s) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(TMOTIF_ERR_NOT_FOUND, "unknown ticket").code;
+    Request *r = it->second.get();
+    if (!s->done_cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), [r] { return r->done; }))
+        return fail(TMOTIF_ERR_TIMEOUT, "request not finished within the timeout").code;
+    return take_result(s, s->reqs.find(ticket), out, verts, times);
 }
 
 extern "C" void tmotif_server_destroy(tmotif_server_t s)

@@ -134,6 +134,30 @@ def test_server_budget_admission(tm):
     for (G_, qq, _), (dec, _, _) in zip(jobs, res):
         alone = tm.tmotif_decide(G, q.k, q.multiset, seed=qq["seed"])
         assert dec.sieve_sum == alone.sieve_sum
+    other = tm.tmotif_server_create(0)
     with pytest.raises(tm.TmotifError) as e:
-        tm.tmotif_poll(one if False else tm.tmotif_server_create(0), 12345, 4)
+        tm.tmotif_poll(other, 12345, 4)
     assert e.value.code == 6
+    other.close()
+
+
+def test_server_wait_times_out_then_completes(tm):
+    # a k = 10 request on a mid-size graph takes milliseconds: a zero-timeout
+    # wait reports TIMEOUT (4) and leaves it pending; a long wait returns the
+    # result, which equals the decision alone
+    g = synth.powerlaw_graph(100000, 1500000, 500, 10, seed=23)
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors)
+    ms = list(range(10))
+    srv = tm.tmotif_server_create(0)
+    t = tm.tmotif_submit(srv, G, 10, ms, seed=4)
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_wait(srv, t, 10, 0)
+    assert e.value.code == 4
+    dec, _, _ = tm.tmotif_wait(srv, t, 10, 600000)
+    alone = tm.tmotif_decide(G, 10, ms, seed=4)
+    assert dec.found == alone.found and dec.sieve_sum == alone.sieve_sum
+    with pytest.raises(tm.TmotifError) as e:  # a finished ticket is forgotten
+        tm.tmotif_wait(srv, t, 10, 0)
+    assert e.value.code == 6
+    srv.close()
+    G.close()
