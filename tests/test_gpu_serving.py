@@ -161,3 +161,37 @@ def test_server_wait_times_out_then_completes(tm):
     assert e.value.code == 6
     srv.close()
     G.close()
+
+
+def test_packed_batch_edge_cases(tm):
+    # the packed form with k = 2..9 (1 to 8 rounds of 64 points), undirected
+    # graphs, a graph without arcs, a multiset whose colours are absent, and
+    # graphs of different colour counts: every per-point value equals the
+    # decision alone
+    rng = random.Random(77)
+    items = []
+    for i in range(40):
+        n = rng.randint(2, 300)
+        m = 0 if i == 5 else rng.randint(1, 6 * n)
+        ncol = rng.randint(1, 9)
+        g = synth.Graph(n, np.array([rng.randrange(n) for _ in range(m)], np.uint32),
+                        np.array([rng.randrange(n) for _ in range(m)], np.uint32),
+                        np.array([rng.randint(1, 30) for _ in range(m)], np.uint32),
+                        np.array([rng.randrange(ncol) for _ in range(n)], np.uint32), ncol, i % 3 == 0)
+        G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, undirected=g.undirected)
+        k = 2 + i % 8
+        ms = [rng.randrange(ncol) for _ in range(k)]
+        if i == 7:
+            ms = [ncol - 1] * k if ncol > 1 else ms
+        q = {"k": k, "multiset": ms, "seed": rng.getrandbits(40)}
+        if i % 4 == 1:
+            q["start"] = rng.randrange(n)
+        if i % 4 == 2:
+            q["end"] = rng.randrange(n)
+        items.append((G, q))
+    res = tm.tmotif_decide_batch([G for G, _ in items], [q for _, q in items])
+    for (G, q), r in zip(items, res):
+        alone = tm.tmotif_decide(G, **q)
+        assert np.array_equal(r.per_point, alone.per_point) and r.found == alone.found
+    for G, _ in items:
+        G.close()
