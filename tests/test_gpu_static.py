@@ -136,3 +136,22 @@ def test_batch_and_server_reject_preprocessing(tm):
     assert e.value.code == 5
     srv.close()
     G.close()
+
+
+def test_preprocessing_with_window_and_ec_tuple(tm):
+    # the static sieve ignores times (the merged graph); the decision on the
+    # kept vertices then applies the window or the EC tuple
+    rng = random.Random(4242)
+    for i in range(40):
+        g, k, ms, kw = rand_case(rng, i)
+        t_hi = int(g.time.max()) if len(g.time) else 1
+        if i % 2 and t_hi >= k - 1:
+            kw["timestamps"] = sorted(rng.sample(range(1, t_hi + 1), k - 1))
+        else:
+            kw["t_min"], kw["t_max"] = 2, 9
+        G = gpu_graph(tm, g)
+        d = tm.tmotif_decide(G, k, ms, preprocess=True, **kw)
+        f, s, pp, _ = oracle.decide_preprocessed(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms,
+                                                 undirected=g.undirected, **kw)
+        assert np.array_equal(d.per_point, pp) and d.sieve_sum == s and d.found == f, i
+        G.close()
