@@ -163,19 +163,22 @@ struct PackBuffers {
     DevBuf graphs, queries, jobs, slot_begin, slot_count;
     DevBuf P_src, P_dst, P_time, P_color, jv;
     DevBuf vflag, act, act_list, keep, f_src, f_dst, f_time, seg_lo, seg_hi, pos, mark, cp_in, cp_out;
+    DevBuf g_src, g_dst, g_time;  // the other set of kept arcs (rounds alternate)
     DevBuf wtab, x, C0, C1, out, block_sums, counters;
     void set_stream(cudaStream_t s)
     {
         DevBuf *all[] = {&graphs, &queries, &jobs, &slot_begin, &slot_count, &P_src, &P_dst, &P_time, &P_color,
                          &jv, &vflag, &act, &act_list, &keep, &f_src, &f_dst, &f_time, &seg_lo, &seg_hi, &pos,
-                         &mark, &cp_in, &cp_out, &wtab, &x, &C0, &C1, &out, &block_sums, &counters};
+                         &mark, &cp_in, &cp_out, &g_src, &g_dst, &g_time, &wtab, &x, &C0, &C1, &out, &block_sums,
+                         &counters};
         for (DevBuf *b : all) b->stream = s;
     }
     void release()
     {
         DevBuf *all[] = {&graphs, &queries, &jobs, &slot_begin, &slot_count, &P_src, &P_dst, &P_time, &P_color,
                          &jv, &vflag, &act, &act_list, &keep, &f_src, &f_dst, &f_time, &seg_lo, &seg_hi, &pos,
-                         &mark, &cp_in, &cp_out, &wtab, &x, &C0, &C1, &out, &block_sums, &counters};
+                         &mark, &cp_in, &cp_out, &g_src, &g_dst, &g_time, &wtab, &x, &C0, &C1, &out, &block_sums,
+                         &counters};
         for (DevBuf *b : all) b->release();
     }
 };
@@ -249,18 +252,23 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
     TM_TRY(B.out.reserve(nq * PL * 8));
     u32 *d_cnt = B.counters.as<u32>();
     u32 *h_cnt = (u32 *)pinned;
+    // arcs the rounds filter: all packed arcs, then the previous round's kept
+    // arcs (a later round keeps a subset: its queries are a subset)
+    const u32 *c_src = B.P_src.as<u32>(), *c_dst = B.P_dst.as<u32>(), *c_time = B.P_time.as<u32>();
+    u64 Mc = M;
     for (u32 r = 0; r < rounds; r++) {
         const u32 p0 = r * PL;
+        DevBuf &o_src = (r & 1) ? B.g_src : B.f_src, &o_dst = (r & 1) ? B.g_dst : B.f_dst,
+               &o_time = (r & 1) ? B.g_time : B.f_time;
         // filter: vertices with a query colour (queries with points in this
         // round), arcs between them inside their query's window
         k_pack_vflag<<<blocks_of(N + 1, 256), 256, 0, st>>>((u32)N, B.P_color.as<u32>(), B.jv.as<u32>(),
                                                            B.queries.as<PackQuery>(), B.slot_count.as<u32>(), p0,
                                                            B.vflag.as<uint8_t>(), B.act.as<u32>());
-        k_pack_keep<<<blocks_of(M + 1, 256), 256, 0, st>>>(M, B.P_src.as<u32>(), B.P_dst.as<u32>(),
-                                                          B.P_time.as<u32>(), B.vflag.as<uint8_t>(), B.jv.as<u32>(),
-                                                          B.queries.as<PackQuery>(), B.keep.as<u32>());
+        k_pack_keep<<<blocks_of(Mc + 1, 256), 256, 0, st>>>(Mc, c_src, c_dst, c_time, B.vflag.as<uint8_t>(),
+                                                           B.jv.as<u32>(), B.queries.as<PackQuery>(), B.keep.as<u32>());
         TM_CUDA(cudaGetLastError());
-        TM_TRY(exclusive_scan_on(st, B.block_sums, B.keep.as<u32>(), M + 1, d_cnt + 0, launches));
+        TM_TRY(exclusive_scan_on(st, B.block_sums, B.keep.as<u32>(), Mc + 1, d_cnt + 0, launches));
         TM_TRY(exclusive_scan_on(st, B.block_sums, B.act.as<u32>(), N + 1, d_cnt + 2, launches));
         k_active_list<<<blocks_of(N, 256), 256, 0, st>>>((u32)N, B.act.as<u32>(), B.act_list.as<u32>());
         *launches += 3;
@@ -269,22 +277,21 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
         const u64 mf = h_cnt[0], n_act = h_cnt[2];
         TM_CUDA(cudaMemsetAsync(B.out.p, 0, nq * PL * 8, st));
         if (mf > 0) {
-            TM_TRY(B.f_src.reserve(mf * 4));
-            TM_TRY(B.f_dst.reserve(mf * 4));
-            TM_TRY(B.f_time.reserve(mf * 4));
+            TM_TRY(o_src.reserve(mf * 4));
+            TM_TRY(o_dst.reserve(mf * 4));
+            TM_TRY(o_time.reserve(mf * 4));
             TM_TRY(B.pos.reserve(mf * 4));
             TM_TRY(B.mark.reserve((mf + 1) * 4));
             TM_TRY(B.cp_in.reserve(mf * 4));
             TM_TRY(B.cp_out.reserve(mf * 4));
-            k_compact<<<blocks_of(M, 256), 256, 0, st>>>(M, B.P_src.as<u32>(), B.P_dst.as<u32>(), B.P_time.as<u32>(),
-                                                         B.keep.as<u32>(), B.f_src.as<u32>(), B.f_dst.as<u32>(),
-                                                         B.f_time.as<u32>());
+            k_compact<<<blocks_of(Mc, 256), 256, 0, st>>>(Mc, c_src, c_dst, c_time, B.keep.as<u32>(), o_src.as<u32>(),
+                                                          o_dst.as<u32>(), o_time.as<u32>());
             TM_CUDA(cudaMemsetAsync(B.seg_lo.p, 0, N * 4, st));
             TM_CUDA(cudaMemsetAsync(B.seg_hi.p, 0, N * 4, st));
             TM_CUDA(cudaMemsetAsync(B.mark.p, 0, (mf + 1) * 4, st));
-            k_segments<<<blocks_of(mf, 256), 256, 0, st>>>(mf, B.f_dst.as<u32>(), B.seg_lo.as<u32>(),
+            k_segments<<<blocks_of(mf, 256), 256, 0, st>>>(mf, o_dst.as<u32>(), B.seg_lo.as<u32>(),
                                                            B.seg_hi.as<u32>());
-            k_pos<<<blocks_of(mf, 256), 256, 0, st>>>(mf, B.f_src.as<u32>(), B.f_time.as<u32>(), B.seg_lo.as<u32>(),
+            k_pos<<<blocks_of(mf, 256), 256, 0, st>>>(mf, o_src.as<u32>(), o_time.as<u32>(), B.seg_lo.as<u32>(),
                                                       B.seg_hi.as<u32>(), B.pos.as<u32>(), B.mark.as<u32>());
             TM_CUDA(cudaGetLastError());
             TM_TRY(exclusive_scan_on(st, B.block_sums, B.mark.as<u32>(), mf + 1, d_cnt + 1, launches));
@@ -310,9 +317,9 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
             // layers 2..kmax: each segment follows its own query's k
             LayerParams lp;
             std::memset(&lp, 0, sizeof(lp));
-            lp.src = B.f_src.as<u32>();
-            lp.dst = B.f_dst.as<u32>();
-            lp.time = B.f_time.as<u32>();
+            lp.src = o_src.as<u32>();
+            lp.dst = o_dst.as<u32>();
+            lp.time = o_time.as<u32>();
             lp.cp_in = B.cp_in.as<u32>();
             lp.cp_out = B.cp_out.as<u32>();
             lp.seg_hi = B.seg_hi.as<u32>();
@@ -329,12 +336,7 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
             lp.pjobs = B.jobs.as<PackJob>();
             lp.pout = B.out.as<u64>();
             u64 *bufs[2] = {B.C0.as<u64>(), B.C1.as<u64>()};
-            const size_t smem = 8 * 256 * 8 + 2048;
-            static bool attr = false;
-            if (!attr) {
-                TM_CUDA(cudaFuncSetAttribute(k_pack_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-                attr = true;
-            }
+            const size_t smem = 8 * 256 * 8 + 2048;  // 18 KB: within the default dynamic limit
             for (u32 ell = 2; ell <= kmax; ell++) {
                 lp.ell = ell;
                 lp.Cin = bufs[ell & 1];
@@ -344,6 +346,10 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
                 (*launches)++;
             }
         }
+        c_src = o_src.as<u32>();
+        c_dst = o_dst.as<u32>();
+        c_time = o_time.as<u32>();
+        Mc = mf;
         TM_CUDA(cudaMemcpyAsync((char *)pinned + 64, B.out.p, nq * PL * 8, cudaMemcpyDeviceToHost, st));
         TM_CUDA(cudaStreamSynchronize(st));
         const u64 *h_out = (const u64 *)((const char *)pinned + 64);

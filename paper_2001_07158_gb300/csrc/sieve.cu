@@ -551,18 +551,14 @@ static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const Laye
     const u64 teams_per_block = threads / T;
     const unsigned blocks = (unsigned)((teams + teams_per_block - 1) / teams_per_block);
     const size_t smem = TAB ? teams_per_block * 256 * 8 + 2048 : 16;
-    static bool attr_set = false;
-    if (!attr_set) {
+    if (smem > 48 * 1024) {  // above the default limit: opt in (per call, so per device and thread-safe)
         if constexpr (MINB == 0) {
-            TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB, false, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         160 * 1024));
-            TM_CUDA(cudaFuncSetAttribute(k_layer<T, TAB, true, LPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         160 * 1024));
+            TM_CUDA(cudaFuncSetAttribute(njobs == 0 ? k_layer<T, TAB, false, LPT> : k_layer<T, TAB, true, LPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         } else {
             TM_CUDA(cudaFuncSetAttribute(k_layer_mb<T, TAB, LPT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         160 * 1024));
+                                         (int)smem));
         }
-        attr_set = true;
     }
     if (!blocks) return Status();
     if constexpr (MINB == 0) {
