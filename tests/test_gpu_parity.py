@@ -201,6 +201,26 @@ def test_errors_are_reported(tm):
     assert_same(*both(tm, G, g, q.k, q.multiset, seed=3))
 
 
+def test_largest_k(tm):
+    # k = TMOTIF_KMAX = 20: 2^20 points in 8192 lane batches on a small graph
+    # with a planted 20-vertex path; three ragged ranges of points against the
+    # oracle; k = 21 is refused
+    g = synth.uniform_graph(60, 500, 40, 4, seed=55)
+    ms = [i % 4 for i in range(20)]
+    g2, _ = synth.plant_paths(g, ms, 1, seed=56, t_max=40)
+    G = gpu_graph(tm, g2)
+    d = tm.tmotif_decide(G, 20, ms, seed=8)
+    assert d.found
+    for lo, hi in ((0, 300), (524_000, 524_611), ((1 << 20) - 257, 1 << 20)):
+        _, _, pp = oracle.decide(g2.n, g2.src, g2.dst, g2.time, g2.color, g2.num_colors, 20, ms, seed=8,
+                                 point_begin=lo, point_end=hi)
+        assert np.array_equal(d.per_point[lo:hi], pp), (lo, hi)
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide(G, 21, ms + [0])
+    assert e.value.code == 5
+    G.close()
+
+
 def test_invalid_graphs_are_rejected(tm):
     n = 4
     src = np.array([0, 1, 2], np.uint32)
