@@ -70,7 +70,7 @@ def layer_bound_s(reg, tab, builds):
 # layer-kernel sources it was taken on (source_sha() below, first 16 hex):
 # a timed-decision layer of the default workload, full size, one-pass dram
 # counters (profiles/k_layer_mid_n1e6_m1e7_k6_dram.md)
-LAYER_TRAFFIC = {"source_sha": "1fc937ff4d3c99bb", "bytes_per_launch": 1120302336 + 399874048}
+LAYER_TRAFFIC = {"source_sha": "e8f0cdb1f52c15ca", "bytes_per_launch": 1120147200 + 399555840}
 
 
 def parse_args():
