@@ -197,10 +197,6 @@ void Profiler::destroy()
 // Graph residency: validate, orient, drop self-loops, merge duplicates, sort
 // arcs by (dst, time, src), upload.  E^tau is a set of triples (Sec. 4).
 // ---------------------------------------------------------------------------
-struct HArc {
-    u32 dst, time, src;
-};
-
 Status build_graph(const tmotif_graph_desc *d, Graph *g)
 {
     if (!d) return fail(TMOTIF_ERR_INVALID, "null graph descriptor");
@@ -209,67 +205,7 @@ Status build_graph(const tmotif_graph_desc *d, Graph *g)
     if (d->m > 0 && (!d->src || !d->dst || !d->time)) return fail(TMOTIF_ERR_INVALID, "null edge array");
     const u64 cap = d->undirected ? 2 * d->m : d->m;
     if (cap >= 0xFFFFFFFFull) return fail(TMOTIF_ERR_UNSUPPORTED, "more than 2^32-2 arcs");
-    {
-        bool done = false;
-        TM_TRY(build_graph_device(d, g, &done));
-        if (done) return Status();
-    }
-    for (u32 u = 0; u < d->n; u++)
-        if (d->color[u] >= d->num_colors) return fail(TMOTIF_ERR_INVALID, "color out of range");
-    std::vector<HArc> arcs;
-    try {
-        arcs.reserve(cap);
-    } catch (const std::bad_alloc &) {
-        return fail(TMOTIF_ERR_OOM, "host allocation failed");
-    }
-    u64 loops = 0;
-    u32 tmax = 0;
-    for (u64 e = 0; e < d->m; e++) {
-        const u32 a = d->src[e], b = d->dst[e], t = d->time[e];
-        if (a >= d->n || b >= d->n) return fail(TMOTIF_ERR_INVALID, "vertex id out of range");
-        if (t == 0) return fail(TMOTIF_ERR_INVALID, "timestamp 0 (timestamps are >= 1)");
-        if (a == b) { loops++; continue; }
-        tmax = std::max(tmax, t);
-        arcs.push_back({b, t, a});
-        if (d->undirected) arcs.push_back({a, t, b});
-    }
-    std::sort(arcs.begin(), arcs.end(), [](const HArc &x, const HArc &y) {
-        if (x.dst != y.dst) return x.dst < y.dst;
-        if (x.time != y.time) return x.time < y.time;
-        return x.src < y.src;
-    });
-    u64 w = 0;
-    for (u64 e = 0; e < arcs.size(); e++) {
-        if (w > 0 && arcs[w - 1].dst == arcs[e].dst && arcs[w - 1].time == arcs[e].time &&
-            arcs[w - 1].src == arcs[e].src)
-            continue;
-        arcs[w++] = arcs[e];
-    }
-    g->n = d->n;
-    g->m_input = d->m;
-    g->m = w;
-    g->self_loops = loops;
-    g->duplicates = arcs.size() - w;
-    g->num_colors = d->num_colors;
-    g->max_time = tmax;
-    g->stream = (cudaStream_t)d->cuda_stream;
-    g->h_color = std::make_shared<std::vector<u32>>(d->color, d->color + d->n);
-    std::vector<u32> hs(w), hd(w), ht(w);
-    for (u64 e = 0; e < w; e++) { hs[e] = arcs[e].src; hd[e] = arcs[e].dst; ht[e] = arcs[e].time; }
-    arcs.clear();
-    arcs.shrink_to_fit();
-    const u64 mb = std::max<u64>(w, 1) * 4;
-    TM_TRY(dev_alloc((void **)&g->d_src, mb, g->stream));
-    TM_TRY(dev_alloc((void **)&g->d_dst, mb, g->stream));
-    TM_TRY(dev_alloc((void **)&g->d_time, mb, g->stream));
-    TM_TRY(dev_alloc((void **)&g->d_color, std::max<u64>(d->n, 1) * 4, g->stream));
-    g->resident_bytes = 3 * mb + std::max<u64>(d->n, 1) * 4;
-    TM_CUDA(cudaMemcpyAsync(g->d_src, hs.data(), w * 4, cudaMemcpyHostToDevice, g->stream));
-    TM_CUDA(cudaMemcpyAsync(g->d_dst, hd.data(), w * 4, cudaMemcpyHostToDevice, g->stream));
-    TM_CUDA(cudaMemcpyAsync(g->d_time, ht.data(), w * 4, cudaMemcpyHostToDevice, g->stream));
-    TM_CUDA(cudaMemcpyAsync(g->d_color, d->color, (u64)d->n * 4, cudaMemcpyHostToDevice, g->stream));
-    TM_CUDA(cudaStreamSynchronize(g->stream));
-    return Status();
+    return build_graph_device(d, g);
 }
 
 void release_graph_arrays(Graph *g)

@@ -356,9 +356,10 @@ Status static_graph_ensure(Graph &g);
 Status static_sieve(Graph &g, const QuerySpec &q, const uint8_t *d_alive, u64 *d_Qv, u64 *kept_pairs);
 // d_mask[u] = (Q_u != 0), device n bytes.
 Status static_mask(Graph &g, const QuerySpec &q, const uint8_t *d_alive, uint8_t *d_mask, u64 *kept_pairs);
-// Device build; *done = false (and no error) when the packed arc key would not
-// fit 64 bits, in which case the caller builds on the host.
-Status build_graph_device(const tmotif_graph_desc *d, Graph *g, bool *done);
+// Device build of the resident arc arrays from the caller's host arrays:
+// validation, orientation, self-loop and duplicate removal, (dst, time, src)
+// order.
+Status build_graph_device(const tmotif_graph_desc *d, Graph *g);
 
 // Device GF multiply of host arrays (diagnostic).
 Status gf_mul_batch(const u64 *a, const u64 *b, u64 *out, u64 n);

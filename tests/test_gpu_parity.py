@@ -261,6 +261,42 @@ def test_device_graph_build_matches_canonical_set(tm):
         G.close()
 
 
+def test_wide_arc_keys_build_and_sieve(tm):
+    # 17-bit vertex ids with timestamps up to 2^32 - 1: dst | time | src needs
+    # 66 bits, so the device build sorts (time | src, dst) pairs instead of one
+    # key; the arc set, decisions, extraction and optimum time must still
+    # equal the oracle's
+    rng = np.random.default_rng(17)
+    n, m = 70000, 120000
+    src = rng.integers(0, n, m, dtype=np.uint32)
+    dst = rng.integers(0, n, m, dtype=np.uint32)
+    time = rng.integers(1, 2**32, m, dtype=np.uint64).astype(np.uint32)
+    time[: m // 3] = rng.integers(2**31, 2**31 + 40, m // 3).astype(np.uint32)  # many time ties
+    time[-5:] = 2**32 - 1
+    src[: m // 20] = dst[: m // 20]                          # self-loops
+    src[m // 20: m // 10] = src[m // 10: 3 * m // 20]        # duplicates
+    dst[m // 20: m // 10] = dst[m // 10: 3 * m // 20]
+    time[m // 20: m // 10] = time[m // 10: 3 * m // 20]
+    color = rng.integers(0, 3, n, dtype=np.uint32)
+    for und in (False, True):
+        G = tm.tmotif_create_graph(n, src, dst, time, color, 3, undirected=und)
+        info = tm.tmotif_graph_get_info(G)
+        cs, cd, ct = oracle.canon(n, src, dst, time, und)
+        assert info["m_arcs"] == len(cs)
+        assert info["self_loops"] == int(np.sum(src == dst))
+        for k, ms, kw in ((3, [0, 1, 2], {}), (4, [0, 0, 1, 2], {"t_min": 2**31, "t_max": 2**31 + 30}),
+                          (4, [1, 2, 2, 0], {"end": int(cd[7])})):
+            d = tm.tmotif_decide(G, k, ms, seed=3, **kw)
+            o = oracle.decide(n, src, dst, time, color, 3, k, ms, undirected=und, seed=3, **kw)
+            assert_same(d, o)
+            f, v, t = tm.tmotif_extract(G, k, ms, seed=3, method="halving", **kw)
+            fo, vo, to, _ = oracle.extract(n, src, dst, time, color, 3, k, ms, undirected=und, seed=3, **kw)
+            assert f == fo and np.array_equal(v, vo) and np.array_equal(t, to)
+        t_opt = tm.tmotif_optimum_time(G, 4, [0, 1, 2, 0], seed=5)
+        assert t_opt == oracle.optimum_time(n, src, dst, time, color, 3, 4, [0, 1, 2, 0], undirected=und, seed=5)
+        G.close()
+
+
 # ---------------------------------------------------------------------------
 # Extraction (Sec. 6.9): same deterministic procedure -> the same path
 # ---------------------------------------------------------------------------
