@@ -39,20 +39,19 @@ WORKLOAD = ("power-law out-degree 2.1, n=1e6, m=1e7 (+50 planted arcs), t in [1,
 
 # Speed of light of the layer kernel, from GB300 unit counts at the maximum SM
 # clock (152 SMs, 2070 MHz) and per-product costs measured by ncu on the
-# library's register-resident probe (tmotif_gf_probe methods 0-2; see
-# profiles/gf_product_probe_instruction_counts.md).  A launch's lower-bound
-# time is the largest of three pipe times for its work:
+# library's register-resident probe (tmotif_gf_probe methods 0-2).  A launch's
+# lower-bound time is the largest of three pipe times for its work:
 #   shared memory, 1 wavefront (128 B) per clock per SM: a table product
 #     reads 16 eight-byte entries (1 wavefront); a table build writes 2 KB
 #     (16 wavefronts);
-#   ALU pipe, 64 lanes per clock per SM: 47.1 ALU instructions per table
-#     product plus 1216 per table build (fitted to the probe at 64 and 128
-#     lanes per table: 66.1 and 56.6 per product), 92.6 per register product
+#   ALU pipe, 64 lanes per clock per SM: 39.6 ALU instructions per table
+#     product plus 1059 per table build (fitted to the probe at 64 and 128
+#     lanes per table: 56.1 and 47.8 per product), 92.6 per register product
 #     (probe counts less about 3-4 of probe loop work);
 #   FMA pipe: 9.28 sub-partition cycles per register product (4 per SM).
 SMS = 152
 SM_HZ = 2.070e9
-ALU_PER_REG, ALU_PER_TAB, ALU_PER_BUILD = 92.6, 47.1, 1216.0
+ALU_PER_REG, ALU_PER_TAB, ALU_PER_BUILD = 92.6, 39.6, 1059.0
 WF_PER_TAB, WF_PER_BUILD = 1.0, 16.0
 FMA_CYC_PER_REG = 9.28
 
@@ -69,8 +68,8 @@ def layer_bound_s(reg, tab, builds):
 # DRAM traffic of one layer launch from an ncu capture, valid only for the
 # layer-kernel sources it was taken on (source_sha() below, first 16 hex):
 # a timed-decision layer of the default workload, full size, one-pass dram
-# counters (profiles/k_layer_mid_n1e6_m1e7_k6_dram.md)
-LAYER_TRAFFIC = {"source_sha": "e8f0cdb1f52c15ca", "bytes_per_launch": 1120147200 + 399555840}
+# counters
+LAYER_TRAFFIC = {"source_sha": "d2fbaa5557b721c0", "bytes_per_launch": 1119535616 + 399804160}
 
 
 def parse_args():

@@ -270,7 +270,8 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
  * carry-less products with holes); method 1 = a warp builds the 16 x 16 nibble
  * table of one multiplier in shared memory and applies it to 64 lanes (2 per
  * thread); method 2 = the same table applied to 128 lanes (4 per thread);
- * method 3 = method 1 with the lookup's nibble shifts done by multiplies.
+ * method 3 = method 1 with the older lookup address (a shift and a logic op
+ * per load) and its nibble shifts done by multiplies.
  * Runs `iters` rounds; ms receives the device time, products the products
  * done.  INVALID for another method or iters = 0. */
 int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products);

@@ -56,11 +56,20 @@ __device__ __forceinline__ u64 gf_mul(u64 a, u64 b)
 
 // a * x^s mod f for 0 <= s < 61 (the bits shifted out are < 2^s, and
 // hi * (x^4 + x^3 + x + 1) < 2^(s+4) <= 2^64, so one fold suffices).
+// Branch-free for a per-thread s: the clamped funnel shifts take shift
+// amounts up to 32, and a second shift by max(s - 32, 0) or max(32 - s, 0)
+// covers the rest (s = 0 gives hi = 0).
 __device__ __forceinline__ u64 gf_mul_xpow(u64 a, int s)
 {
-    if (s == 0) return a;
-    u64 hi = a >> (64 - s);
-    return (a << s) ^ hi ^ (hi << 1) ^ (hi << 3) ^ (hi << 4);
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
+    const u32 up = (u32)s, dn = 64u - up;                     // a << up, a >> dn
+    const u32 up2 = up > 32u ? up - 32u : 0u, dn2 = dn > 32u ? dn - 32u : 0u;
+    const u32 r0 = __funnelshift_lc(0u, a0, up);              // (a << s) low word
+    const u32 r1 = __funnelshift_lc(0u, __funnelshift_lc(a0, a1, up), up2);
+    const u32 h0 = __funnelshift_rc(__funnelshift_rc(a0, a1, dn), 0u, dn2);
+    const u32 h1 = __funnelshift_rc(a1, 0u, dn);
+    const u64 hi = ((u64)h1 << 32) | h0;
+    return (((u64)r1 << 32) | r0) ^ hi ^ (hi << 1) ^ (hi << 3) ^ (hi << 4);
 }
 
 // a * x mod f.
@@ -85,10 +94,8 @@ __device__ __forceinline__ u64 gf_mul_x(u64 a)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthreads)
 {
-    const int per = 256 / nthreads;           // 8, 16 or 32 entries
-    const int first = tt * per;               // first entry index i*16 + b
-    for (int e0 = first; e0 < first + per; e0 += 8) {
-        const int i = e0 >> 4, h = (e0 >> 3) & 1;
+    if (nthreads == 32) {  // half a row (8 entries) per thread
+        const int i = tt >> 1, h = tt & 1;
         const u64 b0 = gf_mul_xpow(y, 4 * i);
         const u64 b1 = gf_mul_x(b0), b2 = gf_mul_x(b1);
         const u64 base = h ? gf_mul_x(b2) : 0ull;
@@ -98,6 +105,22 @@ __device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthr
         row[(c0 + 1) ^ sw] = make_ulonglong2(base ^ b1, base ^ b1 ^ b0);
         row[(c0 + 2) ^ sw] = make_ulonglong2(base ^ b2, base ^ b2 ^ b0);
         row[(c0 + 3) ^ sw] = make_ulonglong2(base ^ b2 ^ b1, base ^ b2 ^ b1 ^ b0);
+        return;
+    }
+    const int rows = 16 / nthreads;  // whole rows per thread (1 or 2)
+    for (int i = tt * rows; i < (tt + 1) * rows; i++) {
+        const u64 b0 = gf_mul_xpow(y, 4 * i);
+        const u64 b1 = gf_mul_x(b0), b2 = gf_mul_x(b1), b3 = gf_mul_x(b2);
+        ulonglong2 *row = (ulonglong2 *)(tab + i * 16);
+        const int sw = i & 7;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const u64 base = h ? b3 : 0ull;
+            row[(4 * h + 0) ^ sw] = make_ulonglong2(base, base ^ b0);
+            row[(4 * h + 1) ^ sw] = make_ulonglong2(base ^ b1, base ^ b1 ^ b0);
+            row[(4 * h + 2) ^ sw] = make_ulonglong2(base ^ b2, base ^ b2 ^ b0);
+            row[(4 * h + 3) ^ sw] = make_ulonglong2(base ^ b2 ^ b1, base ^ b2 ^ b1 ^ b0);
+        }
     }
 }
 
@@ -105,9 +128,11 @@ __device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthr
 // that its shared address has bits 0..10 clear: the address of entry b of row
 // i is then (address | (b' << 3)) + 128 i, where b' = b ^ 2(i & 7) is the
 // swizzled column.  XORing s once with 0xECA86420ECA86420 (nibble i of the
-// constant is 2(i & 7)) swizzles all sixteen nibbles at once, so each lookup
-// costs a shift and one three-input logic op for its address, and the row
-// offset rides in the load's immediate.
+// constant is 2(i & 7)) swizzles all sixteen nibbles at once.  Two masked
+// shifts per 32-bit half place every nibble, times 8, in a byte of its own
+// (even nibbles in one word, odd nibbles in the other); one byte permute per
+// lookup then merges that byte with the table address's upper bytes, and the
+// row offset rides in the load's immediate.
 #define TM_LDS64(out, addr, off) asm volatile("ld.shared.b64 %0, [%1+" #off "];" : "=l"(out) : "r"(addr))
 
 __device__ __forceinline__ u64 gf_table_mul(const u64 *tab, u64 s)
@@ -115,23 +140,29 @@ __device__ __forceinline__ u64 gf_table_mul(const u64 *tab, u64 s)
     const u32 ta = (u32)__cvta_generic_to_shared(tab);
     const u64 sw = s ^ 0xECA86420ECA86420ull;
     const u32 lo = (u32)sw, hi = (u32)(sw >> 32);
+    // byte j of e* / o*: nibble 2j / 2j+1 of the half, times 8
+    const u32 el = (lo << 3) & 0x78787878u, ol = (lo >> 1) & 0x78787878u;
+    const u32 eh = (hi << 3) & 0x78787878u, oh = (hi >> 1) & 0x78787878u;
+    // byte 0 from the nibble word, bytes 1..3 from the table address
+#define TM_NIB(w, j) __byte_perm((w), ta, 0x7650u + (j))
     u64 v0, v1, v2, v3, v4, v5, v6, v7, v8, v9, v10, v11, v12, v13, v14, v15;
-    TM_LDS64(v0, ((lo << 3) & 0x78u) | ta, 0);
-    TM_LDS64(v1, ((lo >> 1) & 0x78u) | ta, 128);
-    TM_LDS64(v2, ((lo >> 5) & 0x78u) | ta, 256);
-    TM_LDS64(v3, ((lo >> 9) & 0x78u) | ta, 384);
-    TM_LDS64(v4, ((lo >> 13) & 0x78u) | ta, 512);
-    TM_LDS64(v5, ((lo >> 17) & 0x78u) | ta, 640);
-    TM_LDS64(v6, ((lo >> 21) & 0x78u) | ta, 768);
-    TM_LDS64(v7, ((lo >> 25) & 0x78u) | ta, 896);
-    TM_LDS64(v8, ((hi << 3) & 0x78u) | ta, 1024);
-    TM_LDS64(v9, ((hi >> 1) & 0x78u) | ta, 1152);
-    TM_LDS64(v10, ((hi >> 5) & 0x78u) | ta, 1280);
-    TM_LDS64(v11, ((hi >> 9) & 0x78u) | ta, 1408);
-    TM_LDS64(v12, ((hi >> 13) & 0x78u) | ta, 1536);
-    TM_LDS64(v13, ((hi >> 17) & 0x78u) | ta, 1664);
-    TM_LDS64(v14, ((hi >> 21) & 0x78u) | ta, 1792);
-    TM_LDS64(v15, ((hi >> 25) & 0x78u) | ta, 1920);
+    TM_LDS64(v0, TM_NIB(el, 0), 0);
+    TM_LDS64(v1, TM_NIB(ol, 0), 128);
+    TM_LDS64(v2, TM_NIB(el, 1), 256);
+    TM_LDS64(v3, TM_NIB(ol, 1), 384);
+    TM_LDS64(v4, TM_NIB(el, 2), 512);
+    TM_LDS64(v5, TM_NIB(ol, 2), 640);
+    TM_LDS64(v6, TM_NIB(el, 3), 768);
+    TM_LDS64(v7, TM_NIB(ol, 3), 896);
+    TM_LDS64(v8, TM_NIB(eh, 0), 1024);
+    TM_LDS64(v9, TM_NIB(oh, 0), 1152);
+    TM_LDS64(v10, TM_NIB(eh, 1), 1280);
+    TM_LDS64(v11, TM_NIB(oh, 1), 1408);
+    TM_LDS64(v12, TM_NIB(eh, 2), 1536);
+    TM_LDS64(v13, TM_NIB(oh, 2), 1664);
+    TM_LDS64(v14, TM_NIB(eh, 3), 1792);
+    TM_LDS64(v15, TM_NIB(oh, 3), 1920);
+#undef TM_NIB
     return ((v0 ^ v1 ^ v2) ^ (v3 ^ v4 ^ v5)) ^ ((v6 ^ v7 ^ v8) ^ (v9 ^ v10 ^ v11)) ^ ((v12 ^ v13 ^ v14) ^ v15);
 }
 
