@@ -83,7 +83,8 @@ struct Workspace {
     DevBuf slot_begin, slot_count;      // num_colors u32
     DevBuf seg_lo, seg_hi;              // n u32: filtered in-segment of each vertex
     DevBuf f_src, f_dst, f_time;        // filtered arcs (m u32 each)
-    DevBuf keep;                        // m+1 u32: flags, then exclusive offsets
+    DevBuf kbits;                       // one bit per arc (whole 4096-arc tiles): kept by the filter
+    DevBuf ftiles;                      // per filter tile: kept count, then exclusive offsets
     DevBuf pos;                         // m u32: last in-arc of src with time < t
     DevBuf mark;                        // m+1 u32: checkpoint flags, then indices
     DevBuf cp_in, cp_out;               // m u32
@@ -269,6 +270,14 @@ void release_graph_arrays(Graph *g);
 // new resident graph with the same vertex ids (extraction's shrinking
 // subgraph).  Uses workspace w on stream st.
 Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_t *d_alive, Graph *sub);
+// Arc filter (Sec. 8.1 (i)) in two passes: _count leaves the keep mask and
+// tile offsets in the workspace and the kept count in d_total (device u32);
+// after the caller reads the count and sizes the outputs, _compact writes the
+// kept arcs in arc order.
+Status filter_arcs_count(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time, u64 m,
+                         const uint8_t *vflag, const ArcFilter &f, u32 *d_total, u64 *launches);
+Status filter_arcs_compact(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time, u64 m,
+                           u32 *o_src, u32 *o_dst, u32 *o_time, u64 *launches);
 
 // Extraction (Sec. 6.9) as a state machine: next_probe() gives the next
 // decision to run (the first one is the query itself, the rest mask the

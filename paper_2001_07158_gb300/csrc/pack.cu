@@ -92,7 +92,7 @@ __global__ void k_pack_keep(u64 M, const u32 *src, const u32 *dst, const u32 *ti
     if (e > M) return;
     if (e == M) { keep[M] = 0; return; }
     const u32 d = dst[e];
-    bool k = vflag[src[e]] && vflag[d];
+    bool k = vflag[d] && vflag[src[e]];  // destinations are sorted: the source is read only when needed
     if (k) {
         const ArcFilter &f = qs[jv[d]].filter;
         const u32 t = time[e];

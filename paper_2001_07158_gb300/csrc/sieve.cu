@@ -52,22 +52,160 @@ __global__ void k_active_list(u32 n, const u32 *act, u32 *list)
     if (u < n && act[u + 1] != act[u]) list[act[u]] = (u32)u;
 }
 
-// Arc e is kept iff both endpoints are flagged, its time lies in the window
-// and, for EC-PathMotif (Sec. 7.3), its time is one of the tuple's.
-__global__ void k_keep(u64 m, const u32 *src, const u32 *dst, const u32 *time, const uint8_t *vflag, ArcFilter f,
-                       u32 *keep)
+// ---------------------------------------------------------------------------
+// Arc filter (Sec. 8.1 (i)).  Arc e is kept iff both endpoints are flagged,
+// its time lies in the window and, for EC-PathMotif (Sec. 7.3), its time is
+// one of the tuple's.  Two passes over tiles of 4096 arcs in arc order:
+//   k_filter_count writes one bit per arc (word j of the mask covers arcs
+//     32j..32j+31) and the tile's kept count;
+//   after an exclusive scan of the tile counts, k_filter_compact writes the
+//     kept arcs, in arc order, from the mask alone.
+// The destination's flag is tested first: arcs are sorted by destination,
+// so those reads are nearly sequential, and the scattered source flag and the
+// time are read only for arcs that pass the tests before them.
+// ---------------------------------------------------------------------------
+namespace {
+
+const int FILTER_THREADS = 256;
+const int FILTER_ROUNDS = 16;                                  // arcs per thread
+const int FILTER_TILE = FILTER_THREADS * FILTER_ROUNDS;        // 4096 arcs
+const int FILTER_WORDS = FILTER_TILE / 32;                     // 128 mask words
+
+__global__ void __launch_bounds__(FILTER_THREADS)
+k_filter_count(u64 m, const u32 *src, const u32 *dst, const u32 *time, const uint8_t *vflag, ArcFilter f, u32 *bits,
+               u32 *tile_count)
 {
-    u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e > m) return;
-    if (e == m) { keep[m] = 0; return; }
-    u32 t = time[e];
-    bool k = vflag[src[e]] && vflag[dst[e]] && t >= f.t_min && (f.t_max == 0 || t <= f.t_max);
-    if (k && f.n_times) {
-        bool in = false;
-        for (u32 i = 0; i < f.n_times; i++) in |= (f.times[i] == t);
-        k = in;
+    __shared__ u32 warp_count[FILTER_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const u64 base = (u64)blockIdx.x * FILTER_TILE;
+    const bool timed = f.t_min != 0 || f.t_max != 0 || f.n_times != 0;
+    u32 d[FILTER_ROUNDS];
+    bool k[FILTER_ROUNDS];
+#pragma unroll
+    for (int i = 0; i < FILTER_ROUNDS; i++) {
+        const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
+        d[i] = e < m ? dst[e] : 0u;
     }
-    keep[e] = k ? 1 : 0;
+#pragma unroll
+    for (int i = 0; i < FILTER_ROUNDS; i++) {
+        const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
+        k[i] = e < m && vflag[d[i]];
+    }
+#pragma unroll
+    for (int i = 0; i < FILTER_ROUNDS; i++) {
+        const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
+        if (k[i]) d[i] = src[e];  // d[] now holds the source
+    }
+#pragma unroll
+    for (int i = 0; i < FILTER_ROUNDS; i++)
+        if (k[i]) k[i] = vflag[d[i]];
+    if (timed) {
+#pragma unroll
+        for (int i = 0; i < FILTER_ROUNDS; i++) {
+            if (!k[i]) continue;
+            const u32 t = time[base + (u64)i * FILTER_THREADS + threadIdx.x];
+            bool in = t >= f.t_min && (f.t_max == 0 || t <= f.t_max);
+            if (in && f.n_times) {
+                // constant indices keep the tuple in the parameter space
+                bool hit = false;
+#pragma unroll
+                for (int r = 0; r < TMOTIF_KMAX; r++) hit |= (r < (int)f.n_times) && f.times[r] == t;
+                in = hit;
+            }
+            k[i] = in;
+        }
+    }
+    u32 count = 0;
+#pragma unroll
+    for (int i = 0; i < FILTER_ROUNDS; i++) {
+        const u32 b = __ballot_sync(0xffffffffu, k[i]);
+        if (lane == 0) bits[(u64)blockIdx.x * FILTER_WORDS + i * (FILTER_THREADS / 32) + w] = b;
+        count += __popc(b);
+    }
+    if (lane == 0) warp_count[w] = count;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 t = 0;
+        for (int i = 0; i < FILTER_THREADS / 32; i++) t += warp_count[i];
+        tile_count[blockIdx.x] = t;
+    }
+}
+
+// tile_off: exclusive offsets of the tiles' kept counts.  One warp per tile,
+// in 4 rounds of 32 mask words (1024 arcs): lane l owns word l of the round;
+// a warp scan of the words' counts places each word's kept arcs, whose tile
+// indices the lane lists in shared memory in arc order; the warp then copies
+// the listed arcs with independent loads and contiguous stores.
+__global__ void __launch_bounds__(FILTER_THREADS)
+k_filter_compact(const u32 *__restrict__ src, const u32 *__restrict__ dst, const u32 *__restrict__ time,
+                 const u32 *__restrict__ bits, const u32 *__restrict__ tile_off, u32 ntiles, u32 *__restrict__ f_src,
+                 u32 *__restrict__ f_dst, u32 *__restrict__ f_time)
+{
+    __shared__ uint16_t list[FILTER_THREADS / 32][1024];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const u64 tile = (u64)blockIdx.x * (FILTER_THREADS / 32) + w;
+    if (tile >= ntiles) return;
+    uint16_t *q = list[w];
+    const u64 abase = tile * FILTER_TILE;
+    u32 out = tile_off[tile];
+    for (int r = 0; r < FILTER_WORDS / 32; r++) {
+        const int wi = 32 * r + lane;  // word index in the tile
+        u32 b = bits[tile * FILTER_WORDS + wi];
+        const u32 c = __popc(b);
+        u32 incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const u32 total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) continue;
+        u32 p = incl - c;
+        while (b) {
+            const int bit = __ffs(b) - 1;
+            b &= b - 1;
+            q[p++] = (uint16_t)(wi * 32 + bit);
+        }
+        __syncwarp();
+        for (u32 i = lane; i < total; i += 32) {
+            const u64 e = abase + q[i];
+            f_src[out + i] = src[e];
+            f_dst[out + i] = dst[e];
+            f_time[out + i] = time[e];
+        }
+        __syncwarp();
+        out += total;
+    }
+}
+
+}  // namespace
+
+// First pass of the arc filter: the keep mask in w.kbits, the tile offsets in
+// w.ftiles and the kept count to d_total (device u32).
+Status filter_arcs_count(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time, u64 m,
+                         const uint8_t *vflag, const ArcFilter &f, u32 *d_total, u64 *launches)
+{
+    const u64 ntiles = std::max<u64>(1, (m + FILTER_TILE - 1) / FILTER_TILE);
+    TM_TRY(w.kbits.reserve(ntiles * FILTER_WORDS * 4));
+    TM_TRY(w.ftiles.reserve(ntiles * 4));
+    k_filter_count<<<(unsigned)ntiles, FILTER_THREADS, 0, st>>>(m, src, dst, time, vflag, f, w.kbits.as<u32>(),
+                                                                w.ftiles.as<u32>());
+    if (launches) *launches += 1;
+    TM_CUDA(cudaGetLastError());
+    return exclusive_scan_on(st, w.block_sums, w.ftiles.as<u32>(), ntiles, d_total, launches);
+}
+
+// Second pass: the kept arcs, in arc order, into (o_src, o_dst, o_time).
+Status filter_arcs_compact(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time, u64 m,
+                           u32 *o_src, u32 *o_dst, u32 *o_time, u64 *launches)
+{
+    const u64 ntiles = std::max<u64>(1, (m + FILTER_TILE - 1) / FILTER_TILE);
+    const u64 per_block = FILTER_THREADS / 32;
+    k_filter_compact<<<(unsigned)((ntiles + per_block - 1) / per_block), FILTER_THREADS, 0, st>>>(
+        src, dst, time, w.kbits.as<u32>(), w.ftiles.as<u32>(), (u32)ntiles, o_src, o_dst, o_time);
+    if (launches) *launches += 1;
+    TM_CUDA(cudaGetLastError());
+    return Status();
 }
 
 // keep[] holds exclusive offsets (length m+1); arc e is kept iff keep[e+1] > keep[e].
@@ -353,7 +491,7 @@ size_t job_bytes(const Job &j)
 {
     const u64 n = j.g->n, m = j.mf ? j.mf : j.g->m, L = j.L ? j.L : LANES_MAX;
     const u64 ncp = j.mf ? j.ncp : m;
-    return (size_t)(n * (1 + 8) + (j.g->m + 1) * 4 + m * 28 + n * L * 8 + 2 * ncp * L * 8 +
+    return (size_t)(n * (1 + 8) + j.g->m / 8 + 4096 + m * 28 + n * L * 8 + 2 * ncp * L * 8 +
                     ((m + CHUNK_MIN - 1) / CHUNK_MIN) * L * 8 + 4096);
 }
 
@@ -386,14 +524,12 @@ Status job_prep(Job &j)
     TM_TRY(w.vflag.reserve(std::max<u64>(n, 1)));
     TM_TRY(w.act.reserve(((u64)n + 1) * 4));
     TM_TRY(w.act_list.reserve(std::max<u64>(n, 1) * 4));
-    TM_TRY(w.keep.reserve((m + 1) * 4));
     k_vflag<<<grid_for((u64)n + 1, 256), 256, 0, st>>>(n, g.d_color, w.slot_count.as<u32>(), j.d_alive,
                                                        w.vflag.as<uint8_t>(), w.act.as<u32>());
-    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), q.filter(),
-                                                 w.keep.as<u32>());
-    *launches += 2;
+    *launches += 1;
     TM_CUDA(cudaGetLastError());
-    TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt + 0, launches));
+    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, m, w.vflag.as<uint8_t>(), q.filter(), d_cnt + 0,
+                             launches));
     TM_TRY(exclusive_scan_on(st, w.block_sums, w.act.as<u32>(), (u64)n + 1, d_cnt + 2, launches));
     k_active_list<<<grid_for(n, 256), 256, 0, st>>>(n, w.act.as<u32>(), w.act_list.as<u32>());
     *launches += 1;
@@ -413,15 +549,15 @@ Status job_prep(Job &j)
         TM_TRY(w.cp_out.reserve(mf * 4));
         TM_TRY(w.seg_lo.reserve((u64)n * 4));
         TM_TRY(w.seg_hi.reserve((u64)n * 4));
-        k_compact<<<grid_for(m, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.keep.as<u32>(),
-                                                    w.f_src.as<u32>(), w.f_dst.as<u32>(), w.f_time.as<u32>());
+        TM_TRY(filter_arcs_compact(st, w, g.d_src, g.d_dst, g.d_time, m, w.f_src.as<u32>(), w.f_dst.as<u32>(),
+                                   w.f_time.as<u32>(), launches));
         TM_CUDA(cudaMemsetAsync(w.seg_lo.p, 0, (u64)n * 4, st));
         TM_CUDA(cudaMemsetAsync(w.seg_hi.p, 0, (u64)n * 4, st));
         TM_CUDA(cudaMemsetAsync(w.mark.p, 0, (mf + 1) * 4, st));
         k_segments<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_dst.as<u32>(), w.seg_lo.as<u32>(), w.seg_hi.as<u32>());
         k_pos<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_src.as<u32>(), w.f_time.as<u32>(), w.seg_lo.as<u32>(),
                                                  w.seg_hi.as<u32>(), w.pos.as<u32>(), w.mark.as<u32>());
-        *launches += 3;
+        *launches += 2;
         TM_CUDA(cudaGetLastError());
         TM_TRY(exclusive_scan_on(st, w.block_sums, w.mark.as<u32>(), mf + 1, d_cnt + 1, launches));
         k_checkpoints<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.pos.as<u32>(), w.mark.as<u32>(), w.cp_in.as<u32>(),
@@ -875,15 +1011,13 @@ Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, cons
 {
     const u64 m = g.m;
     TM_TRY(w.vflag.reserve(std::max<u64>(g.n, 1)));
-    TM_TRY(w.keep.reserve((m + 1) * 4));
     TM_TRY(w.counters.reserve(64));
     k_vflag_mask<<<grid_for(g.n, 256), 256, 0, st>>>(g.n, d_alive, w.vflag.as<uint8_t>());
-    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(), f,
-                                                 w.keep.as<u32>());
-    prof.stats.launches += 2;
+    prof.stats.launches += 1;
     TM_CUDA(cudaGetLastError());
     u32 *d_cnt = w.counters.as<u32>();
-    TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt, (u64 *)&prof.stats.launches));
+    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, m, w.vflag.as<uint8_t>(), f, d_cnt,
+                             (u64 *)&prof.stats.launches));
     u32 mf = 0;
     TM_CUDA(cudaMemcpyAsync(&mf, d_cnt, 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
@@ -894,10 +1028,8 @@ Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, cons
     TM_TRY(w.f_src.reserve((u64)mf * 4));
     TM_TRY(w.f_dst.reserve((u64)mf * 4));
     TM_TRY(w.f_time.reserve((u64)mf * 4));
-    k_compact<<<grid_for(m, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.keep.as<u32>(), w.f_src.as<u32>(),
-                                                w.f_dst.as<u32>(), w.f_time.as<u32>());
-    prof.stats.launches++;
-    TM_CUDA(cudaGetLastError());
+    TM_TRY(filter_arcs_compact(st, w, g.d_src, g.d_dst, g.d_time, m, w.f_src.as<u32>(), w.f_dst.as<u32>(),
+                               w.f_time.as<u32>(), (u64 *)&prof.stats.launches));
     TM_CUDA(cudaMemcpyAsync(src->data(), w.f_src.p, (u64)mf * 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaMemcpyAsync(dst->data(), w.f_dst.p, (u64)mf * 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaMemcpyAsync(time->data(), w.f_time.p, (u64)mf * 4, cudaMemcpyDeviceToHost, st));
@@ -909,14 +1041,12 @@ Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_
 {
     const u64 m = g.m;
     TM_TRY(w.vflag.reserve(std::max<u64>(g.n, 1)));
-    TM_TRY(w.keep.reserve((m + 1) * 4));
     TM_TRY(w.counters.reserve(64));
     k_vflag_mask<<<grid_for(g.n, 256), 256, 0, st>>>(g.n, d_alive, w.vflag.as<uint8_t>());
-    k_keep<<<grid_for(m + 1, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.vflag.as<uint8_t>(),
-                                                 ArcFilter(), w.keep.as<u32>());
     TM_CUDA(cudaGetLastError());
     u32 *d_cnt = w.counters.as<u32>();
-    TM_TRY(exclusive_scan_on(st, w.block_sums, w.keep.as<u32>(), m + 1, d_cnt, nullptr));
+    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, m, w.vflag.as<uint8_t>(), ArcFilter(), d_cnt,
+                             nullptr));
     u32 mk = 0;
     TM_CUDA(cudaMemcpyAsync(&mk, d_cnt, 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
@@ -933,9 +1063,7 @@ Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_
     TM_TRY(dev_alloc((void **)&sub->d_dst, mb, st));
     TM_TRY(dev_alloc((void **)&sub->d_time, mb, st));
     TM_TRY(dev_alloc((void **)&sub->d_color, std::max<u64>(g.n, 1) * 4, st));
-    if (mk)
-        k_compact<<<grid_for(m, 256), 256, 0, st>>>(m, g.d_src, g.d_dst, g.d_time, w.keep.as<u32>(), sub->d_src,
-                                                    sub->d_dst, sub->d_time);
+    if (mk) TM_TRY(filter_arcs_compact(st, w, g.d_src, g.d_dst, g.d_time, m, sub->d_src, sub->d_dst, sub->d_time, nullptr));
     TM_CUDA(cudaMemcpyAsync(sub->d_color, g.d_color, (u64)g.n * 4, cudaMemcpyDeviceToDevice, st));
     TM_CUDA(cudaGetLastError());
     sub->resident_bytes = 3 * mb + (u64)g.n * 4;

@@ -297,6 +297,29 @@ def test_wide_arc_keys_build_and_sieve(tm):
         G.close()
 
 
+def test_arc_filter_over_ragged_tiles(tm):
+    # the per-query arc filter works on 4096-arc tiles with a keep mask of one
+    # bit per arc: graphs of several tiles and a ragged last tile, with time
+    # windows, EC tuples, masked (extraction) and preprocessed subgraphs,
+    # must give the oracle's per-point sums and paths
+    for m, seed in ((4096 * 3 + 123, 41), (4096 * 5, 42), (4095, 43)):
+        g = synth.uniform_graph(2500, m, 40, 4, seed=seed)
+        G = gpu_graph(tm, g)
+        for k, ms, kw in ((4, [0, 1, 2, 3], {}), (5, [0, 0, 1, 2, 3], {"t_min": 5, "t_max": 33}),
+                          (3, [1, 2, 2], {"t_max": 20, "start": 7})):
+            assert_same(*both(tm, G, g, k, ms, **kw))
+            f, v, t = tm.tmotif_extract(G, k, ms, method="halving", **kw)
+            fo, vo, to, _ = oracle.extract(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, **kw)
+            assert f == fo and np.array_equal(v, vo) and np.array_equal(t, to)
+        d, o = _ec_both(tm, G, g, 4, [0, 1, 2, 3], [3, 9, 17])
+        assert_same(d, o)
+        d = tm.tmotif_decide(G, 4, [0, 1, 2, 3], seed=5, preprocess=True)
+        fo, so, po, _ = oracle.decide_preprocessed(g.n, g.src, g.dst, g.time, g.color, g.num_colors, 4, [0, 1, 2, 3],
+                                                  seed=5)
+        assert_same(d, (fo, so, po))
+        G.close()
+
+
 # ---------------------------------------------------------------------------
 # Extraction (Sec. 6.9): same deterministic procedure -> the same path
 # ---------------------------------------------------------------------------
