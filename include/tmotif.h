@@ -249,13 +249,16 @@ void tmotif_server_destroy(tmotif_server_t s);
 int tmotif_set_profiling(tmotif_graph_t g, int on);
 
 /* Launch shape of the generating-function layer kernel for lane width L (a
- * power of two in [4, 128]) on graph g: arcs per team chunk (64, 128 or 256)
+ * power of two in [4, 128]) on graph g: arcs per team chunk (64, 128, 256,
+ * 512 or 1024)
  * and the kernel variant (0 = the default form; 1 = at most 64 registers per
  * thread, 2 = at most 128, for L = 16 and 64; 3 = 16-thread teams at 2 lanes
- * per thread instead of the default warp team at one lane, for L = 32).  The library's autotuner picks it on the first
- * decision that needs it, by timing every candidate on one layer; set pins
- * it (results never depend on it), get reads it (NOT_FOUND when none is set
- * yet).  Errors: INVALID for a bad L, chunk or variant. */
+ * per thread instead of the default warp team at one lane, for L = 32; 1 =
+ * two 64-lane teams per chunk at 2 lanes per thread instead of one warp at 4,
+ * for L = 128).  The library's autotuner picks it on the first decision that
+ * needs it, by timing every candidate on one layer; set pins it (results
+ * never depend on it), get reads it (NOT_FOUND when none is set yet).
+ * Errors: INVALID for a bad L, chunk or variant. */
 int tmotif_set_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t chunk, uint32_t variant);
 int tmotif_get_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t *chunk, uint32_t *variant);
 int tmotif_get_stats(tmotif_graph_t g, tmotif_stats *out);

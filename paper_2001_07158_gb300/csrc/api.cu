@@ -547,8 +547,9 @@ int tmotif_set_profiling(tmotif_graph_t g, int on)
 static bool valid_shape(uint32_t L, uint32_t chunk, uint32_t variant)
 {
     const bool pow2 = L >= 4 && L <= 128 && (L & (L - 1)) == 0;
-    const bool ch = chunk == 64 || chunk == 128 || chunk == 256;
-    const bool var = variant == 0 || (variant <= 2 && (L == 16 || L == 64)) || (variant == 3 && L == 32);
+    const bool ch = chunk == 64 || chunk == 128 || chunk == 256 || chunk == 512 || chunk == 1024;
+    const bool var = variant == 0 || (variant <= 2 && (L == 16 || L == 64)) || (variant == 3 && L == 32) ||
+                     (variant == 1 && L == 128);
     return pow2 && ch && var;
 }
 

@@ -487,6 +487,17 @@ static Status ensure_pinned(Workspace &w, size_t bytes = PIN_BYTES)
     return Status();
 }
 
+// Team width, lane groups and chunk count of a job's layer launches from its
+// lane width and shape: 2 lanes per thread (T = L / 2, at most 32), 4 at
+// L = 128; variant 1 at L = 128 splits the lanes over two 64-lane teams of
+// the 2-lanes-per-thread form (one table build per team).
+static void set_team_shape(Job &j)
+{
+    j.T = j.L / 2 > 32 ? 32 : j.L / 2;
+    j.lane_groups = (j.L == 128 && j.variant == 1) ? 2 : 1;
+    j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
+}
+
 size_t job_bytes(const Job &j)
 {
     const u64 n = j.g->n, m = j.mf ? j.mf : j.g->m, L = j.L ? j.L : LANES_MAX;
@@ -593,8 +604,6 @@ Status job_prep(Job &j)
         while (L > 4 && per_lane * L > room / 10 * 9) L >>= 1;
     }
     j.L = L;
-    j.T = L / 2 > 32 ? 32 : L / 2;  // 2 lanes per thread, 4 at L = 128
-    j.lane_groups = 1;
     j.chunk = CHUNK;
     j.variant = 0;
     {  // the launch shape pinned or tuned for this graph and lane width, else
@@ -610,7 +619,7 @@ Status job_prep(Job &j)
             j.variant = shape.second;
         }
     }
-    j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
+    set_team_shape(j);
     TM_TRY(w.x.reserve((u64)n * L * 8));
     TM_TRY(w.C0.reserve(std::max<u64>(j.ncp, 1) * L * 8));
     TM_TRY(w.C1.reserve(std::max<u64>(j.ncp, 1) * L * 8));
@@ -736,11 +745,14 @@ static Status launch_layer_class(cudaStream_t st, u32 L, u32 variant, const Laye
             if (variant == 3 && njobs == 0) return launch_layer_t<16, true, 2, 0>(st, one, jobs, prefix, njobs, teams);
             return launch_layer_v<32, true, 1>(st, variant, one, jobs, prefix, njobs, teams);
         case 64: return launch_layer_v<32, true, 2>(st, variant, one, jobs, prefix, njobs, teams);
-        default: return launch_layer_v<32, true, 4>(st, variant, one, jobs, prefix, njobs, teams);
+        default:
+            if (variant == 1 && njobs == 0)  // two 64-lane teams per chunk (lane_groups = 2)
+                return launch_layer_t<32, true, 2, 0>(st, one, jobs, prefix, njobs, teams);
+            return launch_layer_v<32, true, 4>(st, variant, one, jobs, prefix, njobs, teams);
     }
 }
 
-static void count_layer(Profiler *prof, const Job &j)
+static void count_layer(Profiler *prof, const Job &j, u32 lane_groups)
 {
     const u64 L = j.L, k = j.q.k;
     prof->stats.layer_arc_lanes += j.mf * L;
@@ -752,7 +764,7 @@ static void count_layer(Profiler *prof, const Job &j)
     prof->stats.layer_gf_muls += (j.mf + writes) * L;
     if (j.T >= 8) {
         prof->stats.layer_table_muls += j.mf * L;
-        prof->stats.layer_table_builds += j.mf;
+        prof->stats.layer_table_builds += j.mf * lane_groups;
     }
 }
 
@@ -770,7 +782,7 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         TM_TRY(prof->end(st, la, FAM_LAYER));
         prof->stats.launches++;
         prof->stats.layer_launches++;
-        count_layer(prof, j);
+        count_layer(prof, j, j.lane_groups);
         return Status();
     }
     // group by lane width; per class: job table + team prefix
@@ -789,9 +801,10 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         u64 teams = 0;
         for (size_t i = 0; i < cls.size(); i++) {
             hp[i] = job_layer_params(*cls[i]);
+            hp[i].lane_groups = 1;  // multi-job launches use the default form of each class
             hpre[i] = teams;
-            teams += cls[i]->n_chunks * cls[i]->lane_groups;
-            count_layer(prof, *cls[i]);
+            teams += cls[i]->n_chunks;
+            count_layer(prof, *cls[i], 1);
         }
         hpre[cls.size()] = teams;
         TM_TRY(dev_params.reserve(host_params_bytes));
@@ -836,10 +849,11 @@ bool tuned_shape(u32 L, u64 mf, std::pair<u32, u32> *shape)
 // Autotuner of the layer kernel's launch shape.  On the first lane batch of
 // a decision whose (graph, lane width) has no entry yet and whose layers
 // hold at least 2^22 arc-lanes, layer 3 is launched
-// for every candidate -- arcs per team chunk in {64, 128, 256} x register
+// for every candidate -- arcs per team chunk in {64, ..., 1024} x register
 // shape {compiler's budget, 4 blocks per SM, 2 blocks per SM} (table forms at
 // 2 lanes per thread, L = 16 and 64; at L = 32 the one-lane warp team and
-// the two-lane 16-thread team) -- twice, each
+// the two-lane 16-thread team; at L = 128 the four-lane warp team and two
+// two-lane teams) -- twice, each
 // launch timed by CUDA events on the job's stream.  The fastest shape (least
 // of its two times) is kept for the graph and used by every later job on it
 // with that lane width; the layer then runs once more in that shape, whose
@@ -852,8 +866,8 @@ static Status tune_layer(Job &j)
         float ms;
     };
     std::vector<Cand> cands;
-    for (u32 c : {64u, 128u, 256u})
-        for (u32 v = 0; v < (j.L == 32 ? 4u : ((j.L == 16 || j.L == 64) ? 3u : 1u)); v++)
+    for (u32 c : {64u, 128u, 256u, 512u, 1024u})
+        for (u32 v = 0; v < (j.L == 32 ? 4u : ((j.L == 16 || j.L == 64) ? 3u : (j.L == 128 ? 2u : 1u))); v++)
             if (!(j.L == 32 && (v == 1 || v == 2))) cands.push_back({c, v, 1e30f});
     const size_t nl = 2 * cands.size();
     std::vector<cudaEvent_t> ev(nl + 1, nullptr);
@@ -868,7 +882,7 @@ static Status tune_layer(Job &j)
             const Cand &c = cands[i % cands.size()];
             j.chunk = c.chunk;
             j.variant = c.variant;
-            j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
+            set_team_shape(j);
             TM_TRY(launch_layer_class(j.st, j.L, j.variant, job_layer_params(j), nullptr, nullptr, 0,
                                       j.n_chunks * j.lane_groups));
             TM_CUDA(cudaGetLastError());
@@ -897,7 +911,7 @@ static Status tune_layer(Job &j)
     }
     j.chunk = best->chunk;
     j.variant = best->variant;
-    j.n_chunks = (j.mf + j.chunk - 1) / j.chunk;
+    set_team_shape(j);
     std::vector<Job *> one{&j};
     DevBuf unused;
     return launch_layers(j.st, one, unused, nullptr, 0, j.prof);

@@ -147,12 +147,12 @@ def test_layer_shapes_give_identical_results(tm):
         assert tm.tmotif_get_layer_shape(G, L) is None
         tuned = tm.tmotif_decide(G, k, ms, seed=9)
         chunk, variant = tm.tmotif_get_layer_shape(G, L)
-        variants = (0, 3) if L == 32 else ((0, 1, 2) if L in (16, 64) else (0,))
-        assert chunk in (64, 128, 256) and variant in variants
-        if k == 4:
+        variants = (0, 3) if L == 32 else ((0, 1, 2) if L in (16, 64) else (0, 1))
+        assert chunk in (64, 128, 256, 512, 1024) and variant in variants
+        if k in (4, 7):
             ref = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, seed=9)
             assert_same(tuned, ref)
-        for c in (64, 128, 256):
+        for c in (64, 128, 256, 512, 1024):
             for v in variants:
                 tm.tmotif_set_layer_shape(G, L, c, v)
                 d = tm.tmotif_decide(G, k, ms, seed=9)
