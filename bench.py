@@ -98,10 +98,10 @@ def dist_env():
 
 
 def source_sha():
-    """Hash of the layer kernel's device code (its team body and the GF(2^64)
-    products it calls)."""
+    """Hash of the layer kernel's device code (its team body, the GF(2^64)
+    products it calls, and the kernels and launches around them)."""
     h = hashlib.sha256()
-    for f in ("layer.cuh", "gf64.cuh"):
+    for f in ("layer.cuh", "gf64.cuh", "sieve.cu"):
         h.update(open(os.path.join(ROOT, "paper_2001_07158_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -98,6 +98,7 @@ struct Workspace {
     DevBuf act, act_list;               // n+1 u32 active flags/offsets, n u32 active vertices
     DevBuf arc_sum;                     // m_f u64: arc-localised sieve sums
     DevBuf partial;                     // chunks * L u64: per-chunk sieve sums
+    DevBuf queue;                       // u64 team counter of the layer launches
     void *host_pinned = nullptr;        // small pinned readback area
     size_t host_pinned_bytes = 0;
     void release();
@@ -198,6 +199,9 @@ struct LayerParams {
     const u32 *jv = nullptr;
     const PackJob *pjobs = nullptr;
     u64 *pout = nullptr;
+    // single-job launches: team counter (zeroed before the launch) from which
+    // resident teams take the next team index; null: one team per team slot
+    unsigned long long *queue = nullptr;
 };
 
 // One decision in flight: its query, its device workspace and its progress

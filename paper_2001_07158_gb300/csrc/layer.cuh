@@ -152,7 +152,11 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
                     for (int i = 0; i < LPT; i++) v ^= gf_mul(xc[i], h[i]);
 #pragma unroll
                     for (int o = T / 2; o > 0; o >>= 1) v ^= __shfl_xor_sync(team_mask, v, o, T);
-                    if (tt == 0) p.arc_sum[base + j] ^= v;
+                    // with several lane groups, teams of other lanes add to the same arc
+                    if (tt == 0) {
+                        if (p.lane_groups > 1) atomicXor(&p.arc_sum[base + j], v);
+                        else p.arc_sum[base + j] ^= v;
+                    }
                 }
             }
             if (coj != NONE) {

@@ -325,8 +325,22 @@ __device__ __forceinline__ void layer_kernel(const LayerParams &one, const Layer
     u64 *tab = smem + (((2048u - (sa & 2047u)) & 2047u) >> 3) + (size_t)(threadIdx.x / T) * 256;
     const u64 team = (u64)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
     if (!MULTI) {
-        layer_team<T, TAB, LPT, false>(one, team, tab);
-        return;
+        if (!one.queue) {
+            layer_team<T, TAB, LPT, false>(one, team, tab);
+            return;
+        }
+        // resident teams take chunks in order from the counter until none is
+        // left, so chunks of uneven work (long in-segments) leave no tail of
+        // idle SMs
+        const u32 team_mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (((threadIdx.x & 31) / T) * T));
+        const u64 total = one.n_chunks * one.lane_groups;
+        for (;;) {
+            unsigned long long t = 0;
+            if (threadIdx.x % T == 0) t = atomicAdd(one.queue, 1ull);
+            t = __shfl_sync(team_mask, t, 0, T);
+            if (t >= total) return;
+            layer_team<T, TAB, LPT, false>(one, t, tab);
+        }
     }
     if (team >= team_prefix[njobs]) return;
     u32 lo = 0, hi = njobs;  // last job with team_prefix[job] <= team
@@ -626,6 +640,7 @@ Status job_prep(Job &j)
     TM_TRY(w.out.reserve(L * 8));
     TM_TRY(w.wtab.reserve((u64)q.k * L * 8));
     TM_TRY(w.partial.reserve(((j.mf + CHUNK_MIN - 1) / CHUNK_MIN) * L * 8));
+    TM_TRY(w.queue.reserve(sizeof(unsigned long long)));
     if (j.localize) {
         TM_TRY(w.arc_sum.reserve(j.mf * 8));
         TM_CUDA(cudaMemsetAsync(w.arc_sum.p, 0, j.mf * 8, st));
@@ -683,11 +698,26 @@ LayerParams job_layer_params(const Job &j)
     lp.start = j.q.start;
     lp.end = j.q.end;
     lp.T = j.T;
+    lp.queue = w.queue.as<unsigned long long>();
     return lp;
 }
 
 // One launch of the layer kernel.  MINB = 0: k_layer (single- or multi-job);
 // MINB > 0: k_layer_mb with that register bound (single-job only).
+// Streaming multiprocessors of the current device (cached per device).
+static int sm_count()
+{
+    static int counts[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!counts[dev]) {
+        int c = 0;
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) return 1;
+        counts[dev] = c;
+    }
+    return counts[dev];
+}
+
 template <int T, bool TAB, int LPT, int MINB>
 static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const LayerParams *jobs,
                              const u64 *prefix, u32 njobs, u64 teams)
@@ -706,12 +736,26 @@ static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const Laye
         }
     }
     if (!blocks) return Status();
+    unsigned grid = blocks;
+    if (one.queue && njobs == 0) {  // resident blocks only, fed from the team counter
+        static const int per_sm = [&] {
+            int nb = 0;
+            cudaError_t e;
+            if constexpr (MINB == 0)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_layer<T, TAB, false, LPT>, threads, smem);
+            else
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_layer_mb<T, TAB, LPT, MINB>, threads, smem);
+            return (e == cudaSuccess && nb > 0) ? nb : 1;
+        }();
+        grid = (unsigned)std::min<u64>(blocks, (u64)per_sm * sm_count());
+        TM_CUDA(cudaMemsetAsync(one.queue, 0, sizeof(unsigned long long), st));
+    }
     if constexpr (MINB == 0) {
-        if (njobs == 0) k_layer<T, TAB, false, LPT><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
+        if (njobs == 0) k_layer<T, TAB, false, LPT><<<grid, threads, smem, st>>>(one, jobs, prefix, njobs);
         else k_layer<T, TAB, true, LPT><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
     } else {
         if (njobs != 0) return fail(TMOTIF_ERR_UNSUPPORTED, "multi-job launches use the default kernel form");
-        k_layer_mb<T, TAB, LPT, MINB><<<blocks, threads, smem, st>>>(one);
+        k_layer_mb<T, TAB, LPT, MINB><<<grid, threads, smem, st>>>(one);
     }
     return Status();
 }
@@ -802,6 +846,7 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         for (size_t i = 0; i < cls.size(); i++) {
             hp[i] = job_layer_params(*cls[i]);
             hp[i].lane_groups = 1;  // multi-job launches use the default form of each class
+            hp[i].queue = nullptr;  // and one team per team slot
             hpre[i] = teams;
             teams += cls[i]->n_chunks;
             count_layer(prof, *cls[i], 1);

@@ -399,6 +399,30 @@ def test_vertex_localized_sieve_matches_oracle(tm):
         assert d.sieve_sum == int(np.bitwise_xor.reduce(want))
 
 
+def test_arc_localisation_in_every_layer_shape(tm):
+    # arc-localised sums (per-vertex Q_u, localised extraction) in every
+    # pinned launch shape at 64 and 128 lanes, including two 64-lane teams per
+    # chunk at 128 lanes, whose teams add to the same arcs
+    g = synth.powerlaw_graph(4000, 60000, 120, 5, seed=23)
+    cs, cd, ct = oracle.canon(g.n, g.src, g.dst, g.time)
+    for k, L, variants in ((6, 64, (0, 1, 2)), (7, 128, (0, 1))):
+        ms = [i % 5 for i in range(k)]
+        pb = oracle.Problem(g.n, cs, cd, ct, g.color, g.num_colors, k, ms)
+        arc = oracle.arc_sums(pb, oracle.query_seed(4, 0))
+        want = np.zeros(g.n, np.uint64)
+        np.bitwise_xor.at(want, cd.astype(np.int64), arc)
+        fo, vo, to = oracle.extract_localized(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, seed=4)
+        G = gpu_graph(tm, g)
+        for v in variants:
+            for c in (64, 256, 1024):
+                tm.tmotif_set_layer_shape(G, L, c, v)
+                d, pv = tm.tmotif_localize(G, k, ms, seed=4)
+                assert np.array_equal(pv, want), (L, c, v)
+                f, verts, times = tm.tmotif_extract(G, k, ms, seed=4)
+                assert f == fo and np.array_equal(verts, vo) and np.array_equal(times, to), (L, c, v)
+        G.close()
+
+
 # ---------------------------------------------------------------------------
 # EC-PathMotif (Sec. 7.3): the path's arc times are a given tuple T
 # ---------------------------------------------------------------------------
