@@ -107,6 +107,19 @@ Status DevBuf::reserve(size_t need)
     return Status();
 }
 
+int sm_count()
+{
+    static int counts[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!counts[dev]) {
+        int c = 0;
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) return 1;
+        counts[dev] = c;
+    }
+    return counts[dev];
+}
+
 void DevBuf::release()
 {
     dev_free(p, stream);

@@ -373,6 +373,8 @@ Status static_mask(Graph &g, const QuerySpec &q, const uint8_t *d_alive, uint8_t
 // validation, orientation, self-loop and duplicate removal, (dst, time, src)
 // order.
 Status build_graph_device(const tmotif_graph_desc *d, Graph *g);
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count();
 
 // Device GF multiply of host arrays (diagnostic).
 Status gf_mul_batch(const u64 *a, const u64 *b, u64 *out, u64 n);

@@ -155,8 +155,15 @@ __global__ void __launch_bounds__(256) k_pack_layer(LayerParams p)
     extern __shared__ __align__(16) u64 smem[];
     const u32 sa = (u32)__cvta_generic_to_shared(smem);
     u64 *tab = smem + (((2048u - (sa & 2047u)) & 2047u) >> 3) + (size_t)(threadIdx.x / 32) * 256;
-    const u64 team = (u64)blockIdx.x * 8 + threadIdx.x / 32;
-    layer_team<32, true, 2, true>(p, team, tab);
+    // resident warps take chunks in order from the counter (p.queue, zeroed
+    // before the launch): graphs of uneven size leave no tail of idle SMs
+    for (;;) {
+        unsigned long long t = 0;
+        if ((threadIdx.x & 31) == 0) t = atomicAdd(p.queue, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= p.n_chunks) return;
+        layer_team<32, true, 2, true>(p, t, tab);
+    }
 }
 
 struct PackBuffers {
@@ -164,13 +171,13 @@ struct PackBuffers {
     DevBuf P_src, P_dst, P_time, P_color, jv;
     DevBuf vflag, act, act_list, keep, f_src, f_dst, f_time, seg_lo, seg_hi, pos, mark, cp_in, cp_out;
     DevBuf g_src, g_dst, g_time;  // the other set of kept arcs (rounds alternate)
-    DevBuf wtab, x, C0, C1, out, block_sums, counters;
+    DevBuf wtab, x, C0, C1, out, block_sums, counters, queue;
     void set_stream(cudaStream_t s)
     {
         DevBuf *all[] = {&graphs, &queries, &jobs, &slot_begin, &slot_count, &P_src, &P_dst, &P_time, &P_color,
                          &jv, &vflag, &act, &act_list, &keep, &f_src, &f_dst, &f_time, &seg_lo, &seg_hi, &pos,
                          &mark, &cp_in, &cp_out, &g_src, &g_dst, &g_time, &wtab, &x, &C0, &C1, &out, &block_sums,
-                         &counters};
+                         &counters, &queue};
         for (DevBuf *b : all) b->stream = s;
     }
     void release()
@@ -178,7 +185,7 @@ struct PackBuffers {
         DevBuf *all[] = {&graphs, &queries, &jobs, &slot_begin, &slot_count, &P_src, &P_dst, &P_time, &P_color,
                          &jv, &vflag, &act, &act_list, &keep, &f_src, &f_dst, &f_time, &seg_lo, &seg_hi, &pos,
                          &mark, &cp_in, &cp_out, &g_src, &g_dst, &g_time, &wtab, &x, &C0, &C1, &out, &block_sums,
-                         &counters};
+                         &counters, &queue};
         for (DevBuf *b : all) b->release();
     }
 };
@@ -337,11 +344,20 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
             lp.pout = B.out.as<u64>();
             u64 *bufs[2] = {B.C0.as<u64>(), B.C1.as<u64>()};
             const size_t smem = 8 * 256 * 8 + 2048;  // 18 KB: within the default dynamic limit
+            TM_TRY(B.queue.reserve(sizeof(unsigned long long)));
+            lp.queue = B.queue.as<unsigned long long>();
+            static const int per_sm = [&] {
+                int nb = 0;
+                const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pack_layer, 256, smem);
+                return (e == cudaSuccess && nb > 0) ? nb : 1;
+            }();
+            const unsigned grid = (unsigned)std::min<u64>(blocks_of(lp.n_chunks, 8), (u64)per_sm * sm_count());
             for (u32 ell = 2; ell <= kmax; ell++) {
                 lp.ell = ell;
                 lp.Cin = bufs[ell & 1];
                 lp.Cout = bufs[(ell + 1) & 1];
-                k_pack_layer<<<blocks_of(lp.n_chunks, 8), 256, smem, st>>>(lp);
+                TM_CUDA(cudaMemsetAsync(lp.queue, 0, sizeof(unsigned long long), st));
+                k_pack_layer<<<grid, 256, smem, st>>>(lp);
                 TM_CUDA(cudaGetLastError());
                 (*launches)++;
             }

@@ -704,20 +704,6 @@ LayerParams job_layer_params(const Job &j)
 
 // One launch of the layer kernel.  MINB = 0: k_layer (single- or multi-job);
 // MINB > 0: k_layer_mb with that register bound (single-job only).
-// Streaming multiprocessors of the current device (cached per device).
-static int sm_count()
-{
-    static int counts[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (!counts[dev]) {
-        int c = 0;
-        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) return 1;
-        counts[dev] = c;
-    }
-    return counts[dev];
-}
-
 template <int T, bool TAB, int LPT, int MINB>
 static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const LayerParams *jobs,
                              const u64 *prefix, u32 njobs, u64 teams)
