@@ -222,7 +222,7 @@ public:
     u64 steps = 0;
 
 private:
-    static_assert(4096 * (sizeof(LayerParams) + 8) + 6 * 256 < (1 << 20), "job tables exceed a slot");
+    static_assert(4096 * (sizeof(LayerParams) + 8) + 6 * (256 + 16) < (1 << 20), "job tables exceed a slot");
     // one job-table slot (host pinned + device) per layer round between syncs
     static const int kMaxLayersPerSync = 8;
     static const size_t kSlotBytes = 1 << 20;

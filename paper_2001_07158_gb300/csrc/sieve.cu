@@ -324,32 +324,36 @@ __device__ __forceinline__ void layer_kernel(const LayerParams &one, const Layer
     const u32 sa = (u32)__cvta_generic_to_shared(smem);
     u64 *tab = smem + (((2048u - (sa & 2047u)) & 2047u) >> 3) + (size_t)(threadIdx.x / T) * 256;
     const u64 team = (u64)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
-    if (!MULTI) {
-        if (!one.queue) {
-            layer_team<T, TAB, LPT, false>(one, team, tab);
+    // one team per team slot ...
+    const u64 total = MULTI ? team_prefix[njobs] : one.n_chunks * one.lane_groups;
+    auto run = [&](u64 t) {
+        if (!MULTI) {
+            layer_team<T, TAB, LPT, false>(one, t, tab);
             return;
         }
-        // resident teams take chunks in order from the counter until none is
-        // left, so chunks of uneven work (long in-segments) leave no tail of
-        // idle SMs
-        const u32 team_mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (((threadIdx.x & 31) / T) * T));
-        const u64 total = one.n_chunks * one.lane_groups;
-        for (;;) {
-            unsigned long long t = 0;
-            if (threadIdx.x % T == 0) t = atomicAdd(one.queue, 1ull);
-            t = __shfl_sync(team_mask, t, 0, T);
-            if (t >= total) return;
-            layer_team<T, TAB, LPT, false>(one, t, tab);
+        u32 lo = 0, hi = njobs;  // last job with team_prefix[job] <= t
+        while (hi - lo > 1) {
+            const u32 mid = (lo + hi) >> 1;
+            if (team_prefix[mid] <= t) lo = mid;
+            else hi = mid;
         }
+        layer_team<T, TAB, LPT, false>(jobs[lo], t - team_prefix[lo], tab);
+    };
+    if (!one.queue) {
+        if (team < total) run(team);
+        return;
     }
-    if (team >= team_prefix[njobs]) return;
-    u32 lo = 0, hi = njobs;  // last job with team_prefix[job] <= team
-    while (hi - lo > 1) {
-        const u32 mid = (lo + hi) >> 1;
-        if (team_prefix[mid] <= team) lo = mid;
-        else hi = mid;
+    // ... or resident teams take team indices in order from the counter until
+    // none is left, so chunks of uneven work (long in-segments, small and
+    // large jobs) leave no tail of idle SMs
+    const u32 team_mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (((threadIdx.x & 31) / T) * T));
+    for (;;) {
+        unsigned long long t = 0;
+        if (threadIdx.x % T == 0) t = atomicAdd(one.queue, 1ull);
+        t = __shfl_sync(team_mask, t, 0, T);
+        if (t >= total) return;
+        run(t);
     }
-    layer_team<T, TAB, LPT, false>(jobs[lo], team - team_prefix[lo], tab);
 }
 
 // k_layer: the compiler's own register budget for 256-thread blocks;
@@ -723,22 +727,27 @@ static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const Laye
     }
     if (!blocks) return Status();
     unsigned grid = blocks;
-    if (one.queue && njobs == 0) {  // resident blocks only, fed from the team counter
-        static const int per_sm = [&] {
+    if (one.queue) {  // resident blocks only, fed from the team counter
+        auto resident = [&](const void *kernel) {
             int nb = 0;
-            cudaError_t e;
-            if constexpr (MINB == 0)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_layer<T, TAB, false, LPT>, threads, smem);
-            else
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_layer_mb<T, TAB, LPT, MINB>, threads, smem);
+            const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem);
             return (e == cudaSuccess && nb > 0) ? nb : 1;
-        }();
+        };
+        int per_sm = 1;
+        if constexpr (MINB == 0) {
+            static const int single = resident((const void *)k_layer<T, TAB, false, LPT>);
+            static const int multi = resident((const void *)k_layer<T, TAB, true, LPT>);
+            per_sm = njobs == 0 ? single : multi;
+        } else {
+            static const int mb = resident((const void *)k_layer_mb<T, TAB, LPT, MINB>);
+            per_sm = mb;
+        }
         grid = (unsigned)std::min<u64>(blocks, (u64)per_sm * sm_count());
         TM_CUDA(cudaMemsetAsync(one.queue, 0, sizeof(unsigned long long), st));
     }
     if constexpr (MINB == 0) {
         if (njobs == 0) k_layer<T, TAB, false, LPT><<<grid, threads, smem, st>>>(one, jobs, prefix, njobs);
-        else k_layer<T, TAB, true, LPT><<<blocks, threads, smem, st>>>(one, jobs, prefix, njobs);
+        else k_layer<T, TAB, true, LPT><<<grid, threads, smem, st>>>(one, jobs, prefix, njobs);
     } else {
         if (njobs != 0) return fail(TMOTIF_ERR_UNSUPPORTED, "multi-job launches use the default kernel form");
         k_layer_mb<T, TAB, LPT, MINB><<<grid, threads, smem, st>>>(one);
@@ -823,7 +832,8 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         for (const Job *j : jobs)
             if (j->L == Lc) cls.push_back(j);
         if (cls.empty()) continue;
-        const size_t need = cls.size() * sizeof(LayerParams) + (cls.size() + 1) * sizeof(u64);
+        // job table, team prefix, then the launch's team counter
+        const size_t need = cls.size() * sizeof(LayerParams) + (cls.size() + 2) * sizeof(u64);
         const size_t at = (off + 255) & ~(size_t)255;
         if (at + need > host_params_bytes) return fail(TMOTIF_ERR_UNSUPPORTED, "too many jobs in one layer launch");
         LayerParams *hp = (LayerParams *)((char *)host_params + at);
@@ -832,7 +842,7 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         for (size_t i = 0; i < cls.size(); i++) {
             hp[i] = job_layer_params(*cls[i]);
             hp[i].lane_groups = 1;  // multi-job launches use the default form of each class
-            hp[i].queue = nullptr;  // and one team per team slot
+            hp[i].queue = nullptr;
             hpre[i] = teams;
             teams += cls[i]->n_chunks;
             count_layer(prof, *cls[i], 1);
@@ -841,9 +851,11 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         TM_TRY(dev_params.reserve(host_params_bytes));
         char *dbase = (char *)dev_params.p + at;
         TM_CUDA(cudaMemcpyAsync(dbase, (char *)host_params + at, need, cudaMemcpyHostToDevice, st));
+        LayerParams head = hp[0];
+        head.queue = (unsigned long long *)(dbase + cls.size() * sizeof(LayerParams) + (cls.size() + 1) * sizeof(u64));
         cudaEvent_t la = nullptr;
         TM_TRY(prof->begin(st, &la));
-        TM_TRY(launch_layer_class(st, Lc, 0, hp[0], (const LayerParams *)dbase,
+        TM_TRY(launch_layer_class(st, Lc, 0, head, (const LayerParams *)dbase,
                                   (const u64 *)(dbase + cls.size() * sizeof(LayerParams)), (u32)cls.size(), teams));
         TM_CUDA(cudaGetLastError());
         TM_TRY(prof->end(st, la, FAM_LAYER));
