@@ -69,7 +69,7 @@ def layer_bound_s(reg, tab, builds):
 # layer-kernel sources it was taken on (source_sha() below, first 16 hex):
 # a timed-decision layer of the default workload, full size, one-pass dram
 # counters
-LAYER_TRAFFIC = {"source_sha": "d2fbaa5557b721c0", "bytes_per_launch": 1119535616 + 399804160}
+LAYER_TRAFFIC = {"source_sha": "04d6faf4ad63e994", "bytes_per_launch": 1124198144 + 399518208}
 
 
 def parse_args():
