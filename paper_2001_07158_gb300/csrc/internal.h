@@ -206,7 +206,7 @@ struct LayerParams {
 
 // One decision in flight: its query, its device workspace and its progress
 // through lane batches and layers.  tmotif_decide runs one job to the end;
-// the batch driver and the server advance many jobs together, one shared
+// the batch path and the server advance many jobs together, one shared
 // layer launch per step.
 struct Job {
     Graph *g = nullptr;

@@ -1,6 +1,6 @@
 """Batching and serving: every result is the same alone and in the mix.
 
-The batch driver and the request server advance many decisions together in
+The batch path and the request server advance many decisions together in
 shared layer launches (different graphs, k, seeds, layers); GF(2^64)
 arithmetic is exact, so each sieve sum, decision and extracted path must equal
 the one tmotif_decide / tmotif_extract give for the same query alone.
