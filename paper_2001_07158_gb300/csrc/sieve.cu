@@ -807,24 +807,28 @@ static void count_layer(Profiler *prof, const Job &j, u32 lane_groups)
     }
 }
 
+// One job's layer launch in its own (tuned or pinned) shape.
+static Status launch_one(cudaStream_t st, const Job &j, Profiler *prof)
+{
+    cudaEvent_t la = nullptr;
+    TM_TRY(prof->begin(st, &la));
+    TM_TRY(launch_layer_class(st, j.L, j.variant, job_layer_params(j), nullptr, nullptr, 0,
+                              j.n_chunks * j.lane_groups));
+    TM_CUDA(cudaGetLastError());
+    TM_TRY(prof->end(st, la, FAM_LAYER));
+    prof->stats.launches++;
+    prof->stats.layer_launches++;
+    count_layer(prof, j, j.lane_groups);
+    return Status();
+}
+
 Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &dev_params, void *host_params,
                      size_t host_params_bytes, Profiler *prof)
 {
     if (jobs.empty()) return Status();
-    if (jobs.size() == 1) {
-        const Job &j = *jobs[0];
-        cudaEvent_t la = nullptr;
-        TM_TRY(prof->begin(st, &la));
-        TM_TRY(launch_layer_class(st, j.L, j.variant, job_layer_params(j), nullptr, nullptr, 0,
-                                  j.n_chunks * j.lane_groups));
-        TM_CUDA(cudaGetLastError());
-        TM_TRY(prof->end(st, la, FAM_LAYER));
-        prof->stats.launches++;
-        prof->stats.layer_launches++;
-        count_layer(prof, j, j.lane_groups);
-        return Status();
-    }
-    // group by lane width; per class: job table + team prefix
+    if (jobs.size() == 1) return launch_one(st, *jobs[0], prof);
+    // group by lane width; per class: job table + team prefix.  A job alone
+    // in its class keeps its own launch shape.
     const u32 classes[6] = {4, 8, 16, 32, 64, 128};
     size_t off = 0;
     for (u32 Lc : classes) {
@@ -832,6 +836,10 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
         for (const Job *j : jobs)
             if (j->L == Lc) cls.push_back(j);
         if (cls.empty()) continue;
+        if (cls.size() == 1) {
+            TM_TRY(launch_one(st, *cls[0], prof));
+            continue;
+        }
         // job table, team prefix, then the launch's team counter
         const size_t need = cls.size() * sizeof(LayerParams) + (cls.size() + 2) * sizeof(u64);
         const size_t at = (off + 255) & ~(size_t)255;
