@@ -22,8 +22,11 @@ namespace tmo {
 // (p.jv); y uses the job's key and the graph's own vertex ids; the job's own
 // k decides whether this layer is past its end (segment skipped), its last
 // (segment sums XORed into the job's lane sums p.pout) or an inner layer.
+//
+// INNER: the caller guarantees 2 < l < k (single job), so the form for the
+// first and the last layer (source rows from x, segment sums) compiles out.
 // ---------------------------------------------------------------------------
-template <int T, bool TAB, int LPT, bool PACKED>
+template <int T, bool TAB, int LPT, bool PACKED, bool INNER = false>
 __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *tab)
 {
     const int tt = threadIdx.x % T;
@@ -32,7 +35,7 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
     if (chunk >= p.n_chunks) return;
     const u32 lane0 = (u32)(team % p.lane_groups) * (LPT * T) + LPT * tt;
     const u64 Lw = p.L;
-    const bool last = !PACKED && (p.ell == p.k);
+    const bool last = !PACKED && !INNER && (p.ell == p.k);
     u64 q[LPT], xc[LPT], acc[LPT];
 #pragma unroll
     for (int i = 0; i < LPT; i++) q[i] = xc[i] = acc[i] = 0;
@@ -71,20 +74,20 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
             s = p.src[e];
             d = p.dst[e];
             const u32 t = p.time[e];
-            if (p.ell > 2) ci = p.cp_in[e];
+            if (INNER || p.ell > 2) ci = p.cp_in[e];
             if (PACKED) {
                 const PackJob &J = p.pjobs[p.jv[d]];
                 if (p.ell < J.k) co = p.cp_out[e];
                 if (p.ell <= J.k) y = coef_y(mix64(J.ky ^ (((u64)(s - J.vbase) << 32) | (d - J.vbase))), t, p.ell - 1);
             } else {
-                if (!last) co = p.cp_out[e];
+                if (INNER || !last) co = p.cp_out[e];
                 y = coef_y(mix64(p.ky ^ (((u64)s << 32) | d)), t, p.ell - 1);
             }
         }
         const int cnt = (int)min((u64)T, stop - base);
         for (int j = 0; j < cnt; j++) {
             const u32 dj = __shfl_sync(team_mask, d, j, T);
-            const u32 sj = __shfl_sync(team_mask, s, j, T);
+            const u32 sj = INNER ? 0u : __shfl_sync(team_mask, s, j, T);
             const u32 cij = __shfl_sync(team_mask, ci, j, T);
             const u32 coj = __shfl_sync(team_mask, co, j, T);
             const u64 yj = __shfl_sync(team_mask, y, j, T);
@@ -116,7 +119,7 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
             }
             if (PACKED && !seg_live) continue;  // past this job's last layer (uniform in the team)
             const u64 *row = nullptr;
-            if (p.ell == 2) {
+            if (!INNER && p.ell == 2) {
                 if (seg_start == NONE || sj == seg_start) row = p.x + (u64)sj * Lw + lane0;
             } else if (cij != NONE) {
                 row = p.Cin + (u64)cij * Lw + lane0;

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L,
 // Layer kernel: eq. (gen-polynomial:3), one walk length per job per launch.
 // MULTI = false: the single job in `one` (read from parameter space);
 // MULTI = true: the team's job is found in the prefix of team counts.
-template <int T, bool TAB, bool MULTI, int LPT>
+template <int T, bool TAB, bool MULTI, int LPT, bool INNER>
 __device__ __forceinline__ void layer_kernel(const LayerParams &one, const LayerParams *__restrict__ jobs,
                                              const u64 *__restrict__ team_prefix, u32 njobs)
 {
@@ -328,7 +328,7 @@ __device__ __forceinline__ void layer_kernel(const LayerParams &one, const Layer
     const u64 total = MULTI ? team_prefix[njobs] : one.n_chunks * one.lane_groups;
     auto run = [&](u64 t) {
         if (!MULTI) {
-            layer_team<T, TAB, LPT, false>(one, t, tab);
+            layer_team<T, TAB, LPT, false, INNER>(one, t, tab);
             return;
         }
         u32 lo = 0, hi = njobs;  // last job with team_prefix[job] <= t
@@ -359,18 +359,19 @@ __device__ __forceinline__ void layer_kernel(const LayerParams &one, const Layer
 // k_layer: the compiler's own register budget for 256-thread blocks;
 // k_layer_mb: the blocks of 256 threads per SM the allocation must allow
 // (2: up to 128 registers per thread, 4: 64).  These are the register shapes
-// the autotuner picks from.
-template <int T, bool TAB, bool MULTI, int LPT>
+// the autotuner picks from.  INNER (single job, 2 < l < k): the form without
+// the first and last layers' cases.
+template <int T, bool TAB, bool MULTI, int LPT, bool INNER = false>
 __global__ void __launch_bounds__(256) k_layer(LayerParams one, const LayerParams *__restrict__ jobs,
                                                const u64 *__restrict__ team_prefix, u32 njobs)
 {
-    layer_kernel<T, TAB, MULTI, LPT>(one, jobs, team_prefix, njobs);
+    layer_kernel<T, TAB, MULTI, LPT, INNER>(one, jobs, team_prefix, njobs);
 }
 
-template <int T, bool TAB, int LPT, int MINB>
+template <int T, bool TAB, int LPT, int MINB, bool INNER = false>
 __global__ void __launch_bounds__(256, MINB) k_layer_mb(LayerParams one)
 {
-    layer_kernel<T, TAB, false, LPT>(one, nullptr, nullptr, 0);
+    layer_kernel<T, TAB, false, LPT, INNER>(one, nullptr, nullptr, 0);
 }
 
 // out[lane] = XOR over chunks of partial[chunk * L + lane]; blockDim.x = L,
@@ -708,8 +709,8 @@ LayerParams job_layer_params(const Job &j)
 
 // One launch of the layer kernel.  MINB = 0: k_layer (single- or multi-job);
 // MINB > 0: k_layer_mb with that register bound (single-job only).
-template <int T, bool TAB, int LPT, int MINB>
-static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const LayerParams *jobs,
+template <int T, bool TAB, int LPT, int MINB, bool INNER>
+static Status launch_layer_f(cudaStream_t st, const LayerParams &one, const LayerParams *jobs,
                              const u64 *prefix, u32 njobs, u64 teams)
 {
     const int threads = 256;
@@ -718,11 +719,11 @@ static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const Laye
     const size_t smem = TAB ? teams_per_block * 256 * 8 + 2048 : 16;
     if (smem > 48 * 1024) {  // above the default limit: opt in (per call, so per device and thread-safe)
         if constexpr (MINB == 0) {
-            TM_CUDA(cudaFuncSetAttribute(njobs == 0 ? k_layer<T, TAB, false, LPT> : k_layer<T, TAB, true, LPT>,
+            TM_CUDA(cudaFuncSetAttribute(njobs == 0 ? k_layer<T, TAB, false, LPT, INNER> : k_layer<T, TAB, true, LPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         } else {
-            TM_CUDA(cudaFuncSetAttribute(k_layer_mb<T, TAB, LPT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+            TM_CUDA(cudaFuncSetAttribute(k_layer_mb<T, TAB, LPT, MINB, INNER>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         }
     }
     if (!blocks) return Status();
@@ -735,24 +736,34 @@ static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const Laye
         };
         int per_sm = 1;
         if constexpr (MINB == 0) {
-            static const int single = resident((const void *)k_layer<T, TAB, false, LPT>);
+            static const int single = resident((const void *)k_layer<T, TAB, false, LPT, INNER>);
             static const int multi = resident((const void *)k_layer<T, TAB, true, LPT>);
             per_sm = njobs == 0 ? single : multi;
         } else {
-            static const int mb = resident((const void *)k_layer_mb<T, TAB, LPT, MINB>);
+            static const int mb = resident((const void *)k_layer_mb<T, TAB, LPT, MINB, INNER>);
             per_sm = mb;
         }
         grid = (unsigned)std::min<u64>(blocks, (u64)per_sm * sm_count());
         TM_CUDA(cudaMemsetAsync(one.queue, 0, sizeof(unsigned long long), st));
     }
     if constexpr (MINB == 0) {
-        if (njobs == 0) k_layer<T, TAB, false, LPT><<<grid, threads, smem, st>>>(one, jobs, prefix, njobs);
+        if (njobs == 0) k_layer<T, TAB, false, LPT, INNER><<<grid, threads, smem, st>>>(one, jobs, prefix, njobs);
         else k_layer<T, TAB, true, LPT><<<grid, threads, smem, st>>>(one, jobs, prefix, njobs);
     } else {
         if (njobs != 0) return fail(TMOTIF_ERR_UNSUPPORTED, "multi-job launches use the default kernel form");
-        k_layer_mb<T, TAB, LPT, MINB><<<grid, threads, smem, st>>>(one);
+        k_layer_mb<T, TAB, LPT, MINB, INNER><<<grid, threads, smem, st>>>(one);
     }
     return Status();
+}
+
+// Single-job launches of inner layers (2 < l < k) take the INNER form.
+template <int T, bool TAB, int LPT, int MINB>
+static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const LayerParams *jobs,
+                             const u64 *prefix, u32 njobs, u64 teams)
+{
+    if (njobs == 0 && one.ell > 2 && one.ell < one.k)
+        return launch_layer_f<T, TAB, LPT, MINB, true>(st, one, jobs, prefix, njobs, teams);
+    return launch_layer_f<T, TAB, LPT, MINB, false>(st, one, jobs, prefix, njobs, teams);
 }
 
 // One kernel form per lane width L (the launch class): L = T * LPT.  The
