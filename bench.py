@@ -69,7 +69,7 @@ def layer_bound_s(reg, tab, builds):
 # layer-kernel sources it was taken on (source_sha() below, first 16 hex):
 # a timed-decision layer of the default workload, full size, one-pass dram
 # counters
-LAYER_TRAFFIC = {"source_sha": "04d6faf4ad63e994", "bytes_per_launch": 1124198144 + 399518208}
+LAYER_TRAFFIC = {"source_sha": "75c023988ddff50f", "bytes_per_launch": 1125220352 + 399725824}
 
 
 def parse_args():
