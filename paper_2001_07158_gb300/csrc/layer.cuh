@@ -10,7 +10,9 @@ namespace tmo {
 // ---------------------------------------------------------------------------
 // A team of T threads owns T * LPT consecutive lanes (LPT = 1, 2 or 4 lanes,
 // 8, 16 or 32 bytes, per thread) of one job and walks one chunk of whole
-// in-segments in arc order.  Segments are never split, so a running XOR is
+// in-segments in arc order: team index = chunk * lane_groups + lane group.
+// A resident team calls this once for every team index it takes from its
+// launch's counter.  Segments are never split, so a running XOR is
 // the prefix of eq. (3)'s stay term.  With TAB the team builds, per arc, the
 // nibble table of y_{e,l-1} in shared memory and every lane's y-product is 16
 // table loads; x-products (one per checkpoint and per segment at the last
