@@ -1,0 +1,77 @@
+"""Host-side parts of the benchmark (CPU only): the reference arm's JSON line,
+rank handling under a launcher, the speed-of-light model and the source hash
+that guards the committed DRAM traffic figure."""
+import json
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _run(args, env_extra=None):
+    env = dict(os.environ)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    env.pop("LOCAL_RANK", None)
+    if env_extra:
+        env.update(env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                          env=env, cwd=ROOT, timeout=600)
+
+
+def test_reference_arm_line():
+    r = _run(["--impl", "reference", "--scale", "0.01", "--steps", "1", "--warmup", "0"])
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    r = _run(["--impl", "reference", "--scale", "0.01", "--steps", "1", "--warmup", "0"],
+             {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_speed_of_light_model():
+    # the bound is the slowest pipe; each pipe time scales with its work
+    t, pipes = bench.layer_bound_s(reg=1e6, tab=1e8, builds=1e6)
+    assert t == max(pipes.values()) and all(v > 0 for v in pipes.values())
+    t2, pipes2 = bench.layer_bound_s(reg=2e6, tab=2e8, builds=2e6)
+    for k in pipes:
+        assert pipes2[k] == pytest.approx(2 * pipes[k])
+    # table products alone: shared memory at 1 wavefront per product and SM clock
+    _, only_tab = bench.layer_bound_s(reg=0, tab=bench.SMS * bench.SM_HZ, builds=0)
+    assert only_tab["smem"] == pytest.approx(1.0)
+    assert only_tab["fma"] == 0
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    src = os.path.join(ROOT, "paper_2001_07158_gb300", "csrc")
+    dst = tmp_path / "paper_2001_07158_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in ("layer.cuh", "gf64.cuh", "sieve.cu"):
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    base = bench.source_sha()
+    assert base == bench.source_sha()
+    p = dst / "layer.cuh"
+    text = p.read_text()
+    p.write_text("// an added comment line\n" + text.replace("namespace tmo {", "namespace tmo {  /* note */", 1))
+    assert bench.source_sha() == base
+    p.write_text(text.replace("namespace tmo {", "namespace tmo {\nstatic const int added_code = 1;", 1))
+    assert bench.source_sha() != base
