@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Benchmark of the temporal path-motif sieve on one GB300 (or N replicas).
 
-Workload: the mid-size decision of the benchmark suite -- a power-law
+Headline workload: the mid-size decision of the benchmark suite -- a power-law
 out-degree temporal graph (exponent 2.1, n = 10^6, m = 10^7 edges, timestamps
 uniform in [1, 1000], 16 colours Zipf(1.0)) with a k = 6 multiset query (one
 colour twice), 2^6 = 64 sieve points, exact GF(2^64) arithmetic.  A step is one
@@ -10,12 +10,25 @@ build, sieve coefficients, the k-1 generating-function layers, the sieve sum.
 
 Metric: edge-steps/s = m * k * 2^k / (time of one decision).
 
+On one GPU the same JSON line also carries the other workloads of the suite,
+each measured after the headline's timed region:
+  large10  the large-sieve decision n = 10^7, m = 10^8, k = 10 (1024 points);
+  batch    10,000 small tour graphs in one batched call, against one
+           tmotif_decide per graph, both timed by CUDA events on the stream;
+  serving  4,096 requests (k in 3..10, 30 % extract) against a resident
+           n = 2*10^6, m = 2*10^7 graph, Poisson arrivals at 70 % of the plain
+           form's capacity: the plain form (one request at a time, in arrival
+           order) and the server, both live, plus both forms saturated;
+  cpu_baseline  the oracle on every host core, on a sample of the points.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--legs large10,batch,serving,cpu] [--workload ...]
 
 With N > 1 it runs under torchrun, one rank per GPU; every rank decides its own
 query (another seed) on its own replica of the graph -- the sieve points of
 different queries are independent, so there is no data-path collective
-("weak" scaling); ranks meet only at the timing barrier.
+("weak" scaling); ranks meet only at the timing barrier.  The extra workloads
+run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -38,32 +51,51 @@ UNIT = "edge-steps/s"
 WORKLOAD = ("power-law out-degree 2.1, n=1e6, m=1e7 (+50 planted arcs), t in [1,1000], 16 colours Zipf(1.0); "
             "PathMotif k=6 with one colour twice, 64 sieve points, GF(2^64)")
 
-# Speed of light of the layer kernel, from GB300 unit counts at the maximum SM
-# clock (152 SMs, 2070 MHz) and per-product costs measured by ncu on the
-# library's register-resident probe (tmotif_gf_probe methods 0-2).  A launch's
-# lower-bound time is the largest of three pipe times for its work:
-#   shared memory, 1 wavefront (128 B) per clock per SM: a table product
-#     reads 16 eight-byte entries (1 wavefront); a table build writes 2 KB
-#     (16 wavefronts);
-#   ALU pipe, 64 lanes per clock per SM: 39.6 ALU instructions per table
-#     product plus 1059 per table build (fitted to the probe at 64 and 128
-#     lanes per table: 56.1 and 47.8 per product), 92.6 per register product
-#     (probe counts less about 3-4 of probe loop work);
-#   FMA pipe: 9.28 sub-partition cycles per register product (4 per SM).
-SMS = 152
-SM_HZ = 2.070e9
-ALU_PER_REG, ALU_PER_TAB, ALU_PER_BUILD = 92.6, 39.6, 1059.0
-WF_PER_TAB, WF_PER_BUILD = 1.0, 16.0
-FMA_CYC_PER_REG = 9.28
+# The paper's own figures (Sec. 10, Table 4 and the headline extraction), on
+# its own hardware: context beside the line, not a target for this workload.
+PAPER = {
+    "decision": {"figure_s": 109.04, "workload": "d-regular d=200, m=10,000,070, t=100, k=8 (256 points), "
+                 "4 threads", "edge_steps_per_s": 10_000_070 * 8 * 256 / 109.04,
+                 "hardware": "Intel Core i5-4570 (Haswell), 3.2 GHz, 4 cores", "cite": "Sec. 10, Table 4"},
+    "extraction": {"figure_s": 444.66, "workload": "optimum solution, Helsinki transport graph, n=7,959, "
+                   "m=6,403,785, t=1,440, k=10", "hardware": "Intel Core i5-4570 (Haswell), 3.2 GHz, 4 cores",
+                   "cite": "abstract and Sec. 10"},
+}
 
 
-def layer_bound_s(reg, tab, builds):
+def table_costs(rates):
+    """Seconds of GPU time per unit of layer work, from the product rates of
+    the register-resident probe (tmotif_gf_probe): `reg` a register product;
+    `lookup` one lane's table product and `build` one shared table, solved from
+    the table form's rates at 64 and 128 lanes per table
+    (1/R64 = build/64 + lookup, 1/R128 = build/128 + lookup)."""
+    inv64, inv128 = 1.0 / rates["table64"], 1.0 / rates["table128"]
+    build = max(128.0 * (inv64 - inv128), 0.0)
+    lookup = max(inv128 - build / 128.0, 0.0)
+    return {"reg": 1.0 / rates["reg"], "lookup": lookup, "build": build}
+
+
+def layer_bound_s(costs, reg, tab, builds):
     """Lower-bound seconds of one layer launch with `reg` register products,
-    `tab` table products and `builds` table builds."""
-    t_smem = (tab * WF_PER_TAB + builds * WF_PER_BUILD) / (SMS * SM_HZ)
-    t_alu = (reg * ALU_PER_REG + tab * ALU_PER_TAB + builds * ALU_PER_BUILD) / (SMS * 64 * SM_HZ)
-    t_fma = reg * FMA_CYC_PER_REG / (SMS * 4 * SM_HZ)
-    return max(t_smem, t_alu, t_fma), {"smem": t_smem, "alu": t_alu, "fma": t_fma}
+    `tab` table products and `builds` table builds: each product form needs
+    at least the time the GPU takes for that form's work alone, at the
+    probe's measured rate, so the bound is the larger of the two."""
+    t_tab = tab * costs["lookup"] + builds * costs["build"]
+    t_reg = reg * costs["reg"]
+    return max(t_tab, t_reg), {"table": t_tab, "register": t_reg}
+
+
+def probe_rates(tm, iters=2048, repeats=3):
+    """GF(2^64) products per second of each product form on this GPU, on
+    register-resident data with no memory traffic (best of `repeats`)."""
+    rates = {}
+    for name, method in (("reg", 0), ("table64", 1), ("table128", 2)):
+        best = 0.0
+        for _ in range(repeats):
+            ms, n = tm.tmotif_gf_probe(method, iters)
+            best = max(best, n / (ms / 1e3))
+        rates[name] = best
+    return rates
 
 
 # DRAM traffic of one layer launch from an ncu capture, valid only for the
@@ -73,16 +105,19 @@ def layer_bound_s(reg, tab, builds):
 LAYER_TRAFFIC = {"source_sha": "d47a2aedf1086717", "bytes_per_launch": 1125220352 + 399725824}
 
 
-def parse_args():
+def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--legs", default="large10,batch,serving,cpu",
+                   help="extra workloads measured after the headline at N = 1 (comma list of large10, batch, "
+                        "serving, cpu; empty for none)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
-    p.add_argument("--serving-requests", type=int, default=256)
+    p.add_argument("--serving-requests", type=int, default=4096)
     p.add_argument("--scale", type=float, default=1.0,
                    help="scale n and m of the workload (profiling captures of a smaller case)")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="mid",
@@ -90,7 +125,16 @@ def parse_args():
                         "n=1e7 with m=5e8, k=5 / m=1e8, k=10; batch: 10,000 small tour graphs in one "
                         "batched call (k in 5..8); transit: a timetable graph for --preprocess")
     p.add_argument("--preprocess", action="store_true", help="static preprocessing sieve before each decision")
-    return p.parse_args()
+    return p.parse_args(argv)
+
+
+def legs_of(args):
+    legs = {x.strip() for x in args.legs.split(",") if x.strip()}
+    if args.no_cpu_baseline:
+        legs.discard("cpu")
+    if args.no_serving:
+        legs.discard("serving")
+    return legs
 
 
 def dist_env():
@@ -190,152 +234,348 @@ def workload(scale=1.0, name="mid"):
     return synth.config2_mid(n=int(1_000_000 * scale), m=int(10_000_000 * scale))
 
 
-def cpu_baseline(g, q, points=None):
-    """The oracle as it stands (plain C, OpenMP over sieve points) on the host
-    cores, on a bounded sample of the same decision: `points` of the 64 sieve
-    points (one point per thread)."""
+def cpu_baseline(g, q):
+    """The oracle as it stands (plain C, OpenMP over sieve points) on every
+    host core, on a bounded sample of the same decision: the first P of its
+    2^k sieve points, P = the host's core count (one point per thread)."""
     import oracle
 
     cores = os.cpu_count() or 1
-    P = points or max(1, min(cores, 16))
+    P = max(1, min(cores, 1 << q.k))
     t0 = time.perf_counter()
     oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed, point_begin=0,
-                  point_end=P, nthreads=min(P, cores))
+                  point_end=P, nthreads=P)
     dt = time.perf_counter() - t0
-    return {"value": g.m * q.k * P / dt, "unit": UNIT, "cores": min(P, cores), "kind": "oracle",
-            "sample": f"{P} of the {1 << q.k} sieve points of the same decision ({dt:.1f} s)"}
+    return {"value": g.m * q.k * P / dt, "unit": UNIT, "cores": P, "nproc": cores, "kind": "oracle",
+            "sample": f"points [0, {P}) of the {1 << q.k} sieve points of the same decision, one per host core "
+                      f"({dt:.1f} s)"}
 
 
-def serving_benchmark(tm, stream, requests=128, load=0.7, seed=8):
+def measure_decision(tm, stream, dev, G, q, steps, warmup, seed, preprocess=False, world=1):
+    """Time `steps` decisions of query q on the resident graph G (after
+    `warmup` untimed ones), L2 flushed between steps, with the library's layer
+    statistics on; returns (total ms, per-step results, stats, clocks)."""
+    import torch
+
+    for i in range(warmup):
+        tm.tmotif_decide(G, q.k, q.multiset, seed=seed + i, preprocess=preprocess, per_point=False)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    sampler = ClockSampler(uuid)
+    tm.tmotif_set_profiling(G, True)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    found = []
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            starts[i].record(stream)
+        d = tm.tmotif_decide(G, q.k, q.multiset, seed=seed + 1000 + i, per_point=False, preprocess=preprocess)
+        ends[i].record(stream)
+        found.append(d.found)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    stats = tm.tmotif_get_stats(G)
+    tm.tmotif_set_profiling(G, False)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    del flush
+    return total_ms, found, stats, clocks
+
+
+def roofline_of(stats, total_ms, costs, rates, traffic):
+    """Roofline of the dominant kernel (the layer kernel), from the library's
+    CUDA events around every layer launch during the timed region: achieved
+    GF(2^64) products per second against the rate at which this GPU does the
+    same products with no memory traffic (the larger of the launch's
+    table-form and register-form times at the probe's measured rates)."""
+    nl = max(stats["layer_launches"], 1)
+    layer_ms = stats["layer_ms"] / nl
+    muls = stats["layer_gf_muls"] / nl
+    tmuls = stats["layer_table_muls"] / nl
+    builds = stats["layer_table_builds"] / nl
+    t_min, forms = layer_bound_s(costs, muls - tmuls, tmuls, builds)
+    achieved = muls / (layer_ms / 1e3) / 1e9
+    peak = muls / t_min / 1e9 if t_min > 0 else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G GF(2^64) products/s",
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "kernel": "k_layer (eq. gen-polynomial:3 layer)",
+            "model": "product rates measured at bench start by tmotif_gf_probe (register-resident, no memory "
+                     "traffic); bound = max(table-form time, register-form time); binding form: "
+                     + max(forms, key=forms.get),
+            "probe_products_per_s": rates, "form_ms": {k: v * 1e3 for k, v in forms.items()},
+            "layer_ms_per_launch": layer_ms, "gf_muls_per_launch": muls, "table_muls_per_launch": tmuls,
+            "table_builds_per_launch": builds, "algorithmic_bytes_per_launch": stats["layer_bytes"] / nl,
+            "achieved_hbm_gbs": stats["layer_bytes"] / nl / (layer_ms / 1e3) / 1e9,
+            "layer_share_of_step": stats["layer_ms"] / total_ms if total_ms else None}
+
+
+def e2e_decision(tm, stream, g, q, seed, steps, preprocess=False):
+    """End to end through the C ABI with host buffers: upload and build the
+    graph from pinned host arrays, decide, read the result back, release;
+    mean seconds per step."""
+    import numpy as np
+    import torch
+
+    pin = {}
+    for name in ("src", "dst", "time"):
+        a = getattr(g, name)
+        tpin = torch.empty(len(a), dtype=torch.int32, pin_memory=True)
+        tpin.numpy().view(np.uint32)[:] = a
+        pin[name] = tpin
+    cpin = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+    cpin.numpy().view(np.uint32)[:] = g.color
+    times = []
+    for i in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = tm.tmotif_create_graph(g.n, pin["src"].numpy().view(np.uint32), pin["dst"].numpy().view(np.uint32),
+                                    pin["time"].numpy().view(np.uint32), cpin.numpy().view(np.uint32),
+                                    g.num_colors, stream=stream)
+        tm.tmotif_decide(G2, q.k, q.multiset, seed=seed + 5000 + i, preprocess=preprocess)
+        G2.close()
+        times.append(time.perf_counter() - t0)
+    return statistics.mean(times) if times else float("nan")
+
+
+def large10_leg(tm, stream, dev, costs, rates, steps, warmup):
+    """The large-sieve decision at k = 10 (n = 10^7, m = 10^8, 1024 points in
+    lane batches of 128): its own timed steps and layer roofline."""
+    g, q = workload(1.0, "large10")
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
+    total_ms, found, stats, clocks = measure_decision(tm, stream, dev, G, q, steps, warmup, q.seed)
+    G.close()
+    e2e_s = e2e_decision(tm, stream, g, q, q.seed, 1)
+    work = g.m * q.k * (1 << q.k)
+    ms = total_ms / steps
+    return {"workload": WORKLOADS["large10"], "n": g.n, "m": g.m, "k": int(q.k), "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "value": work / (ms / 1e3), "unit": UNIT, "found_all": all(found),
+            "clocks": clocks, "roofline": roofline_of(stats, total_ms, costs, rates, None),
+            "e2e": {"ms_per_step": e2e_s * 1e3, "value": work / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 12 * g.m + 4 * g.n + 4 * q.k, "d2h_bytes_per_step": 8 * (1 << q.k) + 16},
+            "gpu_launches": int(stats["launches"])}
+
+
+def batch_leg(tm, stream, dev, steps, warmup, count=10_000, seed=4):
+    """10,000 small tour graphs: a step is one tmotif_decide_batch call over
+    all of them (graphs resident).  The plain form, one tmotif_decide per
+    graph back to back, is timed the same way: CUDA events on the shared
+    stream around the whole pass."""
+    import torch
+
+    import synth
+
+    items = synth.config3_batch(num_graphs=count, seed=seed)
+    graphs = [tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
+              for g, _ in items]
+    queries = [{"k": q.k, "multiset": q.multiset, "seed": q.seed} for _, q in items]
+    work = sum(int(g.m) * q.k * (1 << q.k) for g, q in items)
+    arcs = sum(int(g.m) for g, _ in items)
+    del items
+    for _ in range(warmup):
+        tm.tmotif_decide_batch(graphs, queries)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    sampler = ClockSampler("")
+    sampler.start()
+    total_ms = 0.0
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = tm.tmotif_decide_batch(graphs, queries)
+        b.record(stream)
+        torch.cuda.synchronize()
+        total_ms += a.elapsed_time(b)
+    clocks = sampler.stop()
+    with torch.cuda.stream(stream):
+        flush.fill_(0x5A)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plain = [tm.tmotif_decide(G, **q) for G, q in zip(graphs, queries)]
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b)
+    import numpy as np
+
+    same = all(p.found == r.found and np.array_equal(p.per_point, r.per_point) for p, r in zip(plain, res))
+    for G in graphs:
+        G.close()
+    ms = total_ms / steps
+    return {"workload": WORKLOADS["batch"], "graphs": count, "arcs": arcs, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "value": work / (ms / 1e3), "unit": UNIT, "found": sum(r.found for r in res),
+            "clocks": clocks, "timing": "CUDA events on the shared stream around each call (batch) and around "
+                                        "the whole pass (plain); L2 flushed before each",
+            "plain": {"ms_per_step": plain_ms, "value": work / (plain_ms / 1e3), "results_match": bool(same),
+                      "form": "one tmotif_decide per graph, back to back"},
+            "speedup_over_plain": plain_ms / ms}
+
+
+def serving_benchmark(tm, stream, requests=4096, load=0.7, seed=8, sample=256):
     """Config-5 serving: a stream of decide/extract requests (k in [3,10], 30 %
     extract) against one resident power-law graph (n=2e6, m=2e7, 16 colours).
 
-    plain: requests one at a time, one query per launch sequence (FIFO);
-    their measured service times set the Poisson arrival rate at `load` of
-    the plain form's capacity and give its latencies by replaying the queue.
-    served: the same arrival schedule submitted to the continuous-batching
-    server (tmotif_submit / tmotif_poll), timed live.  Every served result
-    is checked against the plain one."""
+    1. capacity: a seeded sample of the stream, one request at a time, sets
+       the Poisson arrival rate at `load` of the plain form's capacity;
+    2. plain, live: the requests one at a time in arrival order, each call
+       waiting for its arrival (one query per launch sequence);
+    3. served, live: the same arrival schedule submitted to the
+       continuous-batching server (tmotif_submit / tmotif_poll);
+    4. saturated: every request submitted to the server at once; the plain
+       form's saturated rate is the requests over the sum of their service
+       times in step 2 (back to back, a FIFO queue never idles).
+    Every served result is checked against the plain one, point by point for
+    decisions and path by path for extractions."""
     import numpy as np
 
     import synth
 
     g, reqs = synth.config5_serving(requests=requests, seed=7)
     G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
-    warm = reqs[0][0]
-    tm.tmotif_decide(G, warm.k, warm.multiset, seed=warm.seed)
-    plain_res, service = [], []
-    for q, ex in reqs:
-        t0 = time.perf_counter()
+    for q, _ in reqs[:64]:  # tune the launch shapes of every lane width once
+        tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed, per_point=False)
+
+    def run_plain(q, ex):
         if ex:
             f, v, t = tm.tmotif_extract(G, q.k, q.multiset, seed=q.seed)
-            plain_res.append((f, None, v.tolist(), t.tolist()))
-        else:
-            d = tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed, per_point=False)
-            plain_res.append((d.found, d.sieve_sum, None, None))
-        service.append(time.perf_counter() - t0)
-    capacity = len(reqs) / sum(service)
-    rate = load * capacity
+            return (f, None, v.tolist(), t.tolist())
+        d = tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed)
+        return (d.found, d.per_point.copy(), None, None)
+
     rng = np.random.default_rng(seed)
+    idx = rng.choice(len(reqs), min(sample, len(reqs)), replace=False)
+    t0 = time.perf_counter()
+    for i in idx:
+        run_plain(*reqs[i])
+    capacity_est = len(idx) / (time.perf_counter() - t0)
+    rate = load * capacity_est
     arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
     arrivals -= arrivals[0]
-    done_plain, t_free = [], 0.0
-    for a, s_ in zip(arrivals, service):
-        t_free = max(a, t_free) + s_
-        done_plain.append(t_free)
+
+    # plain, live
+    plain_res, service, done_plain = [], [], []
+    t_start = time.perf_counter()
+    for a, (q, ex) in zip(arrivals, reqs):
+        wait = a - (time.perf_counter() - t_start)
+        if wait > 0:
+            time.sleep(wait)
+        s0 = time.perf_counter()
+        plain_res.append(run_plain(q, ex))
+        s1 = time.perf_counter()
+        service.append(s1 - s0)
+        done_plain.append(s1 - t_start)
     lat_plain = np.array(done_plain) - arrivals
 
-    srv = tm.tmotif_server_create(0)
-    tickets = [None] * len(reqs)
-    done_at = [None] * len(reqs)
-    served = [None] * len(reqs)
-    t_start = time.perf_counter()
-    nxt = 0
-    while any(d is None for d in done_at):
-        now = time.perf_counter() - t_start
-        while nxt < len(reqs) and arrivals[nxt] <= now:
-            q, ex = reqs[nxt]
-            tickets[nxt] = tm.tmotif_submit(srv, G, q.k, q.multiset, is_extract=ex, seed=q.seed)
-            nxt += 1
-        for i in range(nxt):
-            if done_at[i] is None:
+    def serve(schedule):
+        srv = tm.tmotif_server_create(0)
+        tickets = [None] * len(reqs)
+        done_at = [None] * len(reqs)
+        served = [None] * len(reqs)
+        outstanding = set()
+        t0 = time.perf_counter()
+        nxt = 0
+        while nxt < len(reqs) or outstanding:
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and (schedule is None or schedule[nxt] <= now):
+                q, ex = reqs[nxt]
+                tickets[nxt] = tm.tmotif_submit(srv, G, q.k, q.multiset, is_extract=ex, seed=q.seed)
+                outstanding.add(nxt)
+                nxt += 1
+            for i in list(outstanding):
                 r = tm.tmotif_poll(srv, tickets[i], reqs[i][0].k)
                 if r is not None:
-                    done_at[i] = time.perf_counter() - t_start
+                    done_at[i] = time.perf_counter() - t0
                     served[i] = r
-        time.sleep(0.0002)
-    srv.close()
-    lat_served = np.array(done_at) - arrivals
+                    outstanding.discard(i)
+            time.sleep(0.0002)
+        srv.close()
+        return np.array(done_at), served
 
-    # saturated: every request submitted at once
-    srv = tm.tmotif_server_create(0)
-    t0 = time.perf_counter()
-    sat = [tm.tmotif_submit(srv, G, q.k, q.multiset, is_extract=ex, seed=q.seed) for q, ex in reqs]
-    pending = set(range(len(reqs)))
-    while pending:
-        for i in list(pending):
-            if tm.tmotif_poll(srv, sat[i], reqs[i][0].k) is not None:
-                pending.discard(i)
-        time.sleep(0.0002)
-    t_sat = time.perf_counter() - t0
-    srv.close()
+    done_served, served = serve(arrivals)
+    lat_served = done_served - arrivals
+    done_sat, served_sat = serve(None)
     G.close()
-    match = True
-    for (q, ex), pr, sr in zip(reqs, plain_res, served):
+
+    def same(pr, sr):
         dec, v, t = sr
-        if ex:
-            match &= dec.found == pr[0] and (not dec.found or (v.tolist() == pr[2] and t.tolist() == pr[3]))
-        else:
-            match &= dec.found == pr[0] and dec.sieve_sum == pr[1]
+        if pr[1] is None:  # extraction
+            return dec.found == pr[0] and (not dec.found or (v.tolist() == pr[2] and t.tolist() == pr[3]))
+        return dec.found == pr[0] and np.array_equal(dec.per_point, pr[1])
+
+    match = all(same(p, s) for p, s in zip(plain_res, served)) and all(
+        same(p, s) for p, s in zip(plain_res, served_sat))
 
     def summary(lat, done):
-        span = max(done) - arrivals[0]
+        span = float(np.max(done) - arrivals[0])
         return {"queries_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3)}
 
     by_k = {}
     for kk in sorted(set(int(q.k) for q, _ in reqs)):
-        idx = [i for i, (q, _) in enumerate(reqs) if q.k == kk]
-        by_k[kk] = {"n": len(idx), "service_ms": float(np.mean([service[i] for i in idx]) * 1e3),
-                    "plain_p50_ms": float(np.percentile(lat_plain[idx], 50) * 1e3),
-                    "served_p50_ms": float(np.percentile(lat_served[idx], 50) * 1e3),
-                    "plain_max_ms": float(np.max(lat_plain[idx]) * 1e3),
-                    "served_max_ms": float(np.max(lat_served[idx]) * 1e3)}
+        ix = [i for i, (q, _) in enumerate(reqs) if q.k == kk]
+        by_k[kk] = {"n": len(ix), "service_ms": float(np.mean([service[i] for i in ix]) * 1e3),
+                    "plain_p50_ms": float(np.percentile(lat_plain[ix], 50) * 1e3),
+                    "served_p50_ms": float(np.percentile(lat_served[ix], 50) * 1e3),
+                    "plain_p99_ms": float(np.percentile(lat_plain[ix], 99) * 1e3),
+                    "served_p99_ms": float(np.percentile(lat_served[ix], 99) * 1e3)}
+    sat_plain = len(reqs) / float(np.sum(service))
+    sat_served = len(reqs) / float(np.max(done_sat))
     return {"workload": "power-law n=2e6 m=2e7 t<=1000 16 colours; requests k~U{3..10}, 30% extract",
-            "requests": len(reqs), "arrival_rate_per_s": rate, "plain_capacity_per_s": capacity,
-            "by_k": by_k,
-            "plain": summary(lat_plain, done_plain), "served": summary(lat_served, done_at),
-            "saturated_queries_per_s": {"plain": capacity, "served": len(reqs) / t_sat},
+            "requests": len(reqs), "arrival_rate_per_s": rate, "plain_capacity_estimate_per_s": capacity_est,
+            "capacity_sample": len(idx), "load": load, "by_k": by_k,
+            "plain": summary(lat_plain, np.array(done_plain)), "served": summary(lat_served, done_served),
+            "saturated_queries_per_s": {"plain": sat_plain, "served": sat_served,
+                                        "served_over_plain": sat_served / sat_plain},
+            "timing": "host wall clock, both forms live on the same arrival schedule",
             "results_match": bool(match)}
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands on every host core, on the
+    same bounded sample of the headline decision as cpu_baseline."""
     rank, _, world = dist_env()
     if rank != 0:
         return 0
     g, q = workload(args.scale)
-    cores = os.cpu_count() or 1
-    P = max(1, min(cores, 8))
     for _ in range(args.warmup):
-        cpu_baseline(g, q, P)
+        cpu_baseline(g, q)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r = cpu_baseline(g, q, P)
-    dt = (time.perf_counter() - t0) / args.steps
+    r = None
+    for _ in range(max(args.steps, 1)):
+        r = cpu_baseline(g, q)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    P = r["cores"]
     value = g.m * q.k * P / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": r["sample"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+            "config": {"workload": WORKLOADS["mid"] if args.scale == 1.0 else f"{WORKLOAD} scaled x{args.scale}",
+                       "sample": r["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "nproc": r["nproc"], "kind": "oracle",
                              "sample": r["sample"]},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "paper": PAPER}
     print(json.dumps(line))
     return 0
 
 
+def run_leg(line, name, fn):
+    """Run one extra workload; a failure is recorded in the line, not raised."""
+    try:
+        line[name] = fn()
+    except Exception as e:  # noqa: BLE001 -- the headline line must still print
+        line[name] = {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     import paper_2001_07158_gb300 as tm
@@ -351,98 +591,28 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     if args.workload == "batch":
         return run_batch(args, tm, stream, dev, rank, world)
+    rates = probe_rates(tm)
+    costs = table_costs(rates)
     g, q = workload(args.scale, args.workload)
     seed = q.seed + 7919 * rank
     work_units = g.m * q.k * (1 << q.k)
 
     G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
-    for i in range(args.warmup):
-        tm.tmotif_decide(G, q.k, q.multiset, seed=seed + i, preprocess=args.preprocess)
-
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    props = torch.cuda.get_device_properties(dev)
-    uuid = str(getattr(props, "uuid", ""))
-    if uuid and not uuid.startswith("GPU-"):
-        uuid = "GPU-" + uuid
-    sampler = ClockSampler(uuid)
-    tm.tmotif_set_profiling(G, True)
-    sampler.start()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    found = []
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(i & 0xFF)
-            starts[i].record(stream)
-        d = tm.tmotif_decide(G, q.k, q.multiset, seed=seed + 1000 + i, per_point=False,
-                             preprocess=args.preprocess)
-        ends[i].record(stream)
-        found.append(d.found)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = sampler.stop()
-    stats = tm.tmotif_get_stats(G)
-    tm.tmotif_set_profiling(G, False)
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms, found, stats, clocks = measure_decision(tm, stream, dev, G, q, args.steps, args.warmup, seed,
+                                                      args.preprocess, world)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = world * work_units * args.steps / (total_ms / 1e3)
-
-    # roofline of the dominant kernel (the layer kernel), from the library's
-    # CUDA events around every layer launch during the timed region: achieved
-    # GF(2^64) products per second against the speed-of-light rate of the
-    # same product mix (layer_bound_s)
-    nl = max(stats["layer_launches"], 1)
-    layer_ms = stats["layer_ms"] / nl
-    muls = stats["layer_gf_muls"] / nl
-    tmuls = stats["layer_table_muls"] / nl
-    builds = stats["layer_table_builds"] / nl
-    t_min, pipes = layer_bound_s(muls - tmuls, tmuls, builds)
-    achieved = muls / (layer_ms / 1e3) / 1e9
-    peak = muls / t_min / 1e9
-    sha = source_sha()
     traffic = (LAYER_TRAFFIC["bytes_per_launch"]
-               if LAYER_TRAFFIC["source_sha"] == sha and args.workload == "mid" and args.scale == 1.0 else None)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G GF(2^64) products/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_layer (eq. gen-polynomial:3 layer)",
-                "model": "integer/shared-memory pipes from unit counts at 2070 MHz; binding pipe: "
-                         + max(pipes, key=pipes.get),
-                "pipe_ms": {k: v * 1e3 for k, v in pipes.items()}, "layer_ms_per_launch": layer_ms,
-                "gf_muls_per_launch": muls, "table_muls_per_launch": tmuls, "table_builds_per_launch": builds,
-                "algorithmic_bytes_per_launch": stats["layer_bytes"] / nl,
-                "achieved_hbm_gbs": stats["layer_bytes"] / nl / (layer_ms / 1e3) / 1e9,
-                "layer_share_of_step": stats["layer_ms"] / total_ms if total_ms else None}
+               if LAYER_TRAFFIC["source_sha"] == source_sha() and args.workload == "mid" and args.scale == 1.0
+               else None)
+    roofline = roofline_of(stats, total_ms, costs, rates, traffic)
 
-    # end to end through the C ABI with host buffers: upload + build the graph,
-    # decide, read the result back, release
-    pin = {}
-    for name in ("src", "dst", "time"):
-        a = getattr(g, name)
-        tpin = torch.empty(len(a), dtype=torch.int32, pin_memory=True)
-        tpin.numpy().view(np.uint32)[:] = a
-        pin[name] = tpin
-    cpin = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
-    cpin.numpy().view(np.uint32)[:] = g.color
-    e2e_times = []
-    for i in range(args.e2e_steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        G2 = tm.tmotif_create_graph(g.n, pin["src"].numpy().view(np.uint32), pin["dst"].numpy().view(np.uint32),
-                                    pin["time"].numpy().view(np.uint32), cpin.numpy().view(np.uint32),
-                                    g.num_colors, stream=stream)
-        d2 = tm.tmotif_decide(G2, q.k, q.multiset, seed=seed + 5000 + i, preprocess=args.preprocess)
-        G2.close()
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_t = torch.tensor([statistics.mean(e2e_times) if e2e_times else float("nan")], dtype=torch.float64,
-                         device=dev)
+    e2e_s = e2e_decision(tm, stream, g, q, seed, args.e2e_steps, args.preprocess)
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
     e2e = {"value": world * work_units / float(e2e_t.item()), "unit": UNIT,
@@ -458,77 +628,48 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
                        "parallelism": f"replicas x{world} (independent queries)"},
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": int(stats["launches"])}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "mid":
-        line["cpu_baseline"] = cpu_baseline(g, q)
-    if rank == 0 and not args.no_serving and args.workload == "mid":
-        line["serving"] = serving_benchmark(tm, stream, requests=args.serving_requests)
+            "gpu_launches": int(stats["launches"]), "paper": PAPER}
+    G.close()
+    legs = legs_of(args) if (world == 1 and args.workload == "mid" and args.scale == 1.0) else set()
+    if rank == 0 and "cpu" in legs:
+        run_leg(line, "cpu_baseline", lambda: cpu_baseline(g, q))
+    del g
+    leg_steps, leg_warmup = max(3, min(args.steps, 5)), 3
+    if "large10" in legs:
+        run_leg(line, "large10", lambda: large10_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup))
+    if "batch" in legs:
+        run_leg(line, "batch", lambda: batch_leg(tm, stream, dev, leg_steps, leg_warmup))
+    if "serving" in legs:
+        run_leg(line, "serving", lambda: serving_benchmark(tm, stream, requests=args.serving_requests))
     if rank == 0:
         print(json.dumps(line))
-    G.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
 def run_batch(args, tm, stream, dev, rank, world):
-    """Batched decisions over many small graphs: a step is one
-    tmotif_decide_batch call over all of them (the graphs resident)."""
+    """--workload batch: the batched call over the small graphs as the
+    headline (per rank, another seed)."""
     import torch
 
-    import synth
-
     count = max(1, int(10_000 * args.scale))
-    items = synth.config3_batch(num_graphs=count, seed=4 + 1000 * rank)
-    graphs = [tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
-              for g, _ in items]
-    queries = [{"k": q.k, "multiset": q.multiset, "seed": q.seed} for _, q in items]
-    work = sum(int(g.m) * q.k * (1 << q.k) for g, q in items)
-    arcs = sum(int(g.m) for g, _ in items)
-    for _ in range(args.warmup):
-        tm.tmotif_decide_batch(graphs, queries)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    sampler = ClockSampler("")
-    sampler.start()
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    total_ms = 0.0
-    found = 0
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(i & 0xFF)
-        torch.cuda.synchronize()
-        res = tm.tmotif_decide_batch(graphs, queries)
-        total_ms += res[0].ms  # device time of the call (events on the shared stream)
-        found = sum(r.found for r in res)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = sampler.stop()
-    # the plain form: one tmotif_decide per graph, back to back (same results)
-    t0 = time.perf_counter()
-    plain = [tm.tmotif_decide(G, per_point=False, **q) for G, q in zip(graphs, queries)]
-    torch.cuda.synchronize()
-    plain_ms = (time.perf_counter() - t0) * 1e3
-    same = all(p.found == r.found and p.sieve_sum == r.sieve_sum for p, r in zip(plain, res))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    leg = batch_leg(tm, stream, dev, args.steps, args.warmup, count=count, seed=4 + 1000 * rank)
+    t = torch.tensor([leg["ms_per_step"]], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * work * args.steps / (total_ms / 1e3)
+    ms = float(t.item())
+    value = world * leg["value"] * leg["ms_per_step"] / ms
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batch"], "graphs": count, "arcs": arcs, "found": found,
+            "config": {"workload": WORKLOADS["batch"], "graphs": count, "arcs": leg["arcs"], "found": leg["found"],
                        "l2": "flushed between timed steps", "parallelism": f"replicas x{world}"},
-            "clocks": clocks,
-            "plain": {"ms_per_step": plain_ms, "value": world * work / (plain_ms / 1e3), "results_match": same,
-                      "form": "one tmotif_decide per graph, sequential"}}
+            "clocks": leg["clocks"], "plain": leg["plain"]}
     if rank == 0:
         print(json.dumps(line))
-    for G in graphs:
-        G.close()
     return 0
 
 

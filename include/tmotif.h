@@ -231,8 +231,17 @@ int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_query *querie
  * asynchronously.  tmotif_submit copies the query and returns a ticket at
  * once (BUSY if the request alone exceeds the budget); tmotif_poll reports
  * done = 1 with the result once finished (verts/times may be NULL for
- * decide requests; they need room for k and k-1 entries otherwise).  A
- * finished ticket is forgotten after it is polled. */
+ * decide requests; they need room for k and k-1 entries otherwise).  For a
+ * decide request, out->per_point (caller-owned, optional: NULL or room for
+ * point_end - point_begin values, 2^k when both are 0) receives the same
+ * per-point sums tmotif_decide gives; extract requests leave it untouched.
+ * A finished ticket is forgotten after it is polled.
+ * Requests run in two lanes that share the memory budget, each with its own
+ * host worker thread and CUDA streams: requests over about 4e9 arc-lane steps
+ * (kept arcs x (k-1) x points, doubled for extraction) run one at a time in
+ * arrival order on streams of the device's least priority; smaller ones run
+ * together, in shared layer launches, on streams of its greatest priority,
+ * beside the large one.  Results never depend on the lane or the mix. */
 int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *out);
 int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_query *q, int is_extract, uint64_t *ticket);
 int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *out, uint32_t *verts, uint32_t *times,
@@ -255,7 +264,10 @@ int tmotif_set_profiling(tmotif_graph_t g, int on);
  * thread, 2 = at most 128, for L = 16 and 64; 3 = 16-thread teams at 2 lanes
  * per thread instead of the default warp team at one lane, for L = 32; 1 =
  * two 64-lane teams per chunk at 2 lanes per thread instead of one warp at 4,
- * for L = 128).  The library's autotuner picks it on the first decision that
+ * for L = 128; 4 = the staged form for L = 32, 64 and 128: the default warp
+ * team, with each team's arc metadata copied into shared memory by 1-D bulk
+ * copies, cp.async.bulk, and read back as broadcasts instead of shuffles).
+ * The library's autotuner picks it on the first decision that
  * needs it, by timing every candidate on one layer; set pins it (results
  * never depend on it), get reads it (NOT_FOUND when none is set yet).
  * Errors: INVALID for a bad L, chunk or variant. */
@@ -272,9 +284,7 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
  * threads per SM: method 0 = register multiply (Karatsuba over 32x32
  * carry-less products with holes); method 1 = a warp builds the 16 x 16 nibble
  * table of one multiplier in shared memory and applies it to 64 lanes (2 per
- * thread); method 2 = the same table applied to 128 lanes (4 per thread);
- * method 3 = method 1 with the older lookup address (a shift and a logic op
- * per load) and its nibble shifts done by multiplies.
+ * thread); method 2 = the same table applied to 128 lanes (4 per thread).
  * Runs `iters` rounds; ms receives the device time, products the products
  * done.  INVALID for another method or iters = 0. */
 int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products);
@@ -297,19 +307,34 @@ int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products);
  *   d_per_point   caller-owned DEVICE output of point_end - point_begin
  *                 values (2^k when both are 0); XOR them for the sieve sum;
  *   cuda_stream   stream for all work; the call returns after it finished.
+ * A graph without arcs (m = 0) gives all-zero sums.
  * Errors: UNSUPPORTED when the graph needs more scratch than the fixed array
  * (the message gives both sizes) or k is outside [2, TMOTIF_KMAX]; INVALID for
- * arcs that are not canonical and sorted, bad colours or query fields; CUDA.
+ * arcs that are not canonical and sorted, m >= 2^32 - 1, a vertex colour (of
+ * any vertex, with or without arcs) >= num_colors, or bad query fields; CUDA.
  * All calls share the array and it keeps the previous call's contents; each
  * call clears what must start at zero.  Calls whose work overlaps on the GPU
  * (other streams or host threads on the same device) race on the array and
- * must be serialised by the caller.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture. */
+ * must be serialised by the caller.  Every call synchronises cuda_stream
+ * before it returns.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  The address is kept for the life of
+ * the process: after a cudaDeviceReset of a device, do not call this entry
+ * point on that device again. */
 #define TMOTIF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int tmotif_decide_noalloc(const uint32_t *d_src, const uint32_t *d_dst, const uint32_t *d_time, uint64_t m,
                           const uint32_t *d_color, uint32_t n, uint32_t num_colors, const tmotif_query *q,
                           uint64_t *d_per_point, void *cuda_stream);
+
+/* 1 for the checked build (libtmotif_checked.so, compiled with
+ * -DTMOTIF_CHECKED), 0 otherwise.  The checked build tests, on the device,
+ * the indices the kernels derive from their inputs (vertex ids of arcs, in-
+ * segment offsets, checkpoint numbers, lane indices, colour slots) before each
+ * access; a failed test skips the access and sets a status bit, and the call
+ * that ran the kernel returns TMOTIF_ERR_INVALID.  No check traps.  Every call
+ * of both builds reads the status word after its work (a failed staged bulk
+ * copy wait gives TMOTIF_ERR_TIMEOUT). */
+uint32_t tmotif_checked_build(void);
 
 /* Message for the last error on the calling thread (never NULL). */
 const char *tmotif_last_error(void);

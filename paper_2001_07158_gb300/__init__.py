@@ -26,7 +26,9 @@ TMOTIF_PREPROCESS_STATIC = 4
 ERRORS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "NOT_FOUND", 7: "BUSY"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libtmotif.so")
+# TMOTIF_LIB selects another build of the library (the checked build,
+# _build_checked/libtmotif_checked.so, for device bounds checks)
+LIB_PATH = os.environ.get("TMOTIF_LIB") or os.path.join(_HERE, "_build", "libtmotif.so")
 
 
 class TmotifError(RuntimeError):
@@ -92,6 +94,7 @@ def _load():
         "tmotif_gf_mul_batch": (C.c_int, [P, P, P, C.c_uint64]),
         "tmotif_gf_probe": (C.c_int, [C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
         "tmotif_decide_noalloc": (C.c_int, [P, P, P, C.c_uint64, P, C.c_uint32, C.c_uint32, C.POINTER(_Query), P, P]),
+        "tmotif_checked_build": (C.c_uint32, []),
         "tmotif_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -330,6 +333,11 @@ def tmotif_gf_probe(method: int, iters: int = 256):
     return ms.value, n.value
 
 
+def tmotif_checked_build() -> bool:
+    """True when the loaded library is the checked build (device bounds checks)."""
+    return bool(_lib.tmotif_checked_build())
+
+
 def tmotif_last_error() -> str:
     return _lib.tmotif_last_error().decode()
 
@@ -340,6 +348,7 @@ def tmotif_last_error() -> str:
 class Server:
     def __init__(self, handle):
         self._h = handle
+        self._npts = {}  # ticket -> (number of per-point sums, their buffer) of a decide request
 
     @property
     def handle(self):
@@ -365,33 +374,48 @@ def tmotif_server_create(hbm_budget_bytes: int) -> Server:
 
 def tmotif_submit(s: Server, g: Graph, k, multiset, *, is_extract=False, start=TMOTIF_ANY, end=TMOTIF_ANY,
                   t_min=0, t_max=0, seed=1, repeats=1, method="localized", timestamps=None,
-                  preprocess=False) -> int:
+                  preprocess=False, point_begin=0, point_end=0) -> int:
     flags = (TMOTIF_EXTRACT_HALVING if method == "halving" else 0) | (TMOTIF_PREPROCESS_STATIC if preprocess else 0)
-    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, 0, 0, flags, timestamps)
+    q, keep = _query(k, multiset, start, end, t_min, t_max, seed, repeats, point_begin, point_end, flags,
+                     timestamps)
     t = C.c_uint64(0)
     _check(_lib.tmotif_submit(s.handle, g.handle, C.byref(q), int(bool(is_extract)), C.byref(t)))
+    if not is_extract:
+        npts = (1 << k) if point_end == 0 else max(point_end - point_begin, 0)
+        s._npts[int(t.value)] = (npts, np.zeros(max(npts, 1), np.uint64))
     return int(t.value)
 
 
+def _poll_buffers(s: Server, ticket: int, k: int):
+    npts, pp = s._npts.get(ticket, (None, None))
+    d = _Decision(0, 0, None if pp is None else pp.ctypes.data, 0.0)
+    return npts, pp, d, np.zeros(max(k, 1), np.uint32), np.zeros(max(k, 1), np.uint32)
+
+
 def tmotif_poll(s: Server, ticket: int, k: int):
-    d = _Decision(0, 0, None, 0.0)
-    verts = np.zeros(max(k, 1), np.uint32)
-    times = np.zeros(max(k, 1), np.uint32)
+    """None while the request runs; then (Decision, verts, times).  A decide
+    request's Decision carries its per-point sums (first repeat)."""
+    npts, pp, d, verts, times = _poll_buffers(s, ticket, k)
     done = C.c_int(0)
-    _check(_lib.tmotif_poll(s.handle, ticket, C.byref(d), verts.ctypes.data, times.ctypes.data, C.byref(done)))
-    if not done.value:
+    rc = _lib.tmotif_poll(s.handle, ticket, C.byref(d), verts.ctypes.data, times.ctypes.data, C.byref(done))
+    if rc == 0 and not done.value:
         return None
-    return Decision(bool(d.found), int(d.sieve_sum), None, float(d.ms)), verts[:k], times[:k - 1]
+    s._npts.pop(ticket, None)
+    _check(rc)
+    return (Decision(bool(d.found), int(d.sieve_sum), None if pp is None else pp[:npts], float(d.ms)), verts[:k],
+            times[:k - 1])
 
 
 def tmotif_wait(s: Server, ticket: int, k: int, timeout_ms: int):
     """Block until the request finishes (raises TmotifError TIMEOUT = 4 after
     timeout_ms, the request staying pending); returns what tmotif_poll does."""
-    d = _Decision(0, 0, None, 0.0)
-    verts = np.zeros(max(k, 1), np.uint32)
-    times = np.zeros(max(k, 1), np.uint32)
-    _check(_lib.tmotif_wait(s.handle, ticket, int(timeout_ms), C.byref(d), verts.ctypes.data, times.ctypes.data))
-    return Decision(bool(d.found), int(d.sieve_sum), None, float(d.ms)), verts[:k], times[:k - 1]
+    npts, pp, d, verts, times = _poll_buffers(s, ticket, k)
+    rc = _lib.tmotif_wait(s.handle, ticket, int(timeout_ms), C.byref(d), verts.ctypes.data, times.ctypes.data)
+    if rc != 4:  # TIMEOUT leaves the request pending
+        s._npts.pop(ticket, None)
+    _check(rc)
+    return (Decision(bool(d.found), int(d.sieve_sum), None if pp is None else pp[:npts], float(d.ms)), verts[:k],
+            times[:k - 1])
 
 
 def tmotif_server_destroy(s: Server):

@@ -131,7 +131,7 @@ void Workspace::set_stream(cudaStream_t s)
 {
     DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &kbits, &ftiles, &pos,
                      &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list,
-                     &arc_sum, &queue};
+                     &arc_sum, &queue, &rec};
     for (DevBuf *b : all) b->stream = s;
 }
 
@@ -139,7 +139,7 @@ void Workspace::release()
 {
     DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &kbits, &ftiles, &pos,
                      &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list,
-                     &arc_sum, &queue};
+                     &arc_sum, &queue, &rec};
     for (DevBuf *b : all) b->release();
     if (host_pinned) cudaFreeHost(host_pinned);
     host_pinned = nullptr;
@@ -150,7 +150,7 @@ size_t Workspace::bytes() const
 {
     const DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &kbits, &ftiles, &pos,
                            &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list,
-                           &arc_sum, &queue};
+                           &arc_sum, &queue, &rec};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->bytes;
     return s;
@@ -562,14 +562,24 @@ static bool valid_shape(uint32_t L, uint32_t chunk, uint32_t variant)
     const bool pow2 = L >= 4 && L <= 128 && (L & (L - 1)) == 0;
     const bool ch = chunk == 64 || chunk == 128 || chunk == 256 || chunk == 512 || chunk == 1024;
     const bool var = variant == 0 || (variant <= 2 && (L == 16 || L == 64)) || (variant == 3 && L == 32) ||
-                     (variant == 1 && L == 128);
+                     (variant == 1 && L == 128) || (variant == 4 && (L == 32 || L == 64 || L == 128));
     return pow2 && ch && var;
+}
+
+uint32_t tmotif_checked_build(void)
+{
+#ifdef TMOTIF_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int tmotif_set_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t chunk, uint32_t variant)
 {
     if (!g) return fail(TMOTIF_ERR_INVALID, "null graph").code;
     if (!valid_shape(L, chunk, variant)) return fail(TMOTIF_ERR_INVALID, "bad layer shape").code;
+    std::lock_guard<std::mutex> lock(layer_tune_mutex());
     g->layer_tune[L] = {chunk, variant};
     return TMOTIF_OK;
 }
@@ -577,6 +587,7 @@ int tmotif_set_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t chunk, uint32_
 int tmotif_get_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t *chunk, uint32_t *variant)
 {
     if (!g || !chunk || !variant) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    std::lock_guard<std::mutex> lock(layer_tune_mutex());
     auto it = g->layer_tune.find(L);
     if (it == g->layer_tune.end()) return fail(TMOTIF_ERR_NOT_FOUND, "no layer shape for this lane width").code;
     *chunk = it->second.first;
@@ -599,7 +610,7 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
 
 int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products)
 {
-    if (!ms || !products || method < 0 || method > 3 || iters == 0)
+    if (!ms || !products || method < 0 || method > 2 || iters == 0)
         return fail(TMOTIF_ERR_INVALID, "bad probe arguments").code;
     return gf_probe(method, iters, ms, (u64 *)products).code;
 }

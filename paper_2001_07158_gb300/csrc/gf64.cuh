@@ -11,9 +11,12 @@
 // (bits 0 mod 4, 1 mod 4, ...) with three-bit holes between set bits; an
 // ordinary integer product of two such spread words counts at most 8 partial
 // products per output bit, which stays inside its 4-bit slot, so the parity
-// of each slot is the carry-less bit ("multiplication with holes").  Three
-// such products form the 64x64 product by Karatsuba.  The table form in
-// gf_mul_table() serves multipliers shared by many sieve lanes.
+// of each slot is the carry-less bit.  This is the "multiplication with
+// holes" of T. Pornin's constant-time GHASH for BearSSL (ghash_ctmul,
+// described on bearssl.org under constant-time multiplication), restated
+// here for 32-bit operands.  Three such products form the 64x64 product by
+// Karatsuba.  The table form, gf_table_mul(), serves multipliers shared by
+// many sieve lanes.
 #pragma once
 #include <stdint.h>
 
@@ -163,50 +166,6 @@ __device__ __forceinline__ u64 gf_table_mul(const u64 *tab, u64 s)
     TM_LDS64(v14, TM_NIB(eh, 3), 1792);
     TM_LDS64(v15, TM_NIB(oh, 3), 1920);
 #undef TM_NIB
-    return ((v0 ^ v1 ^ v2) ^ (v3 ^ v4 ^ v5)) ^ ((v6 ^ v7 ^ v8) ^ (v9 ^ v10 ^ v11)) ^ ((v12 ^ v13 ^ v14) ^ v15);
-}
-
-// The same lookup with the nibble shifts moved to the multiply pipe: for a
-// 32-bit w and s in [1, 31], mul.hi(w, 2^(32-s)) = w >> s.  m[i] holds
-// 2^(32-(4i+1)) for i = 0..6 (shifts 1, 5, ..., 25) and m[7] = 8; the caller
-// keeps them in registers (computed from a value the compiler cannot fold,
-// so that the multiplies are not turned back into shifts), which leaves the
-// ALU pipe one logic op per lookup for the address.
-struct NibbleMuls {
-    u32 m[8];
-};
-
-__device__ __forceinline__ NibbleMuls nibble_muls(u32 one)
-{
-    NibbleMuls n;
-#pragma unroll
-    for (int i = 0; i < 7; i++) n.m[i] = one << (31 - 4 * i);
-    n.m[7] = one << 3;
-    return n;
-}
-
-__device__ __forceinline__ u64 gf_table_mul_m(const u64 *tab, u64 s, const NibbleMuls &n)
-{
-    const u32 ta = (u32)__cvta_generic_to_shared(tab);
-    const u64 sw = s ^ 0xECA86420ECA86420ull;
-    const u32 lo = (u32)sw, hi = (u32)(sw >> 32);
-    u64 v0, v1, v2, v3, v4, v5, v6, v7, v8, v9, v10, v11, v12, v13, v14, v15;
-    TM_LDS64(v0, ((lo * n.m[7]) & 0x78u) | ta, 0);
-    TM_LDS64(v1, (__umulhi(lo, n.m[0]) & 0x78u) | ta, 128);
-    TM_LDS64(v2, (__umulhi(lo, n.m[1]) & 0x78u) | ta, 256);
-    TM_LDS64(v3, (__umulhi(lo, n.m[2]) & 0x78u) | ta, 384);
-    TM_LDS64(v4, (__umulhi(lo, n.m[3]) & 0x78u) | ta, 512);
-    TM_LDS64(v5, (__umulhi(lo, n.m[4]) & 0x78u) | ta, 640);
-    TM_LDS64(v6, (__umulhi(lo, n.m[5]) & 0x78u) | ta, 768);
-    TM_LDS64(v7, (__umulhi(lo, n.m[6]) & 0x78u) | ta, 896);
-    TM_LDS64(v8, ((hi * n.m[7]) & 0x78u) | ta, 1024);
-    TM_LDS64(v9, (__umulhi(hi, n.m[0]) & 0x78u) | ta, 1152);
-    TM_LDS64(v10, (__umulhi(hi, n.m[1]) & 0x78u) | ta, 1280);
-    TM_LDS64(v11, (__umulhi(hi, n.m[2]) & 0x78u) | ta, 1408);
-    TM_LDS64(v12, (__umulhi(hi, n.m[3]) & 0x78u) | ta, 1536);
-    TM_LDS64(v13, (__umulhi(hi, n.m[4]) & 0x78u) | ta, 1664);
-    TM_LDS64(v14, (__umulhi(hi, n.m[5]) & 0x78u) | ta, 1792);
-    TM_LDS64(v15, (__umulhi(hi, n.m[6]) & 0x78u) | ta, 1920);
     return ((v0 ^ v1 ^ v2) ^ (v3 ^ v4 ^ v5)) ^ ((v6 ^ v7 ^ v8) ^ (v9 ^ v10 ^ v11)) ^ ((v12 ^ v13 ^ v14) ^ v15);
 }
 

@@ -5,6 +5,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -77,6 +78,36 @@ struct Profiler {
 
 enum { FAM_LAYER = 0, FAM_PREP = 1, FAM_COEF = 2, FAM_OTHER = 3 };
 
+// Bits of the per-device status word that kernels set when they meet a
+// condition they cannot continue on normally; the host takes (reads and
+// clears) the word after each decision and reports it as an error.
+enum : u32 {
+    TM_STATUS_STAGE_TIMEOUT = 1u,  // a staged layer's bulk copy did not land within its wait limit
+    TM_STATUS_BOUNDS = 2u          // checked build: an index failed its bounds check (access skipped)
+};
+// Device bounds checks of the checked build (compiled with -DTMOTIF_CHECKED,
+// libtmotif_checked.so): TM_IN(i, n, status) is true when i < n; otherwise it
+// sets TM_STATUS_BOUNDS in *status and is false, and the caller skips the
+// access.  It never traps.  In the normal build it is constant true.
+#ifdef TMOTIF_CHECKED
+__device__ __forceinline__ bool tm_in(u64 i, u64 n, u32 *status)
+{
+    if (i < n) return true;
+    if (status) atomicOr(status, TM_STATUS_BOUNDS);
+    return false;
+}
+#define TM_IN(i, n, status) ::tmo::tm_in((u64)(i), (u64)(n), (status))
+#else
+#define TM_IN(i, n, status) true
+#endif
+// Address of the status word on the current device.
+Status status_word(u32 **p);
+// Enqueue on st: move the status word (atomic exchange with 0) to *d_slot
+// (device u32), then copy it to *h_slot (pinned host u32).
+Status status_take_enqueue(cudaStream_t st, u32 *d_slot, u32 *h_slot);
+// After the stream is synchronised: an error for a nonzero taken word.
+Status status_result(u32 taken);
+
 // Per-query scratch on the device (grown on demand, reused across queries).
 struct Workspace {
     DevBuf vflag;                       // n bytes: colour in M and alive
@@ -99,6 +130,7 @@ struct Workspace {
     DevBuf arc_sum;                     // m_f u64: arc-localised sieve sums
     DevBuf partial;                     // chunks * L u64: per-chunk sieve sums
     DevBuf queue;                       // u64 team counter of the layer launches
+    DevBuf rec;                         // m_f x 16 B: {dst, cp_in, cp_out, src} of the staged layer form
     void *host_pinned = nullptr;        // small pinned readback area
     size_t host_pinned_bytes = 0;
     void release();
@@ -202,6 +234,14 @@ struct LayerParams {
     // single-job launches: team counter (zeroed before the launch) from which
     // resident teams take the next team index; null: one team per team slot
     unsigned long long *queue = nullptr;
+    // staged form: per filtered arc {dst, cp_in, cp_out, src} (16 bytes; the
+    // times come from `time`, padded to a multiple of 4 entries)
+    const uint4 *rec = nullptr;
+    // the device status word (TM_STATUS_* bits), or null
+    u32 *status = nullptr;
+    // bounds of the checked build: vertices (x rows) and checkpoints (C rows)
+    u32 n_vert = 0;
+    u64 n_cp = 0;
 };
 
 // One decision in flight: its query, its device workspace and its progress
@@ -245,6 +285,9 @@ Status job_prep(Job &j);
 // A launch shape the autotuner found on this device for lane width L and a
 // layer of about mf arcs (same floor(log2)), if any.
 bool tuned_shape(u32 L, u64 mf, std::pair<u32, u32> *shape);
+// Guards every graph's layer_tune map: the server's lanes prepare jobs on
+// one graph from two host threads.
+std::mutex &layer_tune_mutex();
 Status job_batch_begin(Job &j);
 LayerParams job_layer_params(const Job &j);
 Status job_readout_enqueue(Job &j);
@@ -256,6 +299,14 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
                      size_t host_params_bytes, Profiler *prof);
 // Device bytes a job will hold once prepped (for admission).
 size_t job_bytes(const Job &j);
+// A whole prepped job at once: job_enqueue_all enqueues every lane batch of
+// every repeat (coefficients, layers, readout into a per-batch pinned slot)
+// and the status word's readout on the job's stream -- with tune, layer 3 of
+// the first batch runs the autotuner where the graph has no shape for the
+// lane width yet; after the stream is synchronised, job_finish_all checks the
+// status word and accumulates the readouts (the job is then done).
+Status job_enqueue_all(Job &j, bool tune);
+Status job_finish_all(Job &j);
 
 // Decide on graph g; alive (device, n bytes, may be null) masks vertices.
 // per_point (host, may be null) receives repeat-0 values on [p_begin,p_end).

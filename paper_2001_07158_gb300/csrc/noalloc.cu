@@ -17,7 +17,10 @@
 // In host code the array's name is only a host-side stand-in; its device
 // address comes from cudaGetSymbolAddress, looked up once per device by the
 // first call made on that device (with that device current).  Make that first
-// call before any stream capture.
+// call before any stream capture.  The looked-up address is kept for the life
+// of the process: after a cudaDeviceReset of a device, this entry point must
+// not be called on that device again.  Every call synchronises its stream
+// before it returns (it reads a validation flag and waits for the result).
 #include <mutex>
 
 #include "gf64.cuh"
@@ -66,6 +69,14 @@ Layout layout_for(u32 n, u64 m, u32 num_colors, u32 k)
     l.c1 = take(m * NA_LANES * 8);
     l.total = o;
     return l;
+}
+
+// Every vertex colour must be < num_colors (the coefficient kernel indexes
+// the slot tables by the colour of every vertex, with or without arcs).
+__global__ void k_na_check_colors(u32 n, const u32 *color, u32 num_colors, u32 *err)
+{
+    const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n && color[u] >= num_colors) atomicOr(err, 2u);
 }
 
 // Arcs must be canonical: ids < n, time >= 1, no self-loop, strictly
@@ -299,6 +310,9 @@ Status decide_noalloc(const u32 *src, const u32 *dst, const u32 *time, u64 m, co
     if (num_colors == 0 || num_colors > NA_COLORS_MAX) return fail(TMOTIF_ERR_INVALID, "num_colors must be in [1, 4096]");
     if (n == 0 || (m > 0 && (!src || !dst || !time)) || !color || !d_out)
         return fail(TMOTIF_ERR_INVALID, "null graph or output pointer");
+    // arc offsets, counts and checkpoint numbers are 32-bit (and the scratch
+    // layout below is computed in size_t, which this bound keeps exact)
+    if (m > (u64)0xFFFFFFFEu) return fail(TMOTIF_ERR_INVALID, "m must be below 2^32 - 1");
     if (q->start != TMOTIF_ANY && q->start >= n) return fail(TMOTIF_ERR_INVALID, "start vertex out of range");
     if (q->end != TMOTIF_ANY && q->end >= n) return fail(TMOTIF_ERR_INVALID, "end vertex out of range");
     const u32 k = q->k;
@@ -333,20 +347,28 @@ Status decide_noalloc(const u32 *src, const u32 *dst, const u32 *time, u64 m, co
     u64 *wtab = (u64 *)(S + L.wtab), *out = (u64 *)(S + L.out), *x = (u64 *)(S + L.x);
     u64 *C[2] = {(u64 *)(S + L.c0), (u64 *)(S + L.c1)};
 
-    // Validate the arcs and pick the ones whose colours are in the multiset.
+    // Validate the colours and the arcs and pick the arcs whose colours are in
+    // the multiset.
     TM_CUDA(cudaMemsetAsync(err, 0, 4, st));
     TM_CUDA(cudaMemsetAsync(cnt, 0, 16, st));
     TM_CUDA(cudaMemcpyAsync(d_slot_count, slot_count, num_colors * 4, cudaMemcpyHostToDevice, st));
     TM_CUDA(cudaMemcpyAsync(d_slot_begin, slot_begin, num_colors * 4, cudaMemcpyHostToDevice, st));
+    k_na_check_colors<<<blocks_for(n, 256), 256, 0, st>>>(n, color, num_colors, err);
     k_na_check_keep<<<blocks_for(m + 1, 256), 256, 0, st>>>(m, n, src, dst, time, color, num_colors, d_slot_count,
                                                             q->t_min, q->t_max, keep, err);
     TM_CUDA(cudaGetLastError());
     u32 h_err = 0;
     TM_CUDA(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
+    if (h_err & 2u) return fail(TMOTIF_ERR_INVALID, "every vertex colour must be < num_colors");
     if (h_err)
         return fail(TMOTIF_ERR_INVALID, "arcs must have ids < n, time >= 1, no self-loops, colours < num_colors, "
                                         "and be strictly increasing in (dst, time, src)");
+    if (m == 0) {  // no arcs, no walks: every per-point sum is zero
+        TM_CUDA(cudaMemsetAsync(d_out, 0, (p_end - p_begin) * 8, st));
+        TM_CUDA(cudaStreamSynchronize(st));
+        return Status();
+    }
 
     // Compact, segments, last earlier in-arc, checkpoints (counts stay on the device).
     k_na_scan<<<1, 1024, 0, st>>>(keep, nullptr, m + 1, cnt + 0);

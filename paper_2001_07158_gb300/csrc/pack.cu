@@ -28,10 +28,11 @@ namespace tmo {
 __global__ void k_active_list(u32 n, const u32 *act, u32 *list);
 __global__ void k_compact(u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32 *off, u32 *f_src,
                           u32 *f_dst, u32 *f_time);
-__global__ void k_segments(u64 mf, const u32 *f_dst, u32 *seg_lo, u32 *seg_hi);
+__global__ void k_segments(u64 mf, const u32 *f_dst, u32 *seg_lo, u32 *seg_hi, u32 n);
 __global__ void k_pos(u64 mf, const u32 *f_src, const u32 *f_time, const u32 *seg_lo, const u32 *seg_hi, u32 *pos,
-                      u32 *mark);
-__global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in, u32 *cp_out);
+                      u32 *mark, u32 n);
+__global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in, u32 *cp_out, const u32 *f_src,
+                              const u32 *f_dst, uint4 *rec);
 
 namespace {
 
@@ -297,13 +298,14 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
             TM_CUDA(cudaMemsetAsync(B.seg_hi.p, 0, N * 4, st));
             TM_CUDA(cudaMemsetAsync(B.mark.p, 0, (mf + 1) * 4, st));
             k_segments<<<blocks_of(mf, 256), 256, 0, st>>>(mf, o_dst.as<u32>(), B.seg_lo.as<u32>(),
-                                                           B.seg_hi.as<u32>());
+                                                           B.seg_hi.as<u32>(), (u32)N);
             k_pos<<<blocks_of(mf, 256), 256, 0, st>>>(mf, o_src.as<u32>(), o_time.as<u32>(), B.seg_lo.as<u32>(),
-                                                      B.seg_hi.as<u32>(), B.pos.as<u32>(), B.mark.as<u32>());
+                                                      B.seg_hi.as<u32>(), B.pos.as<u32>(), B.mark.as<u32>(), (u32)N);
             TM_CUDA(cudaGetLastError());
             TM_TRY(exclusive_scan_on(st, B.block_sums, B.mark.as<u32>(), mf + 1, d_cnt + 1, launches));
             k_checkpoints<<<blocks_of(mf, 256), 256, 0, st>>>(mf, B.pos.as<u32>(), B.mark.as<u32>(),
-                                                              B.cp_in.as<u32>(), B.cp_out.as<u32>());
+                                                              B.cp_in.as<u32>(), B.cp_out.as<u32>(), nullptr, nullptr,
+                                                              nullptr);
             TM_CUDA(cudaGetLastError());
             *launches += 4;
             TM_CUDA(cudaMemcpyAsync(h_cnt + 1, d_cnt + 1, 4, cudaMemcpyDeviceToHost, st));
@@ -346,6 +348,9 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
             const size_t smem = 8 * 256 * 8 + 2048;  // 18 KB: within the default dynamic limit
             TM_TRY(B.queue.reserve(sizeof(unsigned long long)));
             lp.queue = B.queue.as<unsigned long long>();
+            lp.n_vert = (u32)N;
+            lp.n_cp = ncp;
+            TM_TRY(status_word(&lp.status));
             static const int per_sm = [&] {
                 int nb = 0;
                 const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pack_layer, 256, smem);

@@ -69,6 +69,29 @@ const double LARGE_WORK = 4e9;
 
 enum JobState { J_BEGIN = 0, J_LAYER = 1, J_READOUT = 2 };
 
+// Device memory shared by the schedulers of one server (or held by one
+// batch): a job is admitted while the bytes it may hold fit the budget, or
+// when nothing is admitted at all, so that a job larger than the budget's
+// free part still runs alone.
+struct Budget {
+    explicit Budget(size_t b) : budget(b) {}
+    bool try_take(size_t bytes)
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (in_use != 0 && in_use + bytes > budget) return false;
+        in_use += bytes;
+        return true;
+    }
+    void give(size_t bytes)
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        in_use -= bytes;
+    }
+    const size_t budget;
+    std::mutex mu;
+    size_t in_use = 0;
+};
+
 struct SJob {
     Job job;
     Workspace ws;
@@ -82,44 +105,44 @@ class Scheduler {
 public:
     // st: the stream of the shared layer launches; prep_st: the stream of
     // job preparation (filter, checkpoints, masks), so that jobs admitted
-    // while layers run are prepared beside them (the same stream when equal)
-    Scheduler(cudaStream_t st, size_t budget, cudaStream_t prep_st = nullptr)
+    // while layers run are prepared beside them (the same stream when equal);
+    // budget: the device memory the admitted jobs draw on
+    Scheduler(cudaStream_t st, Budget *budget, cudaStream_t prep_st = nullptr)
         : st_(st), prep_st_(prep_st ? prep_st : st), budget_(budget)
     {
     }
     ~Scheduler()
     {
         for (auto &d : dev_params_) d.release();
+        status_dev_.release();
         if (host_params_) cudaFreeHost(host_params_);
+        if (status_host_) cudaFreeHost(status_host_);
         prof.destroy();
     }
 
     Status init()
     {
         TM_CUDA(cudaMallocHost(&host_params_, kSlotBytes * kMaxLayersPerSync));
+        TM_CUDA(cudaMallocHost(&status_host_, 64));
         for (auto &d : dev_params_) d.stream = st_;
+        status_dev_.stream = st_;
+        TM_TRY(status_dev_.reserve(64));
         return Status();
     }
 
-    // room for one more job: within the memory budget, and the job tables
-    // of one layer launch stay inside a slot
-    bool fits(size_t bytes) const
-    {
-        return in_use_ + bytes <= budget_ && active_.size() + staged_.size() < kMaxActive;
-    }
-    size_t in_use() const { return in_use_; }
-    size_t budget() const { return budget_; }
+    // room for one more job: the job tables of one layer launch stay inside
+    // a slot (memory is taken from the budget by the caller)
+    bool room() const { return active_.size() + staged_.size() < kMaxActive; }
     bool idle() const { return active_.empty() && staged_.empty(); }
-    size_t active() const { return active_.size(); }
 
-    // Admit a job whose query/graph/mask are set; runs its prep on the prep
-    // stream (which the prep synchronises).  On return the job is staged to
-    // join the active jobs at the end of the current step (or at once when
-    // no step is running), or finished (nothing kept) and appended to done.
+    // Admit a job whose query/graph/mask are set and whose `reserved` bytes
+    // the caller took from the budget; runs its prep on the prep stream
+    // (which the prep synchronises).  On return the job is staged to join
+    // the active jobs at the end of the current step (or at once when no
+    // step is running), or finished (nothing kept) and appended to done.
     Status admit(std::unique_ptr<SJob> sj, size_t reserved, std::vector<std::unique_ptr<SJob>> *done)
     {
         sj->reserved = reserved;
-        in_use_ += reserved;
         sj->ws.set_stream(prep_st_);
         sj->job.ws = &sj->ws;
         sj->job.st = prep_st_;
@@ -128,12 +151,12 @@ public:
         sj->ws.set_stream(st_);
         sj->job.st = st_;
         if (!s.ok()) {
-            in_use_ -= reserved;
+            budget_->give(reserved);
             return s;
         }
         sj->state = J_BEGIN;
         if (sj->job.done) {
-            in_use_ -= sj->reserved;
+            budget_->give(sj->reserved);
             done->push_back(std::move(sj));
         } else if (in_step_) {
             staged_.push_back(std::move(sj));
@@ -166,6 +189,7 @@ public:
         for (auto &sj : staged_) active_.push_back(std::move(sj));
         staged_.clear();
         if (active_.empty()) return Status();
+        if (whole_jobs_ && active_.size() == 1) return step_whole(done, overlap);
         for (int rounds = 0; rounds < kMaxLayersPerSync; rounds++) {
             std::vector<Job *> layer;
             for (auto &sj : active_) {
@@ -191,8 +215,10 @@ public:
         in_step_ = true;
         Status os = overlap();
         in_step_ = false;
+        TM_TRY(status_take_enqueue(st_, status_dev_.as<u32>(), status_host_));
         TM_CUDA(cudaStreamSynchronize(st_));
         TM_TRY(os);
+        TM_TRY(status_result(*status_host_));
         TM_TRY(prof.collect());
         steps++;
         std::vector<std::unique_ptr<SJob>> keep;
@@ -201,7 +227,7 @@ public:
                 job_readout_finish(sj->job);
                 sj->state = J_BEGIN;
                 if (sj->job.done) {
-                    in_use_ -= sj->reserved;
+                    budget_->give(sj->reserved);
                     done->push_back(std::move(sj));
                     continue;
                 }
@@ -218,22 +244,50 @@ public:
         return step(done, [] { return Status(); });
     }
 
+    // Whole jobs: a job alone in the scheduler runs in one step as a plain
+    // decision does -- every lane batch enqueued back to back (the autotuner
+    // on its first layer 3 where the graph has no shape yet), one sync.
+    void set_whole_jobs(bool on) { whole_jobs_ = on; }
+
     Profiler prof;
     u64 steps = 0;
 
 private:
+    template <class F>
+    Status step_whole(std::vector<std::unique_ptr<SJob>> *done, F &&overlap)
+    {
+        SJob &sj = *active_[0];
+        TM_TRY(job_enqueue_all(sj.job, true));
+        in_step_ = true;
+        Status os = overlap();
+        in_step_ = false;
+        TM_CUDA(cudaStreamSynchronize(st_));
+        TM_TRY(os);
+        TM_TRY(prof.collect());
+        TM_TRY(job_finish_all(sj.job));
+        steps++;
+        budget_->give(sj.reserved);
+        done->push_back(std::move(active_[0]));
+        active_.clear();
+        for (auto &x : staged_) active_.push_back(std::move(x));
+        staged_.clear();
+        return Status();
+    }
+
     static_assert(4096 * (sizeof(LayerParams) + 8) + 6 * (256 + 16) < (1 << 20), "job tables exceed a slot");
     // one job-table slot (host pinned + device) per layer round between syncs
     static const int kMaxLayersPerSync = 8;
     static const size_t kSlotBytes = 1 << 20;
     static const size_t kMaxActive = 4096;  // x (LayerParams + prefix) < kSlotBytes
     cudaStream_t st_, prep_st_;
-    size_t budget_;
-    size_t in_use_ = 0;
+    Budget *budget_;
     bool in_step_ = false;
+    bool whole_jobs_ = false;
     std::vector<std::unique_ptr<SJob>> active_, staged_;
     DevBuf dev_params_[kMaxLayersPerSync];
     void *host_params_ = nullptr;
+    DevBuf status_dev_;           // the device status word taken after each step ...
+    u32 *status_host_ = nullptr;  // ... and its pinned host copy
 };
 
 size_t default_budget()
@@ -298,7 +352,8 @@ extern "C" int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_qu
             graphs[0]->prof.stats.launches += launches;
             return TMOTIF_OK;
         }
-        Scheduler sched(st, default_budget());
+        Budget budget(default_budget());
+        Scheduler sched(st, &budget);
         Status s = sched.init();
         if (!s.ok()) return s.code;
         cudaEvent_t e0, e1;
@@ -319,7 +374,7 @@ extern "C" int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_qu
         while (next < count || !sched.idle()) {
             while (next < count) {
                 const size_t need = job_estimate(*graphs[next], specs[next]);
-                if (!sched.idle() && !sched.fits(need)) break;
+                if (!sched.room() || !budget.try_take(need)) break;
                 auto sj = std::make_unique<SJob>();
                 sj->owner = next;
                 sj->job.g = graphs[next];
@@ -346,8 +401,23 @@ extern "C" int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_qu
     }
 }
 
+
 // ---------------------------------------------------------------------------
 // Request server
+//
+// Two lanes, each a worker thread with its own scheduler, streams and
+// finishing workspace, drawing on one memory budget:
+//   lane 0 takes the small requests and runs them on streams of the
+//     device's greatest priority, many at a time in shared layer launches;
+//   lane 1 takes the large requests (over LARGE_WORK arc-lane steps) one at
+//     a time, in arrival order, on streams of the least priority; each of
+//     their jobs runs whole, as a plain decision does (every lane batch
+//     enqueued back to back in the tuned launch shape, one sync).
+// Small requests thus run beside a large one on the device: their kernels are
+// scheduled first whenever SMs free up, and fill the large request's
+// preparation, readout and synchronisation gaps, instead of waiting behind
+// it.  When the large lane waits for memory, the small lane admits nothing
+// new until it has been served.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -367,30 +437,43 @@ struct Request {
     int found = 0;
     u64 sieve_sum = 0;
     double ms = 0;
+    std::vector<u64> vals;   // decide requests: repeat-0 per-point sums on [p_begin, p_end)
     std::vector<u32> verts, times;
+};
+
+struct Lane {
+    tmotif_server *srv = nullptr;
+    bool large = false;
+    cudaStream_t st = nullptr, prep_st = nullptr;  // layer launches; job preparation
+    std::unique_ptr<Scheduler> sched;
+    Workspace finish_ws;  // arc gathering for extraction's final DFS
+    std::thread worker;
+    std::deque<Request *> pending;  // submitted to this lane, not yet taken (server mutex)
+    Request *holder = nullptr;      // large lane: the request now running
+
+    enum { NJ_JOB, NJ_NONE, NJ_FAILED };
+    void complete(Request *r, Status s);
+    int next_job(Request *r, std::unique_ptr<SJob> *out);
+    void finish_extract(Request *r);
+    void run();
 };
 
 }  // namespace
 
 struct tmotif_server {
-    size_t budget = 0;
     int device = 0;
-    cudaStream_t st = nullptr, prep_st = nullptr;  // layer launches; job preparation
-    std::unique_ptr<Scheduler> sched;
-    Workspace finish_ws;  // arc gathering for extraction's final DFS
-    std::thread worker;
+    std::unique_ptr<Budget> budget;
+    Lane lanes[2];  // 0: small requests; 1: large requests
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv;       // work submitted
     std::condition_variable done_cv;  // a request finished (tmotif_wait)
-    std::deque<Request *> pending;           // submitted, not yet admitted
     std::map<u64, std::unique_ptr<Request>> reqs;
     std::atomic<bool> stop{false};
+    std::atomic<bool> large_waiting{false};  // the large lane waits for memory
     u64 next_ticket = 1;
-    Request *large_holder = nullptr;  // the large request now running, if any
 
     void complete(Request *r, Status s)
     {
-        if (large_holder == r) large_holder = nullptr;
         std::lock_guard<std::mutex> lock(mu);
         if (!s.ok()) {
             r->code = s.code;
@@ -400,180 +483,208 @@ struct tmotif_server {
         r->done = true;
         done_cv.notify_all();
     }
+};
 
-    // Make the next job of a request (its decision, or its next probe).
-    // Returns false when the request needs no more jobs.
-    bool next_job(Request *r, std::unique_ptr<SJob> *out)
-    {
-        auto sj = std::make_unique<SJob>();
-        sj->owner = r->ticket;
-        sj->job.g = r->g;
-        if (!r->is_extract) {
-            sj->job.q = r->q;
-            *out = std::move(sj);
-            return true;
-        }
-        if (!r->halving) {
-            QuerySpec sub;
-            u32 rep = 0;
-            const std::vector<uint8_t> *mask = nullptr;
-            if (!r->lex.next(&sub, &rep, &mask)) return false;
-            sj->job.q = sub;
-            sj->job.localize = true;
-            sj->job.rep_offset = rep;
-            if (mask) {
-                Status s = sched->set_mask(*sj, *mask);
-                if (!s.ok()) {
-                    complete(r, s);
-                    return false;
-                }
-            }
-            *out = std::move(sj);
-            return true;
-        }
-        QuerySpec pq;
-        if (!r->ex.next_probe(&pq)) return false;
-        sj->job.q = pq;
-        if (r->ex.stage == ExtractState::PROBING) {
-            Status s = r->ex.maybe_compact(*r->g, finish_ws, prep_st);
-            if (s.ok()) s = sched->set_mask(*sj, r->ex.alive);
+namespace {
+
+void Lane::complete(Request *r, Status s)
+{
+    if (holder == r) holder = nullptr;
+    srv->complete(r, s);
+}
+
+// Make the next job of a request (its decision, or its next probe):
+// NJ_JOB, NJ_NONE when the request needs no more jobs, or NJ_FAILED when it
+// failed and was completed with the error (the caller must not touch it).
+int Lane::next_job(Request *r, std::unique_ptr<SJob> *out)
+{
+    auto sj = std::make_unique<SJob>();
+    sj->owner = r->ticket;
+    sj->job.g = r->g;
+    if (!r->is_extract) {
+        sj->job.q = r->q;
+        *out = std::move(sj);
+        return NJ_JOB;
+    }
+    if (!r->halving) {
+        QuerySpec sub;
+        u32 rep = 0;
+        const std::vector<uint8_t> *mask = nullptr;
+        if (!r->lex.next(&sub, &rep, &mask)) return NJ_NONE;
+        sj->job.q = sub;
+        sj->job.localize = true;
+        sj->job.rep_offset = rep;
+        if (mask) {
+            Status s = sched->set_mask(*sj, *mask);
             if (!s.ok()) {
                 complete(r, s);
-                return false;
+                return NJ_FAILED;
             }
-            sj->job.g = r->ex.current(*r->g);
         }
         *out = std::move(sj);
-        return true;
+        return NJ_JOB;
     }
-
-    void finish_extract(Request *r)
-    {
-        r->verts.assign(r->q.k, 0);
-        r->times.assign(r->q.k, 0);
-        if (!r->halving) {
-            r->found = r->lex.found ? 1 : 0;
-            if (r->lex.found) {
-                r->verts = r->lex.verts;
-                r->times = r->lex.times;
-            }
-            complete(r, Status());
-            return;
+    QuerySpec pq;
+    if (!r->ex.next_probe(&pq)) return NJ_NONE;
+    sj->job.q = pq;
+    if (r->ex.stage == ExtractState::PROBING) {
+        Status s = r->ex.maybe_compact(*r->g, finish_ws, prep_st);
+        if (s.ok()) s = sched->set_mask(*sj, r->ex.alive);
+        if (!s.ok()) {
+            complete(r, s);
+            return NJ_FAILED;
         }
-        Status s;
-        if (r->ex.stage == ExtractState::SHRUNK)
-            s = extract_finish(*r->ex.current(*r->g), finish_ws, prep_st, sched->prof, r->ex, r->verts.data(),
-                               r->times.data(), &r->found);
-        else
-            r->found = 0;
-        complete(r, s);
+        sj->job.g = r->ex.current(*r->g);
     }
+    *out = std::move(sj);
+    return NJ_JOB;
+}
 
-    void run()
-    {
-        cudaSetDevice(device);
-        std::deque<std::pair<Request *, std::unique_ptr<SJob>>> waiting;  // admission queue (FIFO)
-        std::vector<std::unique_ptr<SJob>> done;
-        auto take_pending = [&]() {
-            std::lock_guard<std::mutex> lock(mu);
-            while (!pending.empty()) {
-                Request *r = pending.front();
-                pending.pop_front();
-                waiting.push_back({r, nullptr});
+void Lane::finish_extract(Request *r)
+{
+    r->verts.assign(r->q.k, 0);
+    r->times.assign(r->q.k, 0);
+    if (!r->halving) {
+        r->found = r->lex.found ? 1 : 0;
+        if (r->lex.found) {
+            r->verts = r->lex.verts;
+            r->times = r->lex.times;
+        }
+        complete(r, Status());
+        return;
+    }
+    Status s;
+    if (r->ex.stage == ExtractState::SHRUNK)
+        s = extract_finish(*r->ex.current(*r->g), finish_ws, prep_st, sched->prof, r->ex, r->verts.data(),
+                           r->times.data(), &r->found);
+    else
+        r->found = 0;
+    complete(r, s);
+}
+
+void Lane::run()
+{
+    cudaSetDevice(srv->device);
+    std::deque<std::pair<Request *, std::unique_ptr<SJob>>> waiting;  // admission queue (FIFO)
+    std::vector<std::unique_ptr<SJob>> done;
+    auto take_pending = [&]() {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        while (!pending.empty()) {
+            Request *r = pending.front();
+            pending.pop_front();
+            waiting.push_back({r, nullptr});
+        }
+    };
+    // admit in arrival order while the memory budget allows; the large lane
+    // runs one request at a time
+    auto admit_waiting = [&]() {
+        take_pending();
+        for (auto it = waiting.begin(); it != waiting.end();) {
+            Request *r = it->first;
+            std::unique_ptr<SJob> &sj = it->second;
+            if (large && holder && holder != r) {
+                ++it;
+                continue;
             }
-        };
-        // admit in arrival order while the memory budget allows; a large
-        // request waits for the large slot, and smaller ones behind it may
-        // go first
-        auto admit_waiting = [&]() {
-            take_pending();
-            for (auto it = waiting.begin(); it != waiting.end();) {
-                Request *r = it->first;
-                std::unique_ptr<SJob> &sj = it->second;
-                if (r->large && large_holder && large_holder != r) {
-                    ++it;
-                    continue;
-                }
-                if (!sj && !next_job(r, &sj)) {  // nothing to run (error already recorded)
-                    if (!r->done) finish_extract(r);
+            if (!large && srv->large_waiting.load()) break;  // leave the memory to the large lane
+            if (!sj) {
+                const int nj = next_job(r, &sj);
+                if (nj != NJ_JOB) {  // nothing left to run, or failed and completed
+                    if (nj == NJ_NONE) finish_extract(r);
                     it = waiting.erase(it);
                     continue;
                 }
-                const size_t need = job_estimate(*sj->job.g, sj->job.q);
-                if (!sched->idle() && !sched->fits(need)) break;
-                if (r->large) large_holder = r;
-                Status s = sched->admit(std::move(sj), need, &done);
-                it = waiting.erase(it);
-                if (!s.ok()) complete(r, s);
             }
-        };
-        while (!stop.load()) {
+            const size_t need = job_estimate(*sj->job.g, sj->job.q);
+            if (!sched->room() || !srv->budget->try_take(need)) {
+                if (large) srv->large_waiting.store(true);
+                break;
+            }
+            if (large) {
+                holder = r;
+                srv->large_waiting.store(false);
+            }
+            Status s = sched->admit(std::move(sj), need, &done);
+            it = waiting.erase(it);
+            if (!s.ok()) complete(r, s);
+        }
+    };
+    while (!srv->stop.load()) {
+        {
+            std::unique_lock<std::mutex> lock(srv->mu);
+            if (pending.empty() && waiting.empty() && sched->idle())
+                srv->cv.wait_for(lock, std::chrono::milliseconds(2));
+        }
+        if (sched->idle()) admit_waiting();
+        if (!sched->idle()) {
+            // jobs admitted while this step's layers run are prepared
+            // beside them (prep stream) and join after the step
+            Status s = sched->step(&done, [&] {
+                admit_waiting();
+                return Status();
+            });
+            if (!s.ok()) {  // fail every request of this lane in flight
+                std::lock_guard<std::mutex> lock(srv->mu);
+                const std::string msg = tmotif_last_error();
+                for (auto &kv : srv->reqs)
+                    if (!kv.second->done && kv.second->large == large) {
+                        kv.second->code = s.code;
+                        kv.second->err = msg;
+                        kv.second->done = true;
+                    }
+                if (large) srv->large_waiting.store(false);
+                srv->done_cv.notify_all();
+                return;
+            }
+        } else if (!waiting.empty()) {
+            // waiting for memory the other lane holds
+            std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
+        for (auto &sj : done) {
+            Request *r = nullptr;
             {
-                std::unique_lock<std::mutex> lock(mu);
-                if (pending.empty() && waiting.empty() && sched->idle())
-                    cv.wait_for(lock, std::chrono::milliseconds(2));
+                std::lock_guard<std::mutex> lock(srv->mu);
+                auto it = srv->reqs.find(sj->owner);
+                if (it != srv->reqs.end()) r = it->second.get();
             }
-            if (sched->idle()) admit_waiting();
-            if (!sched->idle()) {
-                // jobs admitted while this step's layers run are prepared
-                // beside them (prep stream) and join after the step
-                Status s = sched->step(&done, [&] {
-                    admit_waiting();
-                    return Status();
-                });
-                if (!s.ok()) {  // fail every request in flight
-                    std::lock_guard<std::mutex> lock(mu);
-                    for (auto &kv : reqs)
-                        if (!kv.second->done) {
-                            kv.second->code = s.code;
-                            kv.second->done = true;
-                        }
-                    done_cv.notify_all();
-                    return;
-                }
+            if (!r) continue;
+            if (!r->is_extract) {
+                r->found = sj->job.found;
+                r->sieve_sum = sj->job.sieve_sum;
+                r->vals = std::move(sj->job.vals);
+                complete(r, Status());
+                continue;
             }
-            for (auto &sj : done) {
-                Request *r = nullptr;
-                {
-                    std::lock_guard<std::mutex> lock(mu);
-                    auto it = reqs.find(sj->owner);
-                    if (it != reqs.end()) r = it->second.get();
-                }
-                if (!r) continue;
-                if (!r->is_extract) {
-                    r->found = sj->job.found;
-                    r->sieve_sum = sj->job.sieve_sum;
-                    complete(r, Status());
+            if (!r->halving) {
+                u32 best = NONE, a = 0, b = 0, t = 0;
+                Status s = sj->job.done && sj->job.mf == 0 ? Status() : job_first_arc(sj->job, &best, &a, &b, &t);
+                if (!s.ok()) {
+                    complete(r, s);
                     continue;
                 }
-                if (!r->halving) {
-                    u32 best = NONE, a = 0, b = 0, t = 0;
-                    Status s = sj->job.done && sj->job.mf == 0 ? Status() : job_first_arc(sj->job, &best, &a, &b, &t);
-                    if (!s.ok()) {
-                        complete(r, s);
-                        continue;
-                    }
-                    r->lex.result(best, a, b, t);
-                    if (r->lex.done) {
-                        finish_extract(r);
-                        continue;
-                    }
-                } else {
-                    r->ex.result(sj->job.found != 0);
-                    if (r->ex.stage == ExtractState::NOT_FOUND) {
-                        finish_extract(r);
-                        continue;
-                    }
+                r->lex.result(best, a, b, t);
+                if (r->lex.done) {
+                    finish_extract(r);
+                    continue;
                 }
-                // next level/probe joins the front of the admission queue (the request keeps its turn)
-                std::unique_ptr<SJob> nj;
-                if (next_job(r, &nj)) waiting.push_front({r, std::move(nj)});
-                else if (!r->done) finish_extract(r);
+            } else {
+                r->ex.result(sj->job.found != 0);
+                if (r->ex.stage == ExtractState::NOT_FOUND) {
+                    finish_extract(r);
+                    continue;
+                }
             }
-            done.clear();
+            // next level/probe joins the front of the admission queue (the request keeps its turn)
+            std::unique_ptr<SJob> nj;
+            const int st = next_job(r, &nj);
+            if (st == NJ_JOB) waiting.push_front({r, std::move(nj)});
+            else if (st == NJ_NONE) finish_extract(r);
         }
+        done.clear();
     }
-};
+}
+
+}  // namespace
 
 extern "C" int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *out)
 {
@@ -582,16 +693,39 @@ extern "C" int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *ou
     try {
         auto s = std::make_unique<tmotif_server>();
         if (cudaGetDevice(&s->device) != cudaSuccess) return fail(TMOTIF_ERR_CUDA, "no CUDA device").code;
-        s->budget = hbm_budget_bytes ? hbm_budget_bytes : default_budget();
-        cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->prep_st, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return cuda_fail(e, "server stream").code;
-        s->sched = std::make_unique<Scheduler>(s->st, s->budget, s->prep_st);
-        Status st = s->sched->init();
-        if (!st.ok()) return st.code;
-        s->finish_ws.set_stream(s->prep_st);
-        tmotif_server *raw = s.get();
-        s->worker = std::thread([raw] { raw->run(); });
+        s->budget = std::make_unique<Budget>(hbm_budget_bytes ? hbm_budget_bytes : default_budget());
+        int least = 0, greatest = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+            Lane &l = s->lanes[i];
+            l.srv = s.get();
+            l.large = i == 1;
+            const int prio = l.large ? least : greatest;
+            e = cudaStreamCreateWithPriority(&l.st, cudaStreamNonBlocking, prio);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&l.prep_st, cudaStreamNonBlocking, prio);
+        }
+        if (e != cudaSuccess) {
+            for (Lane &l : s->lanes)
+                for (cudaStream_t st : {l.st, l.prep_st})
+                    if (st) cudaStreamDestroy(st);
+            return cuda_fail(e, "server streams").code;
+        }
+        for (Lane &l : s->lanes) {
+            l.sched = std::make_unique<Scheduler>(l.st, s->budget.get(), l.prep_st);
+            l.sched->set_whole_jobs(l.large);
+            Status st = l.sched->init();
+            if (!st.ok()) {
+                for (Lane &m : s->lanes)
+                    for (cudaStream_t x : {m.st, m.prep_st})
+                        if (x) cudaStreamDestroy(x);
+                return st.code;
+            }
+            l.finish_ws.set_stream(l.prep_st);
+        }
+        for (Lane &l : s->lanes) {
+            Lane *raw = &l;
+            l.worker = std::thread([raw] { raw->run(); });
+        }
         *out = s.release();
         return TMOTIF_OK;
     } catch (const std::bad_alloc &) {
@@ -611,7 +745,7 @@ extern "C" int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_q
             return fail(TMOTIF_ERR_UNSUPPORTED, "the server takes no static preprocessing").code;
         if (is_extract && (r->q.p_begin != 0 || r->q.p_end != (1ull << r->q.k)))
             return fail(TMOTIF_ERR_INVALID, "extraction needs the full point range").code;
-        if (job_estimate(*g, r->q) > s->budget)
+        if (job_estimate(*g, r->q) > s->budget->budget)
             return fail(TMOTIF_ERR_BUSY, "request needs more device memory than the server budget").code;
         r->g = g;
         r->is_extract = is_extract != 0;
@@ -623,9 +757,9 @@ extern "C" int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_q
         std::lock_guard<std::mutex> lock(s->mu);
         r->ticket = s->next_ticket++;
         *ticket = r->ticket;
-        s->pending.push_back(r.get());
+        s->lanes[r->large ? 1 : 0].pending.push_back(r.get());
         s->reqs[r->ticket] = std::move(r);
-        s->cv.notify_one();
+        s->cv.notify_all();
         return TMOTIF_OK;
     } catch (const std::bad_alloc &) {
         return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
@@ -643,6 +777,11 @@ static int take_result(tmotif_server_t s, std::map<u64, std::unique_ptr<Request>
         out->found = r->found;
         out->sieve_sum = r->sieve_sum;
         out->ms = r->ms;
+        if (out->per_point && !r->is_extract && code == TMOTIF_OK) {
+            const u64 npts = r->q.p_end - r->q.p_begin;
+            if (r->vals.size() == npts) std::memcpy(out->per_point, r->vals.data(), npts * sizeof(u64));
+            else std::memset(out->per_point, 0, npts * sizeof(u64));
+        }
     }
     if (r->is_extract && r->found) {
         if (verts) std::copy(r->verts.begin(), r->verts.begin() + r->q.k, verts);
@@ -682,14 +821,18 @@ extern "C" void tmotif_server_destroy(tmotif_server_t s)
     if (!s) return;
     s->stop.store(true);
     s->cv.notify_all();
-    if (s->worker.joinable()) s->worker.join();
-    s->sched.reset();
-    s->finish_ws.release();
-    s->reqs.clear();  // extraction subgraphs free on the prep stream
-    for (cudaStream_t st : {s->st, s->prep_st})
-        if (st) {
-            cudaStreamSynchronize(st);
-            cudaStreamDestroy(st);
-        }
+    for (Lane &l : s->lanes)
+        if (l.worker.joinable()) l.worker.join();
+    for (Lane &l : s->lanes) {
+        l.sched.reset();
+        l.finish_ws.release();
+    }
+    s->reqs.clear();  // extraction subgraphs free on their lane's prep stream
+    for (Lane &l : s->lanes)
+        for (cudaStream_t st : {l.st, l.prep_st})
+            if (st) {
+                cudaStreamSynchronize(st);
+                cudaStreamDestroy(st);
+            }
     delete s;
 }

@@ -28,6 +28,10 @@
 
 namespace tmo {
 
+// The device status word (TM_STATUS_* bits; see status_word): kernels of this
+// file name it directly, kernels elsewhere get its address in their params.
+static __device__ u32 g_status_word;
+
 // ---------------------------------------------------------------------------
 // Per-query preparation
 // ---------------------------------------------------------------------------
@@ -223,11 +227,12 @@ __global__ void k_compact(u64 m, const u32 *src, const u32 *dst, const u32 *time
 }
 
 // In-segment [seg_lo[v], seg_hi[v]) of each destination in the filtered arcs.
-__global__ void k_segments(u64 mf, const u32 *f_dst, u32 *seg_lo, u32 *seg_hi)
+__global__ void k_segments(u64 mf, const u32 *f_dst, u32 *seg_lo, u32 *seg_hi, u32 n)
 {
     u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= mf) return;
     u32 d = f_dst[e];
+    if (!TM_IN(d, n, &g_status_word)) return;
     if (e == 0 || f_dst[e - 1] != d) seg_lo[d] = (u32)e;
     if (e + 1 == mf || f_dst[e + 1] != d) seg_hi[d] = (u32)(e + 1);
 }
@@ -235,12 +240,14 @@ __global__ void k_segments(u64 mf, const u32 *f_dst, u32 *seg_lo, u32 *seg_hi)
 // pos[e] = last in-arc of src(e) with time < time(e) (strictly increasing times,
 // Sec. 4), or NONE; marks that arc as a checkpoint.
 __global__ void k_pos(u64 mf, const u32 *f_src, const u32 *f_time, const u32 *seg_lo, const u32 *seg_hi,
-                      u32 *pos, u32 *mark)
+                      u32 *pos, u32 *mark, u32 n)
 {
     u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= mf) return;
     u32 a = f_src[e], t = f_time[e];
+    if (!TM_IN(a, n, &g_status_word)) return;
     u32 lo = seg_lo[a], hi = seg_hi[a];
+    if (!TM_IN(hi, mf + 1, &g_status_word) || !TM_IN(lo, (u64)hi + 1, &g_status_word)) return;
     // first index in [lo, hi) with time >= t
     while (lo < hi) {
         u32 mid = lo + ((hi - lo) >> 1);
@@ -255,15 +262,21 @@ __global__ void k_pos(u64 mf, const u32 *f_src, const u32 *f_time, const u32 *se
     pos[e] = p;
 }
 
-// mark[] holds exclusive checkpoint numbers (length mf+1).
-__global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in, u32 *cp_out)
+// mark[] holds exclusive checkpoint numbers (length mf+1).  With rec (the
+// staged layer form), also each arc's record {dst, cp_in, cp_out, src}.
+__global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in, u32 *cp_out, const u32 *f_src,
+                              const u32 *f_dst, uint4 *rec)
 {
     u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= mf) return;
     u32 p = pos[e];
-    cp_in[e] = (p == NONE) ? NONE : ck[p];
+    if (p != NONE && !TM_IN(p, mf, &g_status_word)) return;
+    const u32 ci = (p == NONE) ? NONE : ck[p];
     u32 c = ck[e];
-    cp_out[e] = (ck[e + 1] != c) ? c : NONE;
+    const u32 co = (ck[e + 1] != c) ? c : NONE;
+    cp_in[e] = ci;
+    cp_out[e] = co;
+    if (rec) rec[e] = make_uint4(f_dst[e], ci, co, f_src[e]);
 }
 
 // ---------------------------------------------------------------------------
@@ -287,15 +300,19 @@ __global__ void k_wtab(u32 k, u32 L, u64 p0, QueryKeys keys, u64 *wtab)
 // table once per slot and each lane's product is 16 table loads.
 __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L, const u32 *color,
                                               const u32 *slot_begin, const u32 *slot_count, QueryKeys keys,
-                                              const u64 *wtab, u64 *x)
+                                              const u64 *wtab, u64 *x, u32 n, u32 num_colors, u32 k)
 {
     __shared__ __align__(2048) u64 tabs[8][256];  // tables on 2 KB boundaries
     u64 *tab = tabs[threadIdx.x >> 5];
     const int tt = threadIdx.x & 31;
     const u64 v = (u64)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (v >= n_act) return;  // whole warp leaves together
-    const u32 u = list[v], c = color[u];
+    const u32 u = list[v];
+    if (!TM_IN(u, n, &g_status_word)) return;
+    const u32 c = color[u];
+    if (!TM_IN(c, num_colors, &g_status_word)) return;
     const u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
+    if (!TM_IN(d1, k + 1, &g_status_word)) return;
     u64 s[4] = {0, 0, 0, 0};  // lanes tt, tt + 32, tt + 64, tt + 96 (L <= 128)
     for (u32 d = d0; d < d1; d++) {
         __syncwarp();
@@ -374,6 +391,40 @@ __global__ void __launch_bounds__(256, MINB) k_layer_mb(LayerParams one)
     layer_kernel<T, TAB, false, LPT, INNER>(one, nullptr, nullptr, 0);
 }
 
+// The staged form (variant 4 of the warp-team classes L = 32, 64, 128;
+// single-job launches with a team counter): the same team body with each
+// team's arc metadata staged in shared memory by bulk copies.  Dynamic shared
+// memory: the eight teams' staging areas, then their tables on 2 KB
+// boundaries (STAGED_SMEM bytes).
+constexpr size_t STAGED_SMEM = 8 * sizeof(TeamStage) + 8 * 2048 + 2048;
+
+template <int LPT, bool INNER>
+__global__ void __launch_bounds__(256) k_layer_staged(LayerParams one)
+{
+    extern __shared__ __align__(16) u64 smem[];
+    TeamStage *ts = (TeamStage *)smem + threadIdx.x / 32;
+    u64 *after = (u64 *)((TeamStage *)smem + 8);
+    const u32 sa = smem_u32(after);
+    u64 *tab = after + (((2048u - (sa & 2047u)) & 2047u) >> 3) + (size_t)(threadIdx.x / 32) * 256;
+    if (threadIdx.x % 32 == 0) stage_init(ts);
+    __syncwarp();
+    StageState ss;
+    const u64 total = one.n_chunks * one.lane_groups;
+    for (;;) {
+        unsigned long long t = 0;
+        if (threadIdx.x % 32 == 0) t = atomicAdd(one.queue, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        layer_team<32, true, LPT, false, INNER, true>(one, t, tab, ts, &ss);
+    }
+    // a team whose wait ran out may still have copies in flight into its
+    // buffers: wait for them (each wait bounded) before the block's shared
+    // memory is released
+    if (ss.broken)
+        for (int b = 0; b < 2; b++)
+            if (ss.pending & (1u << b)) stage_wait(ts, b, (ss.phase >> b) & 1u);
+}
+
 // out[lane] = XOR over chunks of partial[chunk * L + lane]; blockDim.x = L,
 // gridDim.x = chunk slices (each XORs its slice, then one atomic per lane).
 __global__ void k_reduce_partials(const u64 *partial, u64 n_chunks, u32 L, u64 *out)
@@ -398,7 +449,9 @@ __global__ void k_gf_mul(const u64 *a, const u64 *b, u64 *out, u64 n)
 // Throughput probe of the two product forms on register-resident data: every
 // warp runs `iters` rounds; a round multiplies 64 lanes (2 per thread) by one
 // multiplier, which changes every round.  method 0: register multiply;
-// method 1: shared-memory nibble table built by the warp, then looked up.
+// method 1: shared-memory nibble table built by the warp, then looked up for
+// 64 lanes (2 per thread); method 2: the same table for 128 lanes (4 per
+// thread).
 template <int METHOD>
 __global__ void __launch_bounds__(256) k_gf_probe(u32 iters, u64 seed, u64 *sink)
 {
@@ -406,7 +459,6 @@ __global__ void __launch_bounds__(256) k_gf_probe(u32 iters, u64 seed, u64 *sink
     u64 *tab = tabs[threadIdx.x >> 5];
     const int tt = threadIdx.x & 31;
     constexpr int LPT = METHOD == 2 ? 4 : 2;  // lanes per thread
-    const NibbleMuls nm = nibble_muls((u32)(iters != 0));
     u64 a[LPT], acc[LPT];
     a[0] = mix64(seed + blockIdx.x * 256 + threadIdx.x);
 #pragma unroll
@@ -423,7 +475,7 @@ __global__ void __launch_bounds__(256) k_gf_probe(u32 iters, u64 seed, u64 *sink
             gf_table_build(tab, y, tt, 32);
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < LPT; i++) acc[i] ^= METHOD == 3 ? gf_table_mul_m(tab, a[i], nm) : gf_table_mul(tab, a[i]);
+            for (int i = 0; i < LPT; i++) acc[i] ^= gf_table_mul(tab, a[i]);
         }
 #pragma unroll
         for (int i = 0; i < LPT; i++) a[i] += acc[(i + 1) % LPT];
@@ -451,8 +503,7 @@ Status gf_probe(int method, u32 iters, double *ms, u64 *products)
         const u32 n = pass ? iters : 4;
         if (method == 0) k_gf_probe<0><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
         else if (method == 1) k_gf_probe<1><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
-        else if (method == 2) k_gf_probe<2><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
-        else k_gf_probe<3><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
+        else k_gf_probe<2><<<blocks, 256>>>(n, 1 + 6 * pass, sink);
     }
     cudaEventRecord(b);
     cudaError_t e = cudaEventSynchronize(b);
@@ -465,6 +516,49 @@ Status gf_probe(int method, u32 iters, double *ms, u64 *products)
     TM_CUDA(cudaGetLastError());
     *ms = f;
     *products = (u64)blocks * 256 * (method == 2 ? 4 : 2) * iters;
+    return Status();
+}
+
+// ---------------------------------------------------------------------------
+// Device status word
+// ---------------------------------------------------------------------------
+static std::mutex g_status_mu;
+static u32 *g_status_ptr[256];  // device address of g_status_word, per device
+
+Status status_word(u32 **p)
+{
+    int dev = 0;
+    TM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(TMOTIF_ERR_UNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    if (!g_status_ptr[dev]) {
+        void *a = nullptr;
+        TM_CUDA(cudaGetSymbolAddress(&a, g_status_word));
+        g_status_ptr[dev] = (u32 *)a;
+    }
+    *p = g_status_ptr[dev];
+    return Status();
+}
+
+__global__ void k_status_take(u32 *word, u32 *out) { *out = atomicExch(word, 0u); }
+
+Status status_take_enqueue(cudaStream_t st, u32 *d_slot, u32 *h_slot)
+{
+    u32 *word = nullptr;
+    TM_TRY(status_word(&word));
+    k_status_take<<<1, 1, 0, st>>>(word, d_slot);
+    TM_CUDA(cudaGetLastError());
+    TM_CUDA(cudaMemcpyAsync(h_slot, d_slot, 4, cudaMemcpyDeviceToHost, st));
+    return Status();
+}
+
+Status status_result(u32 taken)
+{
+    if (taken & TM_STATUS_STAGE_TIMEOUT)
+        return fail(TMOTIF_ERR_TIMEOUT, "a staged layer launch's bulk copy did not complete within its wait limit");
+    if (taken & TM_STATUS_BOUNDS)
+        return fail(TMOTIF_ERR_INVALID, "a device bounds check failed (the access was skipped; results are invalid)");
+    if (taken) return fail(TMOTIF_ERR_CUDA, "unknown device status bits");
     return Status();
 }
 
@@ -572,7 +666,8 @@ Status job_prep(Job &j)
         const u64 mf = j.mf;
         TM_TRY(w.f_src.reserve(mf * 4));
         TM_TRY(w.f_dst.reserve(mf * 4));
-        TM_TRY(w.f_time.reserve(mf * 4));
+        TM_TRY(w.f_time.reserve((mf + 4) * 4));  // the staged form copies times in 16-byte units
+        TM_TRY(w.rec.reserve(mf * 16));
         TM_TRY(w.pos.reserve(mf * 4));
         TM_TRY(w.mark.reserve((mf + 1) * 4));
         TM_TRY(w.cp_in.reserve(mf * 4));
@@ -584,14 +679,16 @@ Status job_prep(Job &j)
         TM_CUDA(cudaMemsetAsync(w.seg_lo.p, 0, (u64)n * 4, st));
         TM_CUDA(cudaMemsetAsync(w.seg_hi.p, 0, (u64)n * 4, st));
         TM_CUDA(cudaMemsetAsync(w.mark.p, 0, (mf + 1) * 4, st));
-        k_segments<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_dst.as<u32>(), w.seg_lo.as<u32>(), w.seg_hi.as<u32>());
+        k_segments<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_dst.as<u32>(), w.seg_lo.as<u32>(), w.seg_hi.as<u32>(),
+                                                      n);
         k_pos<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_src.as<u32>(), w.f_time.as<u32>(), w.seg_lo.as<u32>(),
-                                                 w.seg_hi.as<u32>(), w.pos.as<u32>(), w.mark.as<u32>());
+                                                 w.seg_hi.as<u32>(), w.pos.as<u32>(), w.mark.as<u32>(), n);
         *launches += 2;
         TM_CUDA(cudaGetLastError());
         TM_TRY(exclusive_scan_on(st, w.block_sums, w.mark.as<u32>(), mf + 1, d_cnt + 1, launches));
         k_checkpoints<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.pos.as<u32>(), w.mark.as<u32>(), w.cp_in.as<u32>(),
-                                                         w.cp_out.as<u32>());
+                                                         w.cp_out.as<u32>(), w.f_src.as<u32>(), w.f_dst.as<u32>(),
+                                                         w.rec.as<uint4>());
         *launches += 1;
         TM_CUDA(cudaGetLastError());
         TM_CUDA(cudaMemcpyAsync(h_cnt + 1, d_cnt + 1, 4, cudaMemcpyDeviceToHost, st));
@@ -627,6 +724,7 @@ Status job_prep(Job &j)
     j.variant = 0;
     {  // the launch shape pinned or tuned for this graph and lane width, else
        // one tuned on this device for a layer of about the same size
+        std::lock_guard<std::mutex> lock(layer_tune_mutex());
         auto it = g.layer_tune.find(L);
         std::pair<u32, u32> shape;
         if (it != g.layer_tune.end()) {
@@ -667,7 +765,7 @@ Status job_batch_begin(Job &j)
     if (j.n_act)
         k_coef<<<(unsigned)((j.n_act + 7) / 8), 256, 0, st>>>((u32)j.n_act, w.act_list.as<u32>(), L, g.d_color,
                                                                w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
-                                                               w.wtab.as<u64>(), w.x.as<u64>());
+                                                               w.wtab.as<u64>(), w.x.as<u64>(), g.n, g.num_colors, k);
     j.prof->stats.launches += 2;
     TM_CUDA(cudaGetLastError());
     TM_CUDA(cudaMemsetAsync(w.out.p, 0, L * 8, st));
@@ -704,6 +802,11 @@ LayerParams job_layer_params(const Job &j)
     lp.end = j.q.end;
     lp.T = j.T;
     lp.queue = w.queue.as<unsigned long long>();
+    lp.rec = w.rec.as<uint4>();
+    lp.n_vert = j.g->n;
+    lp.n_cp = j.ncp;
+    u32 *status = nullptr;
+    if (status_word(&status).ok()) lp.status = status;
     return lp;
 }
 
@@ -756,6 +859,37 @@ static Status launch_layer_f(cudaStream_t st, const LayerParams &one, const Laye
     return Status();
 }
 
+// One launch of the staged form (single job, warp teams of LPT lanes per
+// thread): resident blocks only, fed from the team counter.
+template <int LPT, bool INNER>
+static Status launch_staged_f(cudaStream_t st, const LayerParams &one, u64 teams)
+{
+    if (!one.queue || !one.rec) return fail(TMOTIF_ERR_UNSUPPORTED, "the staged layer form needs a job workspace");
+    // bulk copies start on 16-byte boundaries: the arrays' bases must be aligned
+    if (((uintptr_t)one.rec | (uintptr_t)one.time) & 15u)
+        return fail(TMOTIF_ERR_UNSUPPORTED, "the staged layer form needs 16-byte aligned arc arrays");
+    const int threads = 256;
+    const u64 blocks = (teams + 7) / 8;
+    if (!blocks) return Status();
+    static const int per_sm = [] {
+        int nb = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_layer_staged<LPT, INNER>, 256,
+                                                                            STAGED_SMEM);
+        return (e == cudaSuccess && nb > 0) ? nb : 1;
+    }();
+    const unsigned grid = (unsigned)std::min<u64>(blocks, (u64)per_sm * sm_count());
+    TM_CUDA(cudaMemsetAsync(one.queue, 0, sizeof(unsigned long long), st));
+    k_layer_staged<LPT, INNER><<<grid, threads, STAGED_SMEM, st>>>(one);
+    return Status();
+}
+
+template <int LPT>
+static Status launch_staged(cudaStream_t st, const LayerParams &one, u64 teams)
+{
+    if (one.ell > 2 && one.ell < one.k) return launch_staged_f<LPT, true>(st, one, teams);
+    return launch_staged_f<LPT, false>(st, one, teams);
+}
+
 // Single-job launches of inner layers (2 < l < k) take the INNER form.
 template <int T, bool TAB, int LPT, int MINB>
 static Status launch_layer_t(cudaStream_t st, const LayerParams &one, const LayerParams *jobs,
@@ -787,6 +921,11 @@ static Status launch_layer_v(cudaStream_t st, u32 variant, const LayerParams &on
 static Status launch_layer_class(cudaStream_t st, u32 L, u32 variant, const LayerParams &one,
                                  const LayerParams *jobs, const u64 *prefix, u32 njobs, u64 teams)
 {
+    if (variant == 4 && njobs == 0) {  // the staged form of the warp-team classes
+        if (L == 32) return launch_staged<1>(st, one, teams);
+        if (L == 64) return launch_staged<2>(st, one, teams);
+        if (L == 128) return launch_staged<4>(st, one, teams);
+    }
     switch (L) {
         case 4: return launch_layer_v<2, false, 2>(st, variant, one, jobs, prefix, njobs, teams);
         case 8: return launch_layer_v<4, false, 2>(st, variant, one, jobs, prefix, njobs, teams);
@@ -888,6 +1027,12 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
 // Shapes the autotuner found, per device, lane width and layer size class
 // (floor(log2(arcs))), shared by every graph of the process.
 static std::mutex g_tune_mu;
+
+std::mutex &layer_tune_mutex()
+{
+    static std::mutex mu;
+    return mu;
+}
 static std::map<std::tuple<int, u32, u32>, std::pair<u32, u32>> g_tuned;
 
 static std::tuple<int, u32, u32> tune_key(u32 L, u64 mf)
@@ -928,9 +1073,13 @@ static Status tune_layer(Job &j)
         float ms;
     };
     std::vector<Cand> cands;
+    std::vector<u32> variants{0};
+    if (j.L == 16) variants = {0, 1, 2};
+    if (j.L == 32) variants = {0, 3, 4};
+    if (j.L == 64) variants = {0, 1, 2, 4};
+    if (j.L == 128) variants = {0, 1, 4};
     for (u32 c : {64u, 128u, 256u, 512u, 1024u})
-        for (u32 v = 0; v < (j.L == 32 ? 4u : ((j.L == 16 || j.L == 64) ? 3u : (j.L == 128 ? 2u : 1u))); v++)
-            if (!(j.L == 32 && (v == 1 || v == 2))) cands.push_back({c, v, 1e30f});
+        for (u32 v : variants) cands.push_back({c, v, 1e30f});
     const size_t nl = 2 * cands.size();
     std::vector<cudaEvent_t> ev(nl + 1, nullptr);
     Status st;
@@ -966,7 +1115,10 @@ static Status tune_layer(Job &j)
     const Cand *best = &cands[0];
     for (const Cand &c : cands)
         if (c.ms < best->ms) best = &c;
-    j.g->layer_tune[j.L] = {best->chunk, best->variant};
+    {
+        std::lock_guard<std::mutex> lock(layer_tune_mutex());
+        j.g->layer_tune[j.L] = {best->chunk, best->variant};
+    }
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tuned[tune_key(j.L, j.mf)] = {best->chunk, best->variant};
@@ -1011,13 +1163,54 @@ void job_readout_finish(Job &j)
     if (j.r >= j.q.repeats) j.done = true;
 }
 
+Status job_enqueue_all(Job &j, bool tune)
+{
+    std::vector<Job *> one{&j};
+    DevBuf unused;
+    const QuerySpec &q = j.q;
+    const u64 nb = (q.p_end - q.p_begin + j.L - 1) / j.L;
+    const u64 total = nb * q.repeats;
+    TM_TRY(ensure_pinned(*j.ws, 64 + total * j.L * 8));
+    j.multi_slot = true;
+    // tune only where a layer is long enough for the shape to matter
+    // (at least 2^22 arc-lanes, tens of microseconds)
+    tune = tune && q.k >= 3 && j.mf * j.L >= (1ull << 22);
+    if (tune) {
+        std::lock_guard<std::mutex> lock(layer_tune_mutex());
+        tune = j.g->layer_tune.find(j.L) == j.g->layer_tune.end();
+    }
+    for (u64 b = 0; b < total; b++) {
+        j.r = (u32)(b / nb);
+        j.p0 = q.p_begin + (b % nb) * j.L;
+        j.batch_seq = b;
+        TM_TRY(job_batch_begin(j));
+        for (; j.ell <= q.k; j.ell++) {
+            if (tune && b == 0 && j.ell == 3) TM_TRY(tune_layer(j));
+            else TM_TRY(launch_layers(j.st, one, unused, nullptr, 0, j.prof));
+        }
+        TM_TRY(job_readout_enqueue(j));
+    }
+    return status_take_enqueue(j.st, j.ws->counters.as<u32>() + 12, (u32 *)((char *)j.ws->host_pinned + 48));
+}
+
+Status job_finish_all(Job &j)
+{
+    TM_TRY(status_result(*(const u32 *)((const char *)j.ws->host_pinned + 48)));
+    const u64 nb = (j.q.p_end - j.q.p_begin + j.L - 1) / j.L;
+    const u64 total = nb * j.q.repeats;
+    j.r = 0;
+    j.p0 = j.q.p_begin;
+    j.qsum = 0;
+    for (u64 b = 0; b < total; b++) {
+        j.batch_seq = b;
+        job_readout_finish(j);
+    }
+    return Status();
+}
+
 Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *found, u64 *sieve_sum,
                     u64 *per_point, double *ms)
 {
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    TM_CUDA(cudaEventCreate(&ev0));
-    TM_CUDA(cudaEventCreate(&ev1));
-    TM_CUDA(cudaEventRecord(ev0, g.stream));
     Job j;
     j.g = &g;
     j.q = q;
@@ -1025,45 +1218,27 @@ Status sieve_decide(Graph &g, const QuerySpec &q, const uint8_t *d_alive, int *f
     j.ws = &g.ws;
     j.st = g.stream;
     j.prof = &g.prof;
-    TM_TRY(job_prep(j));
-    std::vector<Job *> one{&j};
-    DevBuf unused;
-    if (!j.done) {
-        // every lane batch of every repeat back to back; one sync at the end
-        const u64 nb = (q.p_end - q.p_begin + j.L - 1) / j.L;
-        const u64 total = nb * q.repeats;
-        TM_TRY(ensure_pinned(g.ws, 64 + total * j.L * 8));
-        j.multi_slot = true;
-        // tune only where a layer is long enough for the shape to matter
-        // (at least 2^22 arc-lanes, tens of microseconds)
-        const bool tune = q.k >= 3 && j.mf * j.L >= (1ull << 22) && g.layer_tune.find(j.L) == g.layer_tune.end();
-        for (u64 b = 0; b < total; b++) {
-            j.r = (u32)(b / nb);
-            j.p0 = q.p_begin + (b % nb) * j.L;
-            j.batch_seq = b;
-            TM_TRY(job_batch_begin(j));
-            for (; j.ell <= q.k; j.ell++) {
-                if (tune && b == 0 && j.ell == 3) TM_TRY(tune_layer(j));
-                else TM_TRY(launch_layers(j.st, one, unused, nullptr, 0, j.prof));
-            }
-            TM_TRY(job_readout_enqueue(j));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    Status st = [&]() -> Status {
+        TM_CUDA(cudaEventCreate(&ev[0]));
+        TM_CUDA(cudaEventCreate(&ev[1]));
+        TM_CUDA(cudaEventRecord(ev[0], g.stream));
+        TM_TRY(job_prep(j));
+        if (!j.done) {  // every lane batch of every repeat back to back; one sync at the end
+            TM_TRY(job_enqueue_all(j, true));
+            TM_CUDA(cudaStreamSynchronize(j.st));
+            TM_TRY(job_finish_all(j));
         }
-        TM_CUDA(cudaStreamSynchronize(j.st));
-        j.r = 0;
-        j.p0 = q.p_begin;
-        j.qsum = 0;
-        for (u64 b = 0; b < total; b++) {
-            j.batch_seq = b;
-            job_readout_finish(j);
-        }
-    }
-    TM_CUDA(cudaEventRecord(ev1, g.stream));
-    TM_CUDA(cudaEventSynchronize(ev1));
-    float fms = 0;
-    cudaEventElapsedTime(&fms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    if (ms) *ms = fms;
+        TM_CUDA(cudaEventRecord(ev[1], g.stream));
+        TM_CUDA(cudaEventSynchronize(ev[1]));
+        float fms = 0;
+        TM_CUDA(cudaEventElapsedTime(&fms, ev[0], ev[1]));
+        if (ms) *ms = fms;
+        return Status();
+    }();
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    TM_TRY(st);
     *found = j.found;
     *sieve_sum = j.sieve_sum;
     if (per_point && !j.vals.empty()) std::memcpy(per_point, j.vals.data(), j.vals.size() * sizeof(u64));
@@ -1200,9 +1375,13 @@ Status job_first_arc(Job &j, u32 *best, u32 *a, u32 *b, u32 *t)
     k_first_nonzero<<<grid_for(j.mf, 256), 256, 0, j.st>>>(w.arc_sum.as<u64>(), j.mf, d_best);
     j.prof->stats.launches++;
     TM_CUDA(cudaGetLastError());
-    u32 hb = NONE;
-    TM_CUDA(cudaMemcpyAsync(&hb, d_best, 4, cudaMemcpyDeviceToHost, j.st));
+    TM_TRY(ensure_pinned(w));
+    u32 *h = (u32 *)((char *)w.host_pinned + 48);
+    TM_CUDA(cudaMemcpyAsync(h + 1, d_best, 4, cudaMemcpyDeviceToHost, j.st));
+    TM_TRY(status_take_enqueue(j.st, w.counters.as<u32>() + 12, h));
     TM_CUDA(cudaStreamSynchronize(j.st));
+    TM_TRY(status_result(h[0]));
+    const u32 hb = h[1];
     *best = hb;
     if (hb == NONE) return Status();
     TM_CUDA(cudaMemcpyAsync(a, w.f_src.as<u32>() + hb, 4, cudaMemcpyDeviceToHost, j.st));
@@ -1243,7 +1422,11 @@ Status sieve_localize(Graph &g, const QuerySpec &q, u64 *per_vertex, int *found,
     }
     TM_CUDA(cudaMemcpyAsync(per_vertex, pv.p, (u64)g.n * 8, cudaMemcpyDeviceToHost, g.stream));
     TM_CUDA(cudaEventRecord(ev1, g.stream));
+    TM_TRY(ensure_pinned(w));
+    u32 *h_status = (u32 *)((char *)w.host_pinned + 48);
+    TM_TRY(status_take_enqueue(g.stream, w.counters.as<u32>() + 12, h_status));
     TM_CUDA(cudaStreamSynchronize(g.stream));
+    TM_TRY(status_result(*h_status));
     pv.release();
     float fms = 0;
     cudaEventElapsedTime(&fms, ev0, ev1);

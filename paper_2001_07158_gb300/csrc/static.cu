@@ -39,7 +39,7 @@ __global__ void k_active_list(u32 n, const u32 *act, u32 *list);
 __global__ void k_wtab(u32 k, u32 L, u64 p0, QueryKeys keys, u64 *wtab);
 __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L, const u32 *color,
                                               const u32 *slot_begin, const u32 *slot_count, QueryKeys keys,
-                                              const u64 *wtab, u64 *x);
+                                              const u64 *wtab, u64 *x, u32 n, u32 num_colors, u32 k);
 
 namespace {
 
@@ -346,7 +346,7 @@ Status static_sieve(Graph &g, const QuerySpec &q, const uint8_t *d_alive, u64 *d
         k_wtab<<<grid_of((u64)k * L, 128), 128, 0, st>>>(k, L, p0, keys, w.wtab.as<u64>());
         k_coef<<<(unsigned)((n_act + 7) / 8), 256, 0, st>>>((u32)n_act, w.act_list.as<u32>(), L, g.d_color,
                                                              w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
-                                                             w.wtab.as<u64>(), w.x.as<u64>());
+                                                             w.wtab.as<u64>(), w.x.as<u64>(), g.n, g.num_colors, k);
         TM_CUDA(cudaMemsetAsync(arr, 0, row * 8 * 2 * (k - 1), st));
         const u64 *x = w.x.as<u64>();
         const u32 *act = w.act_list.as<u32>();

@@ -33,10 +33,11 @@ def test_reference_arm_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference"
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
-                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "paper"):
         assert key in d, key
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["cores"] == min(os.cpu_count(), 64) and d["cpu_baseline"]["nproc"] == os.cpu_count()
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
 
 
@@ -48,16 +49,33 @@ def test_reference_arm_other_ranks_exit_quietly():
 
 
 def test_speed_of_light_model():
-    # the bound is the slowest pipe; each pipe time scales with its work
-    t, pipes = bench.layer_bound_s(reg=1e6, tab=1e8, builds=1e6)
-    assert t == max(pipes.values()) and all(v > 0 for v in pipes.values())
-    t2, pipes2 = bench.layer_bound_s(reg=2e6, tab=2e8, builds=2e6)
-    for k in pipes:
-        assert pipes2[k] == pytest.approx(2 * pipes[k])
-    # table products alone: shared memory at 1 wavefront per product and SM clock
-    _, only_tab = bench.layer_bound_s(reg=0, tab=bench.SMS * bench.SM_HZ, builds=0)
-    assert only_tab["smem"] == pytest.approx(1.0)
-    assert only_tab["fma"] == 0
+    # costs solved from the probe's rates reproduce them: a round of the table
+    # probe (one build, 64 or 128 lookups) takes 64 / R64 or 128 / R128
+    rates = {"reg": 1.2e11, "table64": 2.5e11, "table128": 2.8e11}
+    c = bench.table_costs(rates)
+    assert c["build"] / 64 + c["lookup"] == pytest.approx(1 / rates["table64"])
+    assert c["build"] / 128 + c["lookup"] == pytest.approx(1 / rates["table128"])
+    assert c["reg"] == pytest.approx(1 / rates["reg"])
+    # the bound is the larger form time, and each form time scales with its work
+    t, forms = bench.layer_bound_s(c, reg=1e6, tab=1e8, builds=1e6)
+    assert t == max(forms.values()) and all(v > 0 for v in forms.values())
+    t2, forms2 = bench.layer_bound_s(c, reg=2e6, tab=2e8, builds=2e6)
+    for k in forms:
+        assert forms2[k] == pytest.approx(2 * forms[k])
+    _, only_reg = bench.layer_bound_s(c, reg=rates["reg"], tab=0, builds=0)
+    assert only_reg["register"] == pytest.approx(1.0) and only_reg["table"] == 0
+    # a table rate that does not fall with fewer lanes per table cannot give a
+    # negative build cost
+    c2 = bench.table_costs({"reg": 1e11, "table64": 3e11, "table128": 2.9e11})
+    assert c2["build"] == 0 and c2["lookup"] > 0
+
+
+def test_default_legs_and_switches():
+    a = bench.parse_args([])
+    assert bench.legs_of(a) == {"large10", "batch", "serving", "cpu"} and a.serving_requests == 4096
+    a = bench.parse_args(["--no-serving", "--no-cpu-baseline"])
+    assert bench.legs_of(a) == {"large10", "batch"}
+    assert bench.legs_of(bench.parse_args(["--legs", ""])) == set()
 
 
 def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):

@@ -4,13 +4,17 @@ Bit-exact against the oracle wherever the oracle finishes in seconds:
 - large graphs (n = 10^7 with m = 5*10^8 at k = 5, and m = 10^8 at k = 10):
   every point (k = 5) or a ragged sample of points (k = 10) of a decision
   restricted to a narrow time window, which the oracle evaluates on the arcs
-  of that window (arcs outside the window are not used, Sec. 6.8); at the
-  full window, properties that hold at any size: a point range equals the
-  matching slice of the whole decision (a different lane width and launch
-  shape), and extraction returns a valid path;
+  of that window (arcs outside the window are not used, Sec. 6.8); the
+  full-window decision, every point (k = 5) or points across a lane-batch
+  boundary (k = 10), against the oracle run on the arcs whose two endpoint
+  colours are in the multiset (the other arcs change no per-point value, a
+  property the oracle's own tests pin); a point range equals the matching
+  slice of the whole decision (a different lane width and launch shape), and
+  extraction returns a valid path;
 - batched small graphs: a sample of the batch checked point by point;
 - the serving graph: requests in the server's mix equal the same requests
-  alone, and a sample of them equals the oracle.
+  alone, point by point, also when they arrive while large requests run;
+  samples of them equal the oracle.
 """
 import random
 
@@ -42,6 +46,16 @@ def window_arcs(g, t_min, t_max):
     return g.src[sel], g.dst[sel], g.time[sel]
 
 
+def kept_arcs(g, multiset):
+    """The arcs whose two endpoint colours are in the multiset: every other arc
+    has an endpoint with x = 0, so leaving it out changes no per-point value."""
+    cs = np.zeros(max(int(g.num_colors), 1), bool)
+    cs[np.asarray(multiset, np.int64)] = True
+    sel = cs[g.color[g.src]]
+    sel &= cs[g.color[g.dst]]
+    return g.src[sel], g.dst[sel], g.time[sel]
+
+
 def check_path(g, k, ms, v, t, arcs=None):
     assert len(set(v.tolist())) == k
     assert sorted(g.color[v].tolist()) == sorted(int(c) for c in ms)
@@ -67,8 +81,16 @@ def test_large_graph(tm, m, k, seed, points):
         _, _, pp = oracle.decide(g.n, ws, wd, wt, g.color, g.num_colors, k, q.multiset, seed=q.seed, t_min=t0,
                                  t_max=t1, point_begin=lo, point_end=hi, nthreads=min(16, hi - lo))
         assert np.array_equal(d.per_point[lo:hi], pp), (lo, hi)
-    # full window: a point range equals the slice of the whole decision
+    # full window: every point (k = 5), or four points across the lane-batch
+    # boundary at 512 (k = 10, 128 lanes), against the oracle on the kept arcs
     full = tm.tmotif_decide(G, k, q.multiset, seed=q.seed)
+    ks, kd, kt = kept_arcs(g, q.multiset)
+    lo, hi = (0, 1 << k) if points is None else (509, 513)
+    _, _, pp = oracle.decide(g.n, ks, kd, kt, g.color, g.num_colors, k, q.multiset, seed=q.seed, point_begin=lo,
+                             point_end=hi, nthreads=min(16, hi - lo))
+    assert np.array_equal(full.per_point[lo:hi], pp), (lo, hi)
+    del ks, kd, kt
+    # a point range equals the slice of the whole decision
     lo, hi = (3, 11) if k == 5 else (100, 108)
     part = tm.tmotif_decide(G, k, q.multiset, seed=q.seed, point_begin=lo, point_end=hi)
     assert np.array_equal(part.per_point, full.per_point[lo:hi])
@@ -88,13 +110,14 @@ def test_batched_tour_graphs_sample_against_oracle(tm):
     queries = [{"k": q.k, "multiset": q.multiset, "seed": q.seed} for _, q in items]
     res = tm.tmotif_decide_batch(graphs, queries)
     rng = random.Random(5)
-    for i in rng.sample(range(len(items)), 8):
+    for i in rng.sample(range(len(items)), 24):
         g, q = items[i]
-        f, s, pp = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed)
+        f, s, pp = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed,
+                                 nthreads=16)
         assert res[i].found == f and res[i].sieve_sum == s and np.array_equal(res[i].per_point, pp), i
-    for i in rng.sample(range(len(items)), 40):
+    for i in range(len(items)):  # every graph of the batch equals its decision alone
         alone = tm.tmotif_decide(graphs[i], **queries[i])
-        assert np.array_equal(alone.per_point, res[i].per_point)
+        assert np.array_equal(alone.per_point, res[i].per_point), i
     for G in graphs:
         G.close()
 
@@ -126,6 +149,7 @@ def test_serving_graph_mix_equals_alone_and_oracle(tm):
         else:
             alone = tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed)
             assert dec.found == alone.found and dec.sieve_sum == alone.sieve_sum
+            assert np.array_equal(dec.per_point, alone.per_point)
     # two small requests against the oracle, every point
     small = [(q, ex) for q, ex in reqs if q.k <= 4 and not ex][:2]
     for q, _ in small:
@@ -133,4 +157,76 @@ def test_serving_graph_mix_equals_alone_and_oracle(tm):
         f, s, pp = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, q.k, q.multiset, seed=q.seed,
                                  nthreads=16)
         assert d.found == f and d.sieve_sum == s and np.array_equal(d.per_point, pp)
+    G.close()
+
+
+def test_serving_staggered_arrivals_equal_alone_and_oracle(tm):
+    """Requests that arrive while others run on the device: a k = 10 decision
+    and a k = 9 extraction (large requests) are in flight when smaller
+    requests arrive one by one, and a k = 9 decision joins halfway.  Every
+    result equals the same request alone, point by point (decisions) or path
+    by path (extractions); samples equal the oracle."""
+    import time
+
+    g, reqs = synth.config5_serving(requests=128)
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors)
+    tm.tmotif_decide(G, 10, reqs[17][0].multiset, seed=1, per_point=False)  # tune the k = 10 launch shape first
+    first = [next(r for r in reqs if r[0].k == 10 and not r[1]), next(r for r in reqs if r[0].k == 9 and r[1])]
+    later = [next(r for r in reqs if r[0].k == 9 and not r[1])]
+    small = [r for r in reqs if r[0].k <= 7][:24]
+    srv = tm.tmotif_server_create(0)
+    submitted, results = [], {}
+
+    def submit(q, ex):
+        submitted.append((q, ex, tm.tmotif_submit(srv, G, q.k, q.multiset, is_extract=ex, seed=q.seed)))
+
+    def poll_all():
+        for q, ex, t in submitted:
+            if t not in results:
+                r = tm.tmotif_poll(srv, t, q.k)
+                if r is not None:
+                    results[t] = r
+
+    for q, ex in first:
+        submit(q, ex)
+    time.sleep(0.03)
+    overlapped = 0
+    for i, (q, ex) in enumerate(small):
+        poll_all()
+        overlapped += any(t not in results and qq.k >= 9 for qq, _, t in submitted)
+        submit(q, ex)
+        if i == len(small) // 2:
+            for qq, ee in later:
+                submit(qq, ee)
+        time.sleep(0.004)
+    t0 = time.time()
+    while len(results) < len(submitted):
+        poll_all()
+        assert time.time() - t0 < 600
+        time.sleep(0.001)
+    srv.close()
+    assert overlapped >= len(small) // 2, overlapped  # most small requests arrived while a large one ran
+    for q, ex, t in submitted:
+        dec, v, tt = results[t]
+        if ex:
+            f, va, ta = tm.tmotif_extract(G, q.k, q.multiset, seed=q.seed)
+            assert dec.found == f
+            if f:
+                assert np.array_equal(v, va) and np.array_equal(tt, ta)
+                check_path(g, q.k, q.multiset, v, tt)
+        else:
+            alone = tm.tmotif_decide(G, q.k, q.multiset, seed=q.seed)
+            assert dec.found == alone.found and np.array_equal(dec.per_point, alone.per_point), q.k
+    # against the oracle on the kept arcs: two small decisions, every point;
+    # the k = 10 decision, two points across its first lane batch's end
+    by_ticket = {t: (q, ex) for q, ex, t in submitted}
+    small_dec = [t for t, (q, ex) in by_ticket.items() if not ex and q.k <= 5][:2]
+    big_dec = [t for t, (q, ex) in by_ticket.items() if not ex and q.k == 10][:1]
+    for t in small_dec + big_dec:
+        q, _ = by_ticket[t]
+        lo, hi = (0, 1 << q.k) if q.k <= 5 else (127, 129)
+        ks, kd, kt = kept_arcs(g, q.multiset)
+        _, _, pp = oracle.decide(g.n, ks, kd, kt, g.color, g.num_colors, q.k, q.multiset, seed=q.seed,
+                                 point_begin=lo, point_end=hi, nthreads=min(16, hi - lo))
+        assert np.array_equal(results[t][0].per_point[lo:hi], pp), (q.k, lo, hi)
     G.close()

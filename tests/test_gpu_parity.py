@@ -147,7 +147,7 @@ def test_layer_shapes_give_identical_results(tm):
         assert tm.tmotif_get_layer_shape(G, L) is None
         tuned = tm.tmotif_decide(G, k, ms, seed=9)
         chunk, variant = tm.tmotif_get_layer_shape(G, L)
-        variants = (0, 3) if L == 32 else ((0, 1, 2) if L in (16, 64) else (0, 1))
+        variants = {16: (0, 1, 2), 32: (0, 3, 4), 64: (0, 1, 2, 4), 128: (0, 1, 4)}[L]
         assert chunk in (64, 128, 256, 512, 1024) and variant in variants
         if k in (4, 7):
             ref = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, seed=9)
@@ -401,11 +401,12 @@ def test_vertex_localized_sieve_matches_oracle(tm):
 
 def test_arc_localisation_in_every_layer_shape(tm):
     # arc-localised sums (per-vertex Q_u, localised extraction) in every
-    # pinned launch shape at 64 and 128 lanes, including two 64-lane teams per
-    # chunk at 128 lanes, whose teams add to the same arcs
+    # pinned launch shape at 32, 64 and 128 lanes, including two 64-lane teams
+    # per chunk at 128 lanes, whose teams add to the same arcs, and the staged
+    # form (variant 4)
     g = synth.powerlaw_graph(4000, 60000, 120, 5, seed=23)
     cs, cd, ct = oracle.canon(g.n, g.src, g.dst, g.time)
-    for k, L, variants in ((6, 64, (0, 1, 2)), (7, 128, (0, 1))):
+    for k, L, variants in ((5, 32, (0, 3, 4)), (6, 64, (0, 1, 2, 4)), (7, 128, (0, 1, 4))):
         ms = [i % 5 for i in range(k)]
         pb = oracle.Problem(g.n, cs, cd, ct, g.color, g.num_colors, k, ms)
         arc = oracle.arc_sums(pb, oracle.query_seed(4, 0))

@@ -115,6 +115,7 @@ def test_server_mixed_requests_equal_alone(tm):
         else:
             alone = tm.tmotif_decide(G, q["k"], q["multiset"], seed=q["seed"], t_max=q["t_max"])
             assert dec.found == alone.found and dec.sieve_sum == alone.sieve_sum
+            assert np.array_equal(dec.per_point, alone.per_point)
 
 
 def test_server_budget_admission(tm):
@@ -133,7 +134,7 @@ def test_server_budget_admission(tm):
     one.close()
     for (G_, qq, _), (dec, _, _) in zip(jobs, res):
         alone = tm.tmotif_decide(G, q.k, q.multiset, seed=qq["seed"])
-        assert dec.sieve_sum == alone.sieve_sum
+        assert dec.sieve_sum == alone.sieve_sum and np.array_equal(dec.per_point, alone.per_point)
     other = tm.tmotif_server_create(0)
     with pytest.raises(tm.TmotifError) as e:
         tm.tmotif_poll(other, 12345, 4)
@@ -156,6 +157,7 @@ def test_server_wait_times_out_then_completes(tm):
     dec, _, _ = tm.tmotif_wait(srv, t, 10, 600000)
     alone = tm.tmotif_decide(G, 10, ms, seed=4)
     assert dec.found == alone.found and dec.sieve_sum == alone.sieve_sum
+    assert np.array_equal(dec.per_point, alone.per_point)
     with pytest.raises(tm.TmotifError) as e:  # a finished ticket is forgotten
         tm.tmotif_wait(srv, t, 10, 0)
     assert e.value.code == 6

@@ -89,3 +89,92 @@ def test_noalloc_rejects_graphs_beyond_the_fixed_scratch(tm):
         tm.tmotif_decide_noalloc(src.data_ptr(), dst.data_ptr(), time.data_ptr(), 1, color.data_ptr(), n, 1, 6,
                                  [0] * 6, out.data_ptr())
     assert e.value.code == 5 and "scratch" in str(e.value)
+
+
+def hub_graph():
+    """A graph with one vertex whose in-segment (300 arcs) is longer than a
+    team chunk of the allocation-free layer kernel (128 arcs), plus uniform
+    arcs, so that segments cross chunk boundaries."""
+    rng = np.random.default_rng(31)
+    g = synth.uniform_graph(400, 1500, 60, 4, seed=32)
+    hub = 5
+    s = rng.choice(np.setdiff1d(np.arange(400), [hub]), 300, replace=False).astype(np.uint32)
+    t = rng.integers(1, 61, 300).astype(np.uint32)
+    g.src = np.concatenate([g.src, s, np.full(40, hub, np.uint32)])
+    g.dst = np.concatenate([g.dst, np.full(300, hub, np.uint32), rng.integers(0, 400, 40).astype(np.uint32)])
+    g.time = np.concatenate([g.time, t, rng.integers(1, 61, 40).astype(np.uint32)])
+    return g
+
+
+def test_noalloc_start_end_k2_and_long_segments(tm):
+    """Start/end vertices, k = 2 (the first layer is also the last) and an
+    in-segment longer than a chunk: equal to tmotif_decide and to the oracle,
+    point by point."""
+    import torch
+
+    import oracle
+
+    stream = torch.cuda.current_stream()
+    g = hub_graph()
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
+    src, dst, time, color, m = device_graph(g)
+    hub = 5
+    cases = [
+        (2, [int(g.color[hub]), int(g.color[hub])], {"seed": 3}),
+        (2, [0, 1], {"seed": 4, "end": hub}),
+        (4, [int(g.color[hub]), 0, 1, 2], {"seed": 5, "end": hub}),
+        (5, [0, 1, 2, 3, int(g.color[7])], {"seed": 6, "start": 7}),
+        (6, [0, 0, 1, 2, 3, 3], {"seed": 7, "start": 11, "end": hub, "t_min": 3}),
+        (7, [0, 1, 2, 3, 0, 1, 2], {"seed": 8, "point_begin": 60, "point_end": 127}),
+    ]
+    for k, ms, kw in cases:
+        npts = (kw.get("point_end", 0) - kw.get("point_begin", 0)) or (1 << k)
+        out = torch.full((npts,), -1, dtype=torch.int64, device="cuda")
+        tm.tmotif_decide_noalloc(src.data_ptr(), dst.data_ptr(), time.data_ptr(), m, color.data_ptr(), g.n,
+                                 g.num_colors, k, ms, out.data_ptr(), stream=stream, **kw)
+        got = out.cpu().numpy().view(np.uint64)
+        want = tm.tmotif_decide(G, k, ms, **kw).per_point
+        assert np.array_equal(got, want), (k, kw)
+        okw = dict(kw)
+        _, _, pp = oracle.decide(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, **okw)
+        assert np.array_equal(got, pp), (k, kw)
+    G.close()
+
+
+def test_noalloc_empty_graph_gives_zero_sums(tm):
+    import torch
+
+    color = torch.zeros(10, dtype=torch.int32, device="cuda")
+    out = torch.full((16,), -1, dtype=torch.int64, device="cuda")
+    tm.tmotif_decide_noalloc(0, 0, 0, 0, color.data_ptr(), 10, 2, 4, [0, 0, 1, 1], out.data_ptr())
+    assert not out.cpu().numpy().any()
+
+
+def test_noalloc_rejects_invalid_inputs(tm):
+    """Unsorted arcs, and a colour >= num_colors on a vertex with no arcs,
+    are INVALID (checked before any coefficient work)."""
+    import torch
+
+    g = synth.uniform_graph(50, 200, 20, 3, seed=41)
+    src, dst, time, color, m = device_graph(g)
+    out = torch.zeros(16, dtype=torch.int64, device="cuda")
+    # swap two arcs of different destinations: no longer sorted by (dst, time, src)
+    bad_src, bad_dst, bad_time = src.clone(), dst.clone(), time.clone()
+    i, j = 0, m - 1
+    for a in (bad_src, bad_dst, bad_time):
+        a[i], a[j] = a[j].item(), a[i].item()
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide_noalloc(bad_src.data_ptr(), bad_dst.data_ptr(), bad_time.data_ptr(), m, color.data_ptr(),
+                                 g.n, g.num_colors, 4, [0, 1, 2, 0], out.data_ptr())
+    assert e.value.code == 1
+    # one more vertex, without arcs, whose colour is num_colors
+    color2 = torch.cat([color, torch.tensor([g.num_colors], dtype=torch.int32, device="cuda")])
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide_noalloc(src.data_ptr(), dst.data_ptr(), time.data_ptr(), m, color2.data_ptr(), g.n + 1,
+                                 g.num_colors, 4, [0, 1, 2, 0], out.data_ptr())
+    assert e.value.code == 1 and "colour" in str(e.value)
+    # m beyond the 32-bit arc numbering
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_decide_noalloc(src.data_ptr(), dst.data_ptr(), time.data_ptr(), 1 << 32, color.data_ptr(), g.n,
+                                 g.num_colors, 4, [0, 1, 2, 0], out.data_ptr())
+    assert e.value.code == 1
