@@ -13,6 +13,8 @@ Metric: edge-steps/s = m * k * 2^k / (time of one decision).
 On one GPU the same JSON line also carries the other workloads of the suite,
 each measured after the headline's timed region:
   large10  the large-sieve decision n = 10^7, m = 10^8, k = 10 (1024 points);
+  transit  a timetable graph (2.4e7 arcs) at k = 8, without and with the
+           static preprocessing sieve;
   batch    10,000 small tour graphs in one batched call, against one
            tmotif_decide per graph, both timed by CUDA events on the stream;
   serving  4,096 requests (k in 3..10, 30 % extract) against a resident
@@ -22,7 +24,7 @@ each measured after the headline's timed region:
   cpu_baseline  the oracle on every host core, on a sample of the points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--legs large10,batch,serving,cpu] [--workload ...]
+                  [--legs large10,transit,batch,serving,cpu] [--workload ...]
 
 With N > 1 it runs under torchrun, one rank per GPU; every rank decides its own
 query (another seed) on its own replica of the graph -- the sieve points of
@@ -112,9 +114,9 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--legs", default="large10,batch,serving,cpu",
-                   help="extra workloads measured after the headline at N = 1 (comma list of large10, batch, "
-                        "serving, cpu; empty for none)")
+    p.add_argument("--legs", default="large10,transit,batch,serving,cpu",
+                   help="extra workloads measured after the headline at N = 1 (comma list of large10, transit, "
+                        "batch, serving, cpu; empty for none)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serving-requests", type=int, default=4096)
@@ -125,6 +127,9 @@ def parse_args(argv=None):
                         "n=1e7 with m=5e8, k=5 / m=1e8, k=10; batch: 10,000 small tour graphs in one "
                         "batched call (k in 5..8); transit: a timetable graph for --preprocess")
     p.add_argument("--preprocess", action="store_true", help="static preprocessing sieve before each decision")
+    p.add_argument("--layer-shape", default="",
+                   help="CHUNK,VARIANT: pin the layer kernel's launch shape (tmotif_set_layer_shape) for the "
+                        "workload's lane width instead of the autotuner's pick (profiling one form)")
     return p.parse_args(argv)
 
 
@@ -364,6 +369,52 @@ def large10_leg(tm, stream, dev, costs, rates, steps, warmup):
             "gpu_launches": int(stats["launches"])}
 
 
+def static_roofline(stats, costs, rates):
+    """Roofline of the static preprocessing sieve's layer kernel
+    (k_static_layer) from the library's events around its launches, on the
+    same product-rate bound as the temporal layer kernel."""
+    nl = stats["static_launches"]
+    if not nl:
+        return None
+    ms = stats["static_ms"] / nl
+    muls = stats["static_gf_muls"] / nl
+    tmuls = stats["static_table_muls"] / nl
+    builds = stats["static_table_builds"] / nl
+    t_min, forms = layer_bound_s(costs, muls - tmuls, tmuls, builds)
+    achieved = muls / (ms / 1e3) / 1e9
+    peak = muls / t_min / 1e9 if t_min > 0 else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G GF(2^64) products/s",
+            "frac": achieved / peak if peak else None, "kernel": "k_static_layer (eq. gen-polynomial:1 layer)",
+            "ms_per_launch": ms, "gf_muls_per_launch": muls, "launches_per_step": None,
+            "form_ms": {k: v * 1e3 for k, v in forms.items()}}
+
+
+def transit_leg(tm, stream, dev, costs, rates, steps, warmup):
+    """The timetable graph at k = 8 (256 points): decisions without and with
+    the static preprocessing sieve (Sec. 8.1 (ii)), each with its own timed
+    steps; rooflines of the temporal layer kernel in both forms and of the
+    static layer kernel."""
+    g, q = workload(1.0, "transit")
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
+    work = g.m * q.k * (1 << q.k)
+    out = {"workload": WORKLOADS["transit"], "n": g.n, "m": g.m, "k": int(q.k), "steps": steps, "warmup": warmup}
+    for name, pre in (("plain", False), ("preprocess", True)):
+        total_ms, found, stats, clocks = measure_decision(tm, stream, dev, G, q, steps, warmup, q.seed, pre)
+        ms = total_ms / steps
+        leg = {"ms_per_step": ms, "value": work / (ms / 1e3), "unit": UNIT, "found_all": all(found),
+               "clocks": clocks, "roofline": roofline_of(stats, total_ms, costs, rates, None)}
+        if pre:
+            sr = static_roofline(stats, costs, rates)
+            if sr:
+                sr["launches_per_step"] = stats["static_launches"] / steps
+                sr["share_of_step"] = stats["static_ms"] / total_ms
+            leg["static_roofline"] = sr
+        out[name] = leg
+    G.close()
+    out["speedup_of_preprocess"] = out["plain"]["ms_per_step"] / out["preprocess"]["ms_per_step"]
+    return out
+
+
 def batch_leg(tm, stream, dev, steps, warmup, count=10_000, seed=4):
     """10,000 small tour graphs: a step is one tmotif_decide_batch call over
     all of them (graphs resident).  The plain form, one tmotif_decide per
@@ -598,6 +649,12 @@ def run_ours(args):
     work_units = g.m * q.k * (1 << q.k)
 
     G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
+    if args.layer_shape:
+        chunk, variant = (int(x) for x in args.layer_shape.split(","))
+        L = 4
+        while L < 128 and L < (1 << q.k):
+            L *= 2
+        tm.tmotif_set_layer_shape(G, L, chunk, variant)
     total_ms, found, stats, clocks = measure_decision(tm, stream, dev, G, q, args.steps, args.warmup, seed,
                                                       args.preprocess, world)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -637,6 +694,8 @@ def run_ours(args):
     leg_steps, leg_warmup = max(3, min(args.steps, 5)), 3
     if "large10" in legs:
         run_leg(line, "large10", lambda: large10_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup))
+    if "transit" in legs:
+        run_leg(line, "transit", lambda: transit_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup))
     if "batch" in legs:
         run_leg(line, "batch", lambda: batch_leg(tm, stream, dev, leg_steps, leg_warmup))
     if "serving" in legs:

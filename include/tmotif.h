@@ -153,6 +153,11 @@ typedef struct {
     uint64_t layer_gf_muls;    /* GF(2^64) products in the layer kernels    */
     uint64_t layer_table_muls; /* ... of which by a shared multiplier table  */
     uint64_t layer_table_builds; /* shared tables built (one per arc and table layer) */
+    uint64_t static_launches;  /* static preprocessing sieve layers (Sec. 8.1 (ii)) */
+    double static_ms;
+    uint64_t static_gf_muls;   /* GF(2^64) products in those layers           */
+    uint64_t static_table_muls;  /* ... of which by a shared multiplier table */
+    uint64_t static_table_builds;
 } tmotif_stats;
 
 /* Build the resident graph: validate, orient, drop self-loops, merge
@@ -239,8 +244,8 @@ int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_query *querie
  * Requests run in two lanes that share the memory budget, each with its own
  * host worker thread and CUDA streams: requests over about 4e9 arc-lane steps
  * (kept arcs x (k-1) x points, doubled for extraction) run one at a time in
- * arrival order on streams of the device's least priority; smaller ones run
- * together, in shared layer launches, on streams of its greatest priority,
+ * arrival order on streams of the device's greatest priority; smaller ones
+ * run together, in shared layer launches, on streams of its least priority,
  * beside the large one.  Results never depend on the lane or the mix. */
 int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *out);
 int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_query *q, int is_extract, uint64_t *ticket);

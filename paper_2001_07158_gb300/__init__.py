@@ -64,7 +64,9 @@ class _Stats(C.Structure):
                 ("prep_ms", C.c_double), ("coef_ms", C.c_double), ("other_ms", C.c_double),
                 ("layer_arc_lanes", C.c_uint64), ("layer_cp_lanes", C.c_uint64), ("layer_bytes", C.c_uint64),
                 ("layer_gf_muls", C.c_uint64), ("layer_table_muls", C.c_uint64),
-                ("layer_table_builds", C.c_uint64)]
+                ("layer_table_builds", C.c_uint64), ("static_launches", C.c_uint64), ("static_ms", C.c_double),
+                ("static_gf_muls", C.c_uint64), ("static_table_muls", C.c_uint64),
+                ("static_table_builds", C.c_uint64)]
 
 
 def _load():

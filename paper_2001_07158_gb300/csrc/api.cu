@@ -194,6 +194,7 @@ Status Profiler::collect()
         if (p.family == FAM_LAYER) stats.layer_ms += ms;
         else if (p.family == FAM_PREP) stats.prep_ms += ms;
         else if (p.family == FAM_COEF) stats.coef_ms += ms;
+        else if (p.family == FAM_STATIC) stats.static_ms += ms;
         else stats.other_ms += ms;
     }
     pending.clear();

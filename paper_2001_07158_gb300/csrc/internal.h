@@ -76,7 +76,7 @@ struct Profiler {
     void destroy();
 };
 
-enum { FAM_LAYER = 0, FAM_PREP = 1, FAM_COEF = 2, FAM_OTHER = 3 };
+enum { FAM_LAYER = 0, FAM_PREP = 1, FAM_COEF = 2, FAM_OTHER = 3, FAM_STATIC = 4 };
 
 // Bits of the per-device status word that kernels set when they meet a
 // condition they cannot continue on normally; the host takes (reads and

@@ -407,17 +407,17 @@ extern "C" int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_qu
 //
 // Two lanes, each a worker thread with its own scheduler, streams and
 // finishing workspace, drawing on one memory budget:
-//   lane 0 takes the small requests and runs them on streams of the
-//     device's greatest priority, many at a time in shared layer launches;
+//   lane 0 takes the small requests and runs them many at a time in shared
+//     layer launches, on streams of the device's least priority;
 //   lane 1 takes the large requests (over LARGE_WORK arc-lane steps) one at
-//     a time, in arrival order, on streams of the least priority; each of
+//     a time, in arrival order, on streams of its greatest priority; each of
 //     their jobs runs whole, as a plain decision does (every lane batch
 //     enqueued back to back in the tuned launch shape, one sync).
-// Small requests thus run beside a large one on the device: their kernels are
-// scheduled first whenever SMs free up, and fill the large request's
-// preparation, readout and synchronisation gaps, instead of waiting behind
-// it.  When the large lane waits for memory, the small lane admits nothing
-// new until it has been served.
+// Small requests thus run beside a large one instead of queueing behind it:
+// their kernels take the SMs the large request leaves free (its preparation,
+// readout and synchronisation gaps, its launches' tails), while the large
+// request's own blocks are scheduled first.  When the large lane waits for
+// memory, the small lane admits nothing new until it has been served.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -700,7 +700,7 @@ extern "C" int tmotif_server_create(size_t hbm_budget_bytes, tmotif_server_t *ou
             Lane &l = s->lanes[i];
             l.srv = s.get();
             l.large = i == 1;
-            const int prio = l.large ? least : greatest;
+            const int prio = l.large ? greatest : least;
             e = cudaStreamCreateWithPriority(&l.st, cudaStreamNonBlocking, prio);
             if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&l.prep_st, cudaStreamNonBlocking, prio);
         }

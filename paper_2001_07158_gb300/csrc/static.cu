@@ -45,7 +45,8 @@ namespace {
 
 const u64 TAG_YF = 0x4444444444444444ull;
 const u64 TAG_YB = 0x5555555555555555ull;
-const u32 S_CHUNK = 64;  // pairs per warp in a static layer
+const u32 S_CHUNK = 64;        // most pairs per warp in a static layer
+const u32 S_WARPS_PER_SM = 32;  // warps per SM a static layer aims to start
 
 unsigned grid_of(u64 items, int threads) { return (unsigned)std::max<u64>(1, (items + threads - 1) / threads); }
 
@@ -99,44 +100,60 @@ __global__ void k_pair_compact(u64 N, const u32 *own, const u32 *oth, const u32 
 // (per lane), In read through the base-case restriction `only` (vertex id
 // or TMOTIF_ANY) when `base` is set.  y = mix64(mix64(key ^ (a << 32 | b)) ^ p)
 // with (a, b) = (oth, own) when fwd, (own, oth) otherwise.  One warp per
-// chunk of S_CHUNK pairs, lanes tt and tt + 32 per thread; with TAB the warp
-// builds the nibble table of y (2 KB) and each lane product is 16 lookups.
+// chunk of S pairs (S chosen by the launcher so that the launch fills the
+// GPU), lanes tt and tt + 32 per thread; each batch of 32 pairs is loaded and
+// its y computed once, one pair per thread, then broadcast by shuffles; with
+// TAB the warp builds the nibble table of y (2 KB) and each lane product is
+// 16 lookups.  A run of pairs with the same owner is flushed with one
+// atomicXor per lane, so owners split across warps stay exact.
 template <bool TAB>
-__global__ void __launch_bounds__(256) k_static_layer(u64 M, const u32 *own, const u32 *oth, u32 L, const u64 *In,
-                                                      u64 *Out, u64 key, u32 p, int fwd, int base, u32 only)
+__global__ void __launch_bounds__(256) k_static_layer(u64 M, u32 S, const u32 *own, const u32 *oth, u32 L,
+                                                      const u64 *In, u64 *Out, u64 key, u32 p, int fwd, int base,
+                                                      u32 only)
 {
     __shared__ __align__(2048) u64 tabs[TAB ? 8 : 1][TAB ? 256 : 1];  // tables on 2 KB boundaries
     u64 *tab = tabs[TAB ? (threadIdx.x >> 5) : 0];
     const int tt = threadIdx.x & 31;
     const u64 w = (u64)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const u64 e0 = w * S_CHUNK;
+    const u64 e0 = w * S;
     if (e0 >= M) return;  // whole warp leaves together
-    const u64 e1 = min(M, e0 + S_CHUNK);
+    const u64 e1 = min(M, e0 + S);
     const bool l0 = (u32)tt < L, l1 = (u32)tt + 32 < L;
     u64 a0 = 0, a1 = 0;
     u32 cur = own[e0];
-    for (u64 e = e0; e < e1; e++) {
-        const u32 o = own[e], g = oth[e];
-        if (o != cur) {
-            if (l0 && a0) atomicXor(&Out[(u64)cur * L + tt], a0);
-            if (l1 && a1) atomicXor(&Out[(u64)cur * L + tt + 32], a1);
-            a0 = a1 = 0;
-            cur = o;
+    for (u64 eb = e0; eb < e1; eb += 32) {
+        const u64 e = eb + tt;
+        u32 o = 0, g = 0;
+        u64 y = 0;
+        if (e < e1) {
+            o = own[e];
+            g = oth[e];
+            const u64 pair = fwd ? (((u64)g << 32) | o) : (((u64)o << 32) | g);
+            y = mix64(mix64(key ^ pair) ^ (u64)p);
         }
-        const u64 pair = fwd ? (((u64)g << 32) | o) : (((u64)o << 32) | g);
-        const u64 y = mix64(mix64(key ^ pair) ^ (u64)p);
-        const bool use = !base || only == TMOTIF_ANY || only == g;
-        const u64 v0 = (l0 && use) ? In[(u64)g * L + tt] : 0;
-        const u64 v1 = (l1 && use) ? In[(u64)g * L + tt + 32] : 0;
-        if (TAB) {
-            __syncwarp();
-            gf_table_build(tab, y, tt, 32);
-            __syncwarp();
-            a0 ^= gf_table_mul(tab, v0);
-            a1 ^= gf_table_mul(tab, v1);
-        } else {
-            a0 ^= gf_mul(y, v0);
-            a1 ^= gf_mul(y, v1);
+        const int cnt = (int)min((u64)32, e1 - eb);
+        for (int j = 0; j < cnt; j++) {
+            const u32 oj = __shfl_sync(0xffffffffu, o, j), gj = __shfl_sync(0xffffffffu, g, j);
+            const u64 yj = __shfl_sync(0xffffffffu, y, j);
+            if (oj != cur) {
+                if (l0 && a0) atomicXor(&Out[(u64)cur * L + tt], a0);
+                if (l1 && a1) atomicXor(&Out[(u64)cur * L + tt + 32], a1);
+                a0 = a1 = 0;
+                cur = oj;
+            }
+            const bool use = !base || only == TMOTIF_ANY || only == gj;
+            const u64 v0 = (l0 && use) ? In[(u64)gj * L + tt] : 0;
+            const u64 v1 = (l1 && use) ? In[(u64)gj * L + tt + 32] : 0;
+            if (TAB) {
+                __syncwarp();
+                gf_table_build(tab, yj, tt, 32);
+                __syncwarp();
+                a0 ^= gf_table_mul(tab, v0);
+                a1 ^= gf_table_mul(tab, v1);
+            } else {
+                a0 ^= gf_mul(yj, v0);
+                a1 ^= gf_mul(yj, v1);
+            }
         }
     }
     if (l0 && a0) atomicXor(&Out[(u64)cur * L + tt], a0);
@@ -192,8 +209,12 @@ Status launch_static_layer(cudaStream_t st, u64 M, const u32 *own, const u32 *ot
                            u64 key, u32 p, int fwd, int base, u32 only)
 {
     if (M == 0) return Status();
-    const u64 warps = (M + S_CHUNK - 1) / S_CHUNK;
-    k_static_layer<TAB><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(M, own, oth, L, In, Out, key, p, fwd, base,
+    // pairs per warp: enough warps for every SM to hold S_WARPS_PER_SM of
+    // them, at most S_CHUNK pairs per warp
+    const u64 target = (u64)sm_count() * S_WARPS_PER_SM;
+    const u32 S = (u32)std::min<u64>(S_CHUNK, std::max<u64>(1, (M + target - 1) / target));
+    const u64 warps = (M + S - 1) / S;
+    k_static_layer<TAB><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(M, S, own, oth, L, In, Out, key, p, fwd, base,
                                                                     only);
     TM_CUDA(cudaGetLastError());
     return Status();
@@ -339,8 +360,19 @@ Status static_sieve(Graph &g, const QuerySpec &q, const uint8_t *d_alive, u64 *d
     auto layer = [&](u64 Mp, const u32 *own, const u32 *oth, const u64 *In, u64 *Out, u64 key, u32 p, int fwd,
                      int base, u32 only) -> Status {
         (*launches)++;
-        return tab ? launch_static_layer<true>(st, Mp, own, oth, L, In, Out, key, p, fwd, base, only)
-                   : launch_static_layer<false>(st, Mp, own, oth, L, In, Out, key, p, fwd, base, only);
+        cudaEvent_t ea = nullptr;
+        TM_TRY(g.prof.begin(st, &ea));
+        TM_TRY(tab ? launch_static_layer<true>(st, Mp, own, oth, L, In, Out, key, p, fwd, base, only)
+                   : launch_static_layer<false>(st, Mp, own, oth, L, In, Out, key, p, fwd, base, only));
+        TM_TRY(g.prof.end(st, ea, FAM_STATIC));
+        tmotif_stats &sx = g.prof.stats;
+        sx.static_launches++;
+        sx.static_gf_muls += Mp * L;
+        if (tab) {
+            sx.static_table_muls += Mp * L;
+            sx.static_table_builds += Mp;
+        }
+        return Status();
     };
     for (u64 p0 = 0; p0 < npts; p0 += L) {
         k_wtab<<<grid_of((u64)k * L, 128), 128, 0, st>>>(k, L, p0, keys, w.wtab.as<u64>());
