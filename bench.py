@@ -623,7 +623,10 @@ def run_leg(line, name, fn):
     try:
         line[name] = fn()
     except Exception as e:  # noqa: BLE001 -- the headline line must still print
-        line[name] = {"error": f"{type(e).__name__}: {e}"}
+        import traceback
+
+        line[name] = {"error": f"{type(e).__name__}: {e}",
+                      "where": traceback.format_exc(limit=4).splitlines()[-6:]}
 
 
 def run_ours(args):
