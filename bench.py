@@ -13,6 +13,7 @@ Metric: edge-steps/s = m * k * 2^k / (time of one decision).
 On one GPU the same JSON line also carries the other workloads of the suite,
 each measured after the headline's timed region:
   large10  the large-sieve decision n = 10^7, m = 10^8, k = 10 (1024 points);
+  large5   the large-sieve decision n = 10^7, m = 5*10^8, k = 5 (32 points);
   transit  a timetable graph (2.4e7 arcs) at k = 8, without and with the
            static preprocessing sieve;
   batch    10,000 small tour graphs in one batched call, against one
@@ -24,7 +25,7 @@ each measured after the headline's timed region:
   cpu_baseline  the oracle on every host core, on a sample of the points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--legs large10,transit,batch,serving,cpu] [--workload ...]
+                  [--legs large10,large5,transit,batch,serving,cpu] [--workload ...]
 
 With N > 1 it runs under torchrun, one rank per GPU; every rank decides its own
 query (another seed) on its own replica of the graph -- the sieve points of
@@ -114,9 +115,9 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--legs", default="large10,transit,batch,serving,cpu",
-                   help="extra workloads measured after the headline at N = 1 (comma list of large10, transit, "
-                        "batch, serving, cpu; empty for none)")
+    p.add_argument("--legs", default="large10,large5,transit,batch,serving,cpu",
+                   help="extra workloads measured after the headline at N = 1 (comma list of large10, large5, "
+                        "transit, batch, serving, cpu; empty for none)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serving-requests", type=int, default=4096)
@@ -351,17 +352,18 @@ def e2e_decision(tm, stream, g, q, seed, steps, preprocess=False):
     return statistics.mean(times) if times else float("nan")
 
 
-def large10_leg(tm, stream, dev, costs, rates, steps, warmup):
-    """The large-sieve decision at k = 10 (n = 10^7, m = 10^8, 1024 points in
-    lane batches of 128): its own timed steps and layer roofline."""
-    g, q = workload(1.0, "large10")
+def large_leg(tm, stream, dev, costs, rates, steps, warmup, name="large10"):
+    """A large-sieve decision: k = 10 on n = 10^7, m = 10^8 (1024 points in
+    lane batches of 128), or k = 5 on m = 5*10^8 (32 points, one lane batch of
+    32): its own timed steps and layer roofline."""
+    g, q = workload(1.0, name)
     G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
     total_ms, found, stats, clocks = measure_decision(tm, stream, dev, G, q, steps, warmup, q.seed)
     G.close()
     e2e_s = e2e_decision(tm, stream, g, q, q.seed, 1)
     work = g.m * q.k * (1 << q.k)
     ms = total_ms / steps
-    return {"workload": WORKLOADS["large10"], "n": g.n, "m": g.m, "k": int(q.k), "steps": steps, "warmup": warmup,
+    return {"workload": WORKLOADS[name], "n": g.n, "m": g.m, "k": int(q.k), "steps": steps, "warmup": warmup,
             "ms_per_step": ms, "value": work / (ms / 1e3), "unit": UNIT, "found_all": all(found),
             "clocks": clocks, "roofline": roofline_of(stats, total_ms, costs, rates, None),
             "e2e": {"ms_per_step": e2e_s * 1e3, "value": work / e2e_s, "unit": UNIT,
@@ -695,8 +697,9 @@ def run_ours(args):
         run_leg(line, "cpu_baseline", lambda: cpu_baseline(g, q))
     del g
     leg_steps, leg_warmup = max(3, min(args.steps, 5)), 3
-    if "large10" in legs:
-        run_leg(line, "large10", lambda: large10_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup))
+    for name in ("large10", "large5"):
+        if name in legs:
+            run_leg(line, name, lambda: large_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup, name))
     if "transit" in legs:
         run_leg(line, "transit", lambda: transit_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup))
     if "batch" in legs:

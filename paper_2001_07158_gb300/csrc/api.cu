@@ -401,6 +401,7 @@ Status prepare(Graph &g, const QuerySpec &q, Prepared *p)
     cudaEventDestroy(e1);
     p->ms = f;
     p->g = p->sub.get();
+    TM_TRY(g.prof.collect());  // the static sieve's events, recorded on g
     return Status();
 }
 

@@ -130,7 +130,7 @@ __device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthr
 // Lookup side.  The table must start on a 2 KB boundary of shared memory, so
 // that its shared address has bits 0..10 clear: the address of entry b of row
 // i is then (address | (b' << 3)) + 128 i, where b' = b ^ 2(i & 7) is the
-// swizzled column.  XORing s with 0xECA86420ECA86420 (nibble i of the
+// swizzled column.  XORing s once with 0xECA86420ECA86420 (nibble i of the
 // constant is 2(i & 7)) swizzles all sixteen nibbles at once.  Two masked
 // shifts per 32-bit half place every nibble, times 8, in a byte of its own
 // (even nibbles in one word, odd nibbles in the other); one byte permute per
@@ -141,13 +141,11 @@ __device__ __forceinline__ void gf_table_build(u64 *tab, u64 y, int tt, int nthr
 __device__ __forceinline__ u64 gf_table_mul(const u64 *tab, u64 s)
 {
     const u32 ta = (u32)__cvta_generic_to_shared(tab);
-    const u32 lo = (u32)s, hi = (u32)(s >> 32);
-    // byte j of e* / o*: nibble 2j / 2j+1 of the half, swizzled, times 8.  The
-    // swizzle XOR with 0xECA86420 commutes with the shift and the mask, so it
-    // folds into the mask step as a constant: ((w ^ K) << 3) & M =
-    // ((w << 3) & M) ^ 0x60402000 and ((w ^ K) >> 1) & M = ((w >> 1) & M) ^ 0x70503010.
-    const u32 el = ((lo << 3) & 0x78787878u) ^ 0x60402000u, ol = ((lo >> 1) & 0x78787878u) ^ 0x70503010u;
-    const u32 eh = ((hi << 3) & 0x78787878u) ^ 0x60402000u, oh = ((hi >> 1) & 0x78787878u) ^ 0x70503010u;
+    const u64 sw = s ^ 0xECA86420ECA86420ull;
+    const u32 lo = (u32)sw, hi = (u32)(sw >> 32);
+    // byte j of e* / o*: nibble 2j / 2j+1 of the half, times 8
+    const u32 el = (lo << 3) & 0x78787878u, ol = (lo >> 1) & 0x78787878u;
+    const u32 eh = (hi << 3) & 0x78787878u, oh = (hi >> 1) & 0x78787878u;
     // byte 0 from the nibble word, bytes 1..3 from the table address
 #define TM_NIB(w, j) __byte_perm((w), ta, 0x7650u + (j))
     u64 v0, v1, v2, v3, v4, v5, v6, v7, v8, v9, v10, v11, v12, v13, v14, v15;

@@ -72,9 +72,9 @@ def test_speed_of_light_model():
 
 def test_default_legs_and_switches():
     a = bench.parse_args([])
-    assert bench.legs_of(a) == {"large10", "transit", "batch", "serving", "cpu"} and a.serving_requests == 4096
+    assert bench.legs_of(a) == {"large10", "large5", "transit", "batch", "serving", "cpu"} and a.serving_requests == 4096
     a = bench.parse_args(["--no-serving", "--no-cpu-baseline"])
-    assert bench.legs_of(a) == {"large10", "transit", "batch"}
+    assert bench.legs_of(a) == {"large10", "large5", "transit", "batch"}
     assert bench.legs_of(bench.parse_args(["--legs", ""])) == set()
 
 
