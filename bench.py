@@ -105,7 +105,7 @@ def probe_rates(tm, iters=2048, repeats=3):
 # layer-kernel sources it was taken on (source_sha() below, first 16 hex):
 # a timed-decision layer of the default workload, full size, one-pass dram
 # counters
-LAYER_TRAFFIC = {"source_sha": "d47a2aedf1086717", "bytes_per_launch": 1125220352 + 399725824}
+LAYER_TRAFFIC = {"source_sha": "52733b1dac2c775b", "bytes_per_launch": 1124556544 + 399504640}
 
 
 def parse_args(argv=None):

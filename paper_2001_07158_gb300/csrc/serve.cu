@@ -117,7 +117,33 @@ public:
         status_dev_.release();
         if (host_params_) cudaFreeHost(host_params_);
         if (status_host_) cudaFreeHost(status_host_);
+        for (auto &b : pinned_) cudaFreeHost(b.first);
         prof.destroy();
+    }
+
+    // Pinned host blocks move from finished jobs to the next ones instead of
+    // being freed: cudaFreeHost waits for the whole device, which would hold
+    // one server lane up behind the other lane's work.
+    void lend_pinned(SJob &sj)
+    {
+        if (sj.ws.host_pinned) return;
+        if (!pinned_.empty()) {
+            sj.ws.host_pinned = pinned_.back().first;
+            sj.ws.host_pinned_bytes = pinned_.back().second;
+            pinned_.pop_back();
+        } else if (cudaMallocHost(&sj.ws.host_pinned, kPinnedBlock) == cudaSuccess) {
+            sj.ws.host_pinned_bytes = kPinnedBlock;
+        } else {
+            sj.ws.host_pinned = nullptr;  // the job's own readout path allocates (or reports OOM)
+            cudaGetLastError();
+        }
+    }
+    void recycle(SJob &sj)
+    {
+        if (!sj.ws.host_pinned) return;
+        pinned_.push_back({sj.ws.host_pinned, sj.ws.host_pinned_bytes});
+        sj.ws.host_pinned = nullptr;
+        sj.ws.host_pinned_bytes = 0;
     }
 
     Status init()
@@ -143,6 +169,7 @@ public:
     Status admit(std::unique_ptr<SJob> sj, size_t reserved, std::vector<std::unique_ptr<SJob>> *done)
     {
         sj->reserved = reserved;
+        lend_pinned(*sj);
         sj->ws.set_stream(prep_st_);
         sj->job.ws = &sj->ws;
         sj->job.st = prep_st_;
@@ -288,6 +315,8 @@ private:
     void *host_params_ = nullptr;
     DevBuf status_dev_;           // the device status word taken after each step ...
     u32 *status_host_ = nullptr;  // ... and its pinned host copy
+    static const size_t kPinnedBlock = 64 * 1024;
+    std::vector<std::pair<void *, size_t>> pinned_;  // pinned blocks of finished jobs
 };
 
 size_t default_budget()
@@ -385,7 +414,10 @@ extern "C" int tmotif_decide_batch(const tmotif_graph_t *graphs, const tmotif_qu
             }
             s = sched.step(&done);
             if (!s.ok()) return s.code;
-            for (auto &sj : done) finish(sj);
+            for (auto &sj : done) {
+                finish(sj);
+                sched.recycle(*sj);
+            }
             done.clear();
         }
         cudaEventRecord(e1, st);
@@ -680,6 +712,7 @@ void Lane::run()
             if (st == NJ_JOB) waiting.push_front({r, std::move(nj)});
             else if (st == NJ_NONE) finish_extract(r);
         }
+        for (auto &sj : done) sched->recycle(*sj);
         done.clear();
     }
 }
