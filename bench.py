@@ -318,6 +318,9 @@ def roofline_of(stats, total_ms, costs, rates, traffic):
                      "traffic); bound = max(table-form time, register-form time); binding form: "
                      + max(forms, key=forms.get),
             "probe_products_per_s": rates, "form_ms": {k: v * 1e3 for k, v in forms.items()},
+            # not a bound: the two forms' times back to back, for comparison
+            # with the measured launch (equal when the forms do not overlap)
+            "forms_sum_ms": sum(forms.values()) * 1e3,
             "layer_ms_per_launch": layer_ms, "gf_muls_per_launch": muls, "table_muls_per_launch": tmuls,
             "table_builds_per_launch": builds, "algorithmic_bytes_per_launch": stats["layer_bytes"] / nl,
             "achieved_hbm_gbs": stats["layer_bytes"] / nl / (layer_ms / 1e3) / 1e9,
