@@ -623,10 +623,16 @@ def run_reference(args):
     return 0
 
 
-def run_leg(line, name, fn):
-    """Run one extra workload; a failure is recorded in the line, not raised."""
+def run_leg(line, name, fn, tm=None):
+    """Run one extra workload; a failure is recorded in the line, not raised.
+    With tm, the leg also reports the most device memory the library's pool
+    held during it (peak_hbm_bytes)."""
     try:
+        if tm is not None:
+            tm.tmotif_memory_stats(reset=True)
         line[name] = fn()
+        if tm is not None:
+            line[name]["peak_hbm_bytes"] = tm.tmotif_memory_stats()["used_high"]
     except Exception as e:  # noqa: BLE001 -- the headline line must still print
         import traceback
 
@@ -656,6 +662,7 @@ def run_ours(args):
     seed = q.seed + 7919 * rank
     work_units = g.m * q.k * (1 << q.k)
 
+    tm.tmotif_memory_stats(reset=True)
     G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
     if args.layer_shape:
         chunk, variant = (int(x) for x in args.layer_shape.split(","))
@@ -693,7 +700,8 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
                        "parallelism": f"replicas x{world} (independent queries)"},
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": int(stats["launches"]), "paper": PAPER}
+            "gpu_launches": int(stats["launches"]), "paper": PAPER,
+            "peak_hbm_bytes": tm.tmotif_memory_stats()["used_high"]}
     G.close()
     legs = legs_of(args) if (world == 1 and args.workload == "mid" and args.scale == 1.0) else set()
     if rank == 0 and "cpu" in legs:
@@ -702,13 +710,13 @@ def run_ours(args):
     leg_steps, leg_warmup = max(3, min(args.steps, 5)), 3
     for name in ("large10", "large5"):
         if name in legs:
-            run_leg(line, name, lambda: large_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup, name))
+            run_leg(line, name, lambda: large_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup, name), tm)
     if "transit" in legs:
-        run_leg(line, "transit", lambda: transit_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup))
+        run_leg(line, "transit", lambda: transit_leg(tm, stream, dev, costs, rates, leg_steps, leg_warmup), tm)
     if "batch" in legs:
-        run_leg(line, "batch", lambda: batch_leg(tm, stream, dev, leg_steps, leg_warmup))
+        run_leg(line, "batch", lambda: batch_leg(tm, stream, dev, leg_steps, leg_warmup), tm)
     if "serving" in legs:
-        run_leg(line, "serving", lambda: serving_benchmark(tm, stream, requests=args.serving_requests))
+        run_leg(line, "serving", lambda: serving_benchmark(tm, stream, requests=args.serving_requests), tm)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -60,7 +60,8 @@ enum {
     TMOTIF_ERR_TIMEOUT = 4,     /* a bounded device or host wait gave up    */
     TMOTIF_ERR_UNSUPPORTED = 5, /* outside the supported range (e.g. k = 1) */
     TMOTIF_ERR_NOT_FOUND = 6,   /* unknown ticket                           */
-    TMOTIF_ERR_BUSY = 7         /* over the admission budget; retry later   */
+    TMOTIF_ERR_BUSY = 7,        /* over the admission budget; retry later   */
+    TMOTIF_ERR_CANCELLED = 8    /* the request was cancelled (tmotif_cancel) */
 };
 
 typedef struct tmotif_graph *tmotif_graph_t;   /* opaque, library-owned */
@@ -256,6 +257,13 @@ int tmotif_poll(tmotif_server_t s, uint64_t ticket, tmotif_decision *out, uint32
  * polled or waited for again); otherwise as tmotif_poll with done = 1. */
 int tmotif_wait(tmotif_server_t s, uint64_t ticket, uint32_t timeout_ms, tmotif_decision *out, uint32_t *verts,
                 uint32_t *times);
+/* Cancel a request.  One not yet admitted is dropped; one whose decisions are
+ * running stops after its current decision (a decision already on the
+ * device is not interrupted).  Either way it then completes with
+ * TMOTIF_ERR_CANCELLED, which tmotif_poll / tmotif_wait report once (then
+ * the ticket is forgotten).  A request that had already finished keeps its
+ * result.  NOT_FOUND for an unknown ticket. */
+int tmotif_cancel(tmotif_server_t s, uint64_t ticket);
 void tmotif_server_destroy(tmotif_server_t s);
 
 /* Profiling counters for a graph (see tmotif_stats).  set_profiling(g, 1)
@@ -331,6 +339,25 @@ int tmotif_decide_noalloc(const uint32_t *d_src, const uint32_t *d_dst, const ui
                           const uint32_t *d_color, uint32_t n, uint32_t num_colors, const tmotif_query *q,
                           uint64_t *d_per_point, void *cuda_stream);
 
+/* Device memory of the library's stream-ordered pool on the current device
+ * (graphs, workspaces and server jobs all draw on it): bytes in use now, the
+ * most in use since the last reset, and bytes the pool holds from the device
+ * (freed blocks stay cached for reuse).  Any pointer may be NULL; reset = 1
+ * restarts the high-water mark.  Errors: CUDA. */
+int tmotif_memory_stats(uint64_t *used, uint64_t *used_high, uint64_t *reserved, int reset);
+
+/* The autotuner's launch shapes for the whole process (per device, lane width
+ * and layer size class; see tmotif_set_layer_shape), as text: one line
+ * "device L log2_arcs chunk variant" per shape, so that a later process can
+ * start from them instead of tuning again.
+ *   export: writes at most cap - 1 bytes of the text and a NUL to buf (cap =
+ *   0: nothing written) and the text's full length to *len;
+ *   import: adds the lines' shapes, replacing those with the same key;
+ *   blank lines are skipped.  INVALID for a malformed line or a shape the
+ *   kernels do not accept; nothing is added then. */
+int tmotif_tuner_export(char *buf, size_t cap, size_t *len);
+int tmotif_tuner_import(const char *text);
+
 /* 1 for the checked build (libtmotif_checked.so, compiled with
  * -DTMOTIF_CHECKED), 0 otherwise.  The checked build tests, on the device,
  * the indices the kernels derive from their inputs (vertex ids of arcs, in-
@@ -340,6 +367,14 @@ int tmotif_decide_noalloc(const uint32_t *d_src, const uint32_t *d_dst, const ui
  * of both builds reads the status word after its work (a failed staged bulk
  * copy wait gives TMOTIF_ERR_TIMEOUT). */
 uint32_t tmotif_checked_build(void);
+
+/* Checked build only (UNSUPPORTED otherwise): on = 1 makes every later
+ * staged layer launch (tmotif_set_layer_shape variant 4) expect 16 bytes more
+ * than its bulk copies bring, so each of its bounded waits (0.1 s in this
+ * build) runs out: the copies land and nothing stays in flight, the teams
+ * finish from global memory, and the call reports TMOTIF_ERR_TIMEOUT.  This
+ * is the test of the timeout path; on = 0 restores normal launches. */
+int tmotif_debug_stage_timeout(int on);
 
 /* Message for the last error on the calling thread (never NULL). */
 const char *tmotif_last_error(void);

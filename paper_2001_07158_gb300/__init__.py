@@ -23,7 +23,8 @@ TMOTIF_KMAX = 20
 TMOTIF_EXTRACT_HALVING = 1
 TMOTIF_EXTRACT_OPTIMUM = 2
 TMOTIF_PREPROCESS_STATIC = 4
-ERRORS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "NOT_FOUND", 7: "BUSY"}
+ERRORS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "NOT_FOUND", 7: "BUSY",
+          8: "CANCELLED"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 # TMOTIF_LIB selects another build of the library (the checked build,
@@ -88,6 +89,7 @@ def _load():
         "tmotif_submit": (C.c_int, [P, P, C.POINTER(_Query), C.c_int, C.POINTER(C.c_uint64)]),
         "tmotif_poll": (C.c_int, [P, C.c_uint64, C.POINTER(_Decision), P, P, C.POINTER(C.c_int)]),
         "tmotif_wait": (C.c_int, [P, C.c_uint64, C.c_uint32, C.POINTER(_Decision), P, P]),
+        "tmotif_cancel": (C.c_int, [P, C.c_uint64]),
         "tmotif_server_destroy": (None, [P]),
         "tmotif_set_profiling": (C.c_int, [P, C.c_int]),
         "tmotif_set_layer_shape": (C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32]),
@@ -97,6 +99,11 @@ def _load():
         "tmotif_gf_probe": (C.c_int, [C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
         "tmotif_decide_noalloc": (C.c_int, [P, P, P, C.c_uint64, P, C.c_uint32, C.c_uint32, C.POINTER(_Query), P, P]),
         "tmotif_checked_build": (C.c_uint32, []),
+        "tmotif_debug_stage_timeout": (C.c_int, [C.c_int]),
+        "tmotif_memory_stats": (C.c_int, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                          C.c_int]),
+        "tmotif_tuner_export": (C.c_int, [C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+        "tmotif_tuner_import": (C.c_int, [C.c_char_p]),
         "tmotif_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -335,9 +342,36 @@ def tmotif_gf_probe(method: int, iters: int = 256):
     return ms.value, n.value
 
 
+def tmotif_memory_stats(reset=False) -> dict:
+    """Device memory of the library's pool: used, used_high (since the last
+    reset) and reserved bytes; reset restarts the high-water mark."""
+    u, h, r = C.c_uint64(0), C.c_uint64(0), C.c_uint64(0)
+    _check(_lib.tmotif_memory_stats(C.byref(u), C.byref(h), C.byref(r), int(bool(reset))))
+    return {"used": u.value, "used_high": h.value, "reserved": r.value}
+
+
+def tmotif_tuner_export() -> str:
+    """The autotuner's shapes as text lines "device L log2_arcs chunk variant"."""
+    n = C.c_size_t(0)
+    _check(_lib.tmotif_tuner_export(None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value + 1)
+    _check(_lib.tmotif_tuner_export(buf, n.value + 1, C.byref(n)))
+    return buf.value.decode()
+
+
+def tmotif_tuner_import(text: str):
+    _check(_lib.tmotif_tuner_import(text.encode()))
+
+
 def tmotif_checked_build() -> bool:
     """True when the loaded library is the checked build (device bounds checks)."""
     return bool(_lib.tmotif_checked_build())
+
+
+def tmotif_debug_stage_timeout(on: bool):
+    """Checked build only: force the staged layer form's bounded waits to run
+    out (the test of the timeout path)."""
+    _check(_lib.tmotif_debug_stage_timeout(int(bool(on))))
 
 
 def tmotif_last_error() -> str:
@@ -418,6 +452,12 @@ def tmotif_wait(s: Server, ticket: int, k: int, timeout_ms: int):
     _check(rc)
     return (Decision(bool(d.found), int(d.sieve_sum), None if pp is None else pp[:npts], float(d.ms)), verts[:k],
             times[:k - 1])
+
+
+def tmotif_cancel(s: Server, ticket: int):
+    """Cancel a request (it then completes with TmotifError CANCELLED = 8,
+    unless it had already finished)."""
+    _check(_lib.tmotif_cancel(s.handle, ticket))
 
 
 def tmotif_server_destroy(s: Server):

@@ -92,6 +92,33 @@ Status device_headroom(size_t *bytes)
     return Status();
 }
 
+bool layer_shape_valid(u32 L, u32 chunk, u32 variant)
+{
+    const bool pow2 = L >= 4 && L <= 128 && (L & (L - 1)) == 0;
+    const bool ch = chunk == 64 || chunk == 128 || chunk == 256 || chunk == 512 || chunk == 1024;
+    const bool var = variant == 0 || (variant <= 2 && (L == 16 || L == 64)) || (variant == 3 && L == 32) ||
+                     (variant == 1 && L == 128) || (variant == 4 && (L == 32 || L == 64 || L == 128));
+    return pow2 && ch && var;
+}
+
+Status memory_stats(u64 *used, u64 *used_high, u64 *reserved, bool reset)
+{
+    cudaMemPool_t pool;
+    TM_TRY(pool_for_current_device(&pool));
+    unsigned long long u = 0, h = 0, r = 0;
+    TM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+    TM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &h));
+    TM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r));
+    if (used) *used = u;
+    if (used_high) *used_high = h;
+    if (reserved) *reserved = r;
+    if (reset) {
+        unsigned long long zero = 0;  // the high-water mark restarts from the current use
+        TM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    return Status();
+}
+
 void dev_free(void *p, cudaStream_t s)
 {
     if (p) cudaFreeAsync(p, s);
@@ -559,14 +586,6 @@ int tmotif_set_profiling(tmotif_graph_t g, int on)
     return TMOTIF_OK;
 }
 
-static bool valid_shape(uint32_t L, uint32_t chunk, uint32_t variant)
-{
-    const bool pow2 = L >= 4 && L <= 128 && (L & (L - 1)) == 0;
-    const bool ch = chunk == 64 || chunk == 128 || chunk == 256 || chunk == 512 || chunk == 1024;
-    const bool var = variant == 0 || (variant <= 2 && (L == 16 || L == 64)) || (variant == 3 && L == 32) ||
-                     (variant == 1 && L == 128) || (variant == 4 && (L == 32 || L == 64 || L == 128));
-    return pow2 && ch && var;
-}
 
 uint32_t tmotif_checked_build(void)
 {
@@ -580,7 +599,7 @@ uint32_t tmotif_checked_build(void)
 int tmotif_set_layer_shape(tmotif_graph_t g, uint32_t L, uint32_t chunk, uint32_t variant)
 {
     if (!g) return fail(TMOTIF_ERR_INVALID, "null graph").code;
-    if (!valid_shape(L, chunk, variant)) return fail(TMOTIF_ERR_INVALID, "bad layer shape").code;
+    if (!layer_shape_valid(L, chunk, variant)) return fail(TMOTIF_ERR_INVALID, "bad layer shape").code;
     std::lock_guard<std::mutex> lock(layer_tune_mutex());
     g->layer_tune[L] = {chunk, variant};
     return TMOTIF_OK;
@@ -608,6 +627,40 @@ int tmotif_gf_mul_batch(const uint64_t *a, const uint64_t *b, uint64_t *out, uin
 {
     if (n && (!a || !b || !out)) return fail(TMOTIF_ERR_INVALID, "null argument").code;
     return gf_mul_batch((const u64 *)a, (const u64 *)b, (u64 *)out, n).code;
+}
+
+int tmotif_debug_stage_timeout(int on) { return debug_stage_timeout(on != 0).code; }
+
+int tmotif_memory_stats(uint64_t *used, uint64_t *used_high, uint64_t *reserved, int reset)
+{
+    return memory_stats((u64 *)used, (u64 *)used_high, (u64 *)reserved, reset != 0).code;
+}
+
+int tmotif_tuner_export(char *buf, size_t cap, size_t *len)
+{
+    if (!len || (cap && !buf)) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    try {
+        const std::string t = tuner_export();
+        *len = t.size();
+        if (cap) {
+            const size_t n = std::min(cap - 1, t.size());
+            std::memcpy(buf, t.data(), n);
+            buf[n] = 0;
+        }
+        return TMOTIF_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
+}
+
+int tmotif_tuner_import(const char *text)
+{
+    if (!text) return fail(TMOTIF_ERR_INVALID, "null text").code;
+    try {
+        return tuner_import(text).code;
+    } catch (const std::bad_alloc &) {
+        return fail(TMOTIF_ERR_OOM, "host allocation failed").code;
+    }
 }
 
 int tmotif_gf_probe(int method, uint32_t iters, double *ms, uint64_t *products)

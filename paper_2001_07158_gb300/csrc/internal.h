@@ -242,6 +242,9 @@ struct LayerParams {
     // bounds of the checked build: vertices (x rows) and checkpoints (C rows)
     u32 n_vert = 0;
     u64 n_cp = 0;
+    // staged form: bytes added to each copy's expected count (the checked
+    // build's forced-timeout test; 0 otherwise)
+    u32 stage_extra_tx = 0;
 };
 
 // One decision in flight: its query, its device workspace and its progress
@@ -288,6 +291,18 @@ bool tuned_shape(u32 L, u64 mf, std::pair<u32, u32> *shape);
 // Guards every graph's layer_tune map: the server's lanes prepare jobs on
 // one graph from two host threads.
 std::mutex &layer_tune_mutex();
+// A layer launch shape the kernels accept (lane width, arcs per chunk, variant).
+bool layer_shape_valid(u32 L, u32 chunk, u32 variant);
+// The process-wide autotuner shapes as text, one "device L log2_arcs chunk
+// variant" line each; import adds (or replaces) the lines' shapes.
+std::string tuner_export();
+Status tuner_import(const std::string &text);
+// Checked build: the staged layer form's copies are expected to bring 16
+// bytes more than they do, so that every bounded wait runs out (the test of
+// the timeout path).  UNSUPPORTED in the normal build.
+Status debug_stage_timeout(bool on);
+// Device memory of the library's pool on the current device.
+Status memory_stats(u64 *used, u64 *used_high, u64 *reserved, bool reset);
 Status job_batch_begin(Job &j);
 LayerParams job_layer_params(const Job &j);
 Status job_readout_enqueue(Job &j);

@@ -40,8 +40,13 @@ struct StageState {
 
 // A wait on a buffer's mbarrier gives up after this long (ns of the global
 // timer), sets TM_STATUS_STAGE_TIMEOUT and the team reads its arcs from
-// global memory instead.
+// global memory instead.  The checked build waits 0.1 s, so that its test of
+// the timeout path stays short.
+#ifdef TMOTIF_CHECKED
+constexpr unsigned long long STAGE_WAIT_NS = 100000000ull;
+#else
 constexpr unsigned long long STAGE_WAIT_NS = 1000000000ull;
+#endif
 
 __device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
@@ -61,15 +66,19 @@ __device__ __forceinline__ void stage_init(TeamStage *ts)
 
 // Lane 0 of the team: copy arcs [sb, se) (se - sb <= STAGE_ARCS) into buffer b.
 // rec is 16 bytes per arc; time is read from index sb & ~3 up to the next
-// multiple of 4 at or above se, which the workspace pads.
-__device__ __forceinline__ void stage_issue(const uint4 *rec, const u32 *time, TeamStage *ts, int b, u64 sb, u64 se)
+// multiple of 4 at or above se, which the workspace pads.  extra_tx (0 except
+// in the checked build's forced-timeout test) is added to the bytes the
+// barrier expects, so that the copies land but the wait runs out.
+__device__ __forceinline__ void stage_issue(const uint4 *rec, const u32 *time, TeamStage *ts, int b, u64 sb, u64 se,
+                                            u32 extra_tx)
 {
     StageBuf &B = ts->buf[b];
     const u64 t0 = sb & ~3ull, t1 = (se + 3) & ~3ull;
     const u32 nrec = (u32)(se - sb) * 16u, ntime = (u32)(t1 - t0) * 4u;
     const u32 bar = smem_u32(&ts->bar[b]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nrec + ntime) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nrec + ntime + extra_tx)
+                 : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(B.rec)),
                  "l"((unsigned long long)__cvta_generic_to_global(rec + sb)), "r"(nrec), "r"(bar)
@@ -265,7 +274,7 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
     if constexpr (STAGED) {
         const u64 nsub = stop > begin ? (stop - begin + STAGE_ARCS - 1) / STAGE_ARCS : 0;
         if (nsub && !ss->broken) {
-            if (tt == 0) stage_issue(p.rec, p.time, ts, 0, begin, min(begin + STAGE_ARCS, stop));
+            if (tt == 0) stage_issue(p.rec, p.time, ts, 0, begin, min(begin + STAGE_ARCS, stop), p.stage_extra_tx);
             ss->pending |= 1u;
         }
         for (u64 b = 0; b < nsub; b++) {
@@ -273,7 +282,7 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
             const u64 sb = begin + b * STAGE_ARCS, se = min(sb + STAGE_ARCS, stop);
             const int cnt = (int)(se - sb);
             if (b + 1 < nsub && !ss->broken) {  // buffer bi ^ 1 was released at the end of sub-batch b - 1
-                if (tt == 0) stage_issue(p.rec, p.time, ts, bi ^ 1, se, min(se + STAGE_ARCS, stop));
+                if (tt == 0) stage_issue(p.rec, p.time, ts, bi ^ 1, se, min(se + STAGE_ARCS, stop), p.stage_extra_tx);
                 ss->pending |= 1u << (bi ^ 1);
             }
             bool staged = false;

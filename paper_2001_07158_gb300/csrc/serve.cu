@@ -464,6 +464,7 @@ struct Request {
     LocalizedExtract lex;    // localisation procedure
     Clock::time_point t_submit;
     bool done = false;
+    std::atomic<bool> cancelled{false};  // tmotif_cancel: complete with CANCELLED at the next chance
     int code = TMOTIF_OK;
     std::string err;
     int found = 0;
@@ -614,6 +615,11 @@ void Lane::run()
         for (auto it = waiting.begin(); it != waiting.end();) {
             Request *r = it->first;
             std::unique_ptr<SJob> &sj = it->second;
+            if (r->cancelled.load()) {  // dropped before (or between) its decisions
+                complete(r, fail(TMOTIF_ERR_CANCELLED, "request cancelled"));
+                it = waiting.erase(it);
+                continue;
+            }
             if (large && holder && holder != r) {
                 ++it;
                 continue;
@@ -680,6 +686,10 @@ void Lane::run()
                 if (it != srv->reqs.end()) r = it->second.get();
             }
             if (!r) continue;
+            if (r->cancelled.load()) {  // its current decision finished; no more
+                complete(r, fail(TMOTIF_ERR_CANCELLED, "request cancelled"));
+                continue;
+            }
             if (!r->is_extract) {
                 r->found = sj->job.found;
                 r->sieve_sum = sj->job.sieve_sum;
@@ -847,6 +857,17 @@ extern "C" int tmotif_wait(tmotif_server_t s, uint64_t ticket, uint32_t timeout_
     if (!s->done_cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), [r] { return r->done; }))
         return fail(TMOTIF_ERR_TIMEOUT, "request not finished within the timeout").code;
     return take_result(s, s->reqs.find(ticket), out, verts, times);
+}
+
+extern "C" int tmotif_cancel(tmotif_server_t s, uint64_t ticket)
+{
+    if (!s) return fail(TMOTIF_ERR_INVALID, "null argument").code;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(TMOTIF_ERR_NOT_FOUND, "unknown ticket").code;
+    if (!it->second->done) it->second->cancelled.store(true);
+    s->cv.notify_all();
+    return TMOTIF_OK;
 }
 
 extern "C" void tmotif_server_destroy(tmotif_server_t s)

@@ -17,6 +17,8 @@
 // P_{a,1,i} = x_a for all i (the base case, read at i = 0 as well), so layer 2
 // reads x directly.
 #include <algorithm>
+#include <atomic>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <tuple>
@@ -859,6 +861,19 @@ static Status launch_layer_f(cudaStream_t st, const LayerParams &one, const Laye
     return Status();
 }
 
+static std::atomic<u32> g_stage_extra_tx{0};
+
+Status debug_stage_timeout(bool on)
+{
+#ifdef TMOTIF_CHECKED
+    g_stage_extra_tx.store(on ? 16u : 0u);
+    return Status();
+#else
+    (void)on;
+    return fail(TMOTIF_ERR_UNSUPPORTED, "the forced staged-copy timeout exists only in the checked build");
+#endif
+}
+
 // One launch of the staged form (single job, warp teams of LPT lanes per
 // thread): resident blocks only, fed from the team counter.
 template <int LPT, bool INNER>
@@ -879,7 +894,9 @@ static Status launch_staged_f(cudaStream_t st, const LayerParams &one, u64 teams
     }();
     const unsigned grid = (unsigned)std::min<u64>(blocks, (u64)per_sm * sm_count());
     TM_CUDA(cudaMemsetAsync(one.queue, 0, sizeof(unsigned long long), st));
-    k_layer_staged<LPT, INNER><<<grid, threads, STAGED_SMEM, st>>>(one);
+    LayerParams p = one;
+    p.stage_extra_tx = g_stage_extra_tx.load();
+    k_layer_staged<LPT, INNER><<<grid, threads, STAGED_SMEM, st>>>(p);
     return Status();
 }
 
@@ -1042,6 +1059,42 @@ static std::tuple<int, u32, u32> tune_key(u32 L, u64 mf)
     u32 b = 0;
     while ((mf >> (b + 1)) != 0) b++;
     return {dev, L, b};
+}
+
+std::string tuner_export()
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::string out;
+    for (const auto &kv : g_tuned) {
+        char line[96];
+        std::snprintf(line, sizeof(line), "%d %u %u %u %u\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                      std::get<2>(kv.first), kv.second.first, kv.second.second);
+        out += line;
+    }
+    return out;
+}
+
+Status tuner_import(const std::string &text)
+{
+    std::map<std::tuple<int, u32, u32>, std::pair<u32, u32>> add;
+    size_t at = 0;
+    while (at < text.size()) {
+        size_t eol = text.find('\n', at);
+        if (eol == std::string::npos) eol = text.size();
+        const std::string line = text.substr(at, eol - at);
+        at = eol + 1;
+        if (line.find_first_not_of(" \t\r") == std::string::npos) continue;  // blank line
+        int dev = -1;
+        unsigned L = 0, b = 0, chunk = 0, variant = 0;
+        char extra = 0;
+        if (std::sscanf(line.c_str(), "%d %u %u %u %u %c", &dev, &L, &b, &chunk, &variant, &extra) != 5 || dev < 0 ||
+            dev > 255 || b > 63 || !layer_shape_valid(L, chunk, variant))
+            return fail(TMOTIF_ERR_INVALID, "bad tuner line: \"" + line + "\"");
+        add[{dev, L, b}] = {chunk, variant};
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto &kv : add) g_tuned[kv.first] = kv.second;
+    return Status();
 }
 
 bool tuned_shape(u32 L, u64 mf, std::pair<u32, u32> *shape)

@@ -10,7 +10,9 @@ the tiny configuration, a suite of random graphs (directed and undirected,
 start/end vertices, windows), every layer launch shape including the staged
 form, a packed batch and the server run under it in a child process: each
 call must succeed (the status word stays clear) and every per-point sum and
-path must equal the oracle's or the normal build's.
+path must equal the oracle's or the normal build's.  The child also forces the
+staged form's bounded waits to run out once (tmotif_debug_stage_timeout): that
+call must report TIMEOUT, and the next one on the same context must run clean.
 """
 import os
 import subprocess
@@ -86,6 +88,24 @@ for k, L, variants in ((4, 16, (0, 1, 2)), (5, 32, (0, 3, 4)), (6, 64, (0, 1, 2,
         _, _, pp = oracle.decide(*args(g), k, ms, seed=9, nthreads=16)
         assert np.array_equal(ref.per_point, pp)
     G.close()
+
+# the staged form's bounded waits, forced to run out: the call reports
+# TIMEOUT (4), and the next call on the same context runs clean with the same
+# sums
+G = tm.tmotif_create_graph(*args(g))
+ms = [j % 4 for j in range(6)]
+tm.tmotif_set_layer_shape(G, 64, 128, 4)
+ref = tm.tmotif_decide(G, 6, ms, seed=9)
+tm.tmotif_debug_stage_timeout(True)
+try:
+    tm.tmotif_decide(G, 6, ms, seed=9)
+    raise AssertionError("the forced timeout was not reported")
+except tm.TmotifError as e:
+    assert e.code == 4, e
+finally:
+    tm.tmotif_debug_stage_timeout(False)
+assert np.array_equal(tm.tmotif_decide(G, 6, ms, seed=9).per_point, ref.per_point)
+G.close()
 
 # a packed batch and the server, against the decisions alone
 items = synth.config3_batch(num_graphs=40, n_hi=800)

@@ -197,3 +197,36 @@ def test_packed_batch_edge_cases(tm):
         assert np.array_equal(r.per_point, alone.per_point) and r.found == alone.found
     for G, _ in items:
         G.close()
+
+
+def test_server_cancel(tm):
+    # a queue of k = 10 decisions (large requests run one at a time): the last
+    # one is still waiting when it is cancelled and completes with CANCELLED
+    # (8); every request not cancelled equals its decision alone; a request
+    # cancelled after it finished keeps its result; an unknown ticket is
+    # NOT_FOUND
+    g = synth.powerlaw_graph(100000, 1500000, 500, 10, seed=23)
+    G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors)
+    ms = list(range(10))
+    want = [tm.tmotif_decide(G, 10, ms, seed=s).per_point for s in range(1, 12)]
+    small = tm.tmotif_decide(G, 4, ms[:4], seed=3).per_point
+    srv = tm.tmotif_server_create(0)
+    tickets = [tm.tmotif_submit(srv, G, 10, ms, seed=s) for s in range(1, 13)]
+    tm.tmotif_cancel(srv, tickets[-1])
+    for i, t in enumerate(tickets[:-1]):
+        dec, _, _ = tm.tmotif_wait(srv, t, 10, 600000)
+        assert np.array_equal(dec.per_point, want[i]), i
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_wait(srv, tickets[-1], 10, 600000)
+    assert e.value.code == 8
+    # cancelled after it finished: the result stays
+    t = tm.tmotif_submit(srv, G, 4, ms[:4], seed=3)
+    time.sleep(2.0)
+    tm.tmotif_cancel(srv, t)
+    dec, _, _ = tm.tmotif_wait(srv, t, 4, 600000)
+    assert np.array_equal(dec.per_point, small)
+    with pytest.raises(tm.TmotifError) as e:
+        tm.tmotif_cancel(srv, 987654321)
+    assert e.value.code == 6
+    srv.close()
+    G.close()
