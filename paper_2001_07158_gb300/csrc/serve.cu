@@ -612,6 +612,7 @@ void Lane::run()
     // runs one request at a time
     auto admit_waiting = [&]() {
         take_pending();
+        bool blocked = false;  // large lane: the next request does not fit the budget yet
         for (auto it = waiting.begin(); it != waiting.end();) {
             Request *r = it->first;
             std::unique_ptr<SJob> &sj = it->second;
@@ -635,17 +636,17 @@ void Lane::run()
             }
             const size_t need = job_estimate(*sj->job.g, sj->job.q);
             if (!sched->room() || !srv->budget->try_take(need)) {
-                if (large) srv->large_waiting.store(true);
+                blocked = true;
                 break;
             }
-            if (large) {
-                holder = r;
-                srv->large_waiting.store(false);
-            }
+            if (large) holder = r;
             Status s = sched->admit(std::move(sj), need, &done);
             it = waiting.erase(it);
             if (!s.ok()) complete(r, s);
         }
+        // recomputed on every pass, so that a waiting request that is
+        // cancelled or fails does not leave the small lane closed
+        if (large) srv->large_waiting.store(blocked);
     };
     while (!srv->stop.load()) {
         {
