@@ -6,7 +6,10 @@ import os
 import shutil
 import subprocess
 import sys
+import time
+import types
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -93,3 +96,98 @@ def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.source_sha() == base
     p.write_text(text.replace("namespace tmo {", "namespace tmo {\nstatic const int added_code = 1;", 1))
     assert bench.source_sha() != base
+
+
+class _FakeDecision:
+    def __init__(self, found, per_point):
+        self.found = found
+        self.per_point = per_point
+        self.sieve_sum = int(np.bitwise_xor.reduce(per_point)) if len(per_point) else 0
+        self.ms = 0.0
+
+
+class _FakeLibrary:
+    """Stands in for the binding in the serving leg: every request's result
+    is a function of its query, and a request takes 0.1 ms per point of k
+    (the server completes it that long after submission)."""
+
+    def __init__(self, corrupt_ticket=None):
+        self.corrupt = corrupt_ticket
+        self.next = 1
+        self.subs = {}
+
+    @staticmethod
+    def _result(k, ms, seed):
+        rng = np.random.default_rng([int(seed) % (2**32), int(k)] + [int(c) for c in ms])
+        return rng.integers(0, 2**63, 1 << k, dtype=np.uint64)
+
+    def tmotif_create_graph(self, *a, **kw):
+        return types.SimpleNamespace(close=lambda: None)
+
+    def tmotif_decide(self, G, k, ms, seed=1, per_point=True):
+        time.sleep(1e-4 * k)
+        return _FakeDecision(True, self._result(k, ms, seed))
+
+    def tmotif_extract(self, G, k, ms, seed=1):
+        time.sleep(1e-4 * k)
+        v = self._result(k, ms, seed)[:k].astype(np.uint32)
+        return True, v, v[:k - 1]
+
+    def tmotif_server_create(self, budget):
+        return types.SimpleNamespace(close=lambda: None)
+
+    def tmotif_submit(self, srv, G, k, ms, is_extract=False, seed=1):
+        t = self.next
+        self.next += 1
+        self.subs[t] = (time.perf_counter() + 1e-4 * k, k, list(ms), seed, is_extract)
+        return t
+
+    def tmotif_poll(self, srv, t, k):
+        due, k, ms, seed, ex = self.subs[t]
+        if time.perf_counter() < due:
+            return None
+        pp = self._result(k, ms, seed)
+        if t == self.corrupt:
+            pp = pp ^ np.uint64(1)
+        v = pp[:k].astype(np.uint32)
+        return _FakeDecision(True, pp), v, v[:k - 1]
+
+
+def _small_serving(monkeypatch):
+    import synth
+
+    real = synth.config5_serving
+    monkeypatch.setattr(synth, "config5_serving", lambda requests, seed: real(n=2000, m=20000, requests=requests,
+                                                                                seed=seed))
+
+
+def test_serving_leg_summary_on_a_fake_library(monkeypatch):
+    _small_serving(monkeypatch)
+    out = bench.serving_benchmark(_FakeLibrary(), None, requests=48, sample=16)
+    assert out["requests"] == 48 and out["results_match"]
+    assert out["arrival_rate_per_s"] == pytest.approx(out["load"] * out["plain_capacity_estimate_per_s"])
+    for form in ("plain", "served"):
+        s = out[form]
+        assert s["queries_per_s"] > 0 and 0 <= s["p50_ms"] <= s["p99_ms"]
+    sat = out["saturated_queries_per_s"]
+    assert sat["plain"] > 0 and sat["served"] > 0
+    assert sat["served_over_plain"] == pytest.approx(sat["served"] / sat["plain"])
+    assert sum(v["n"] for v in out["by_k"].values()) == 48
+
+
+def test_serving_leg_detects_a_wrong_served_result(monkeypatch):
+    _small_serving(monkeypatch)
+    out = bench.serving_benchmark(_FakeLibrary(corrupt_ticket=5), None, requests=24, sample=8)
+    assert not out["results_match"]
+
+
+def test_failed_leg_is_recorded_not_raised():
+    line = {}
+
+    def boom():
+        raise ValueError("no such workload")
+
+    bench.run_leg(line, "leg", boom)
+    assert line["leg"]["error"].startswith("ValueError") and line["leg"]["where"]
+    bench.run_leg(line, "ok", lambda: {"value": 1})
+    assert line["ok"] == {"value": 1}
