@@ -131,6 +131,8 @@ struct Workspace {
     DevBuf partial;                     // chunks * L u64: per-chunk sieve sums
     DevBuf queue;                       // u64 team counter of the layer launches
     DevBuf rec;                         // m_f x 16 B: {dst, cp_in, cp_out, src} of the staged layer form
+    DevBuf order;                       // n_chunks + 1 u32: heavy-first chunk order, then flags and offsets
+    u32 order_chunk = 0;                // arcs per chunk the order was built for (0: none)
     void *host_pinned = nullptr;        // small pinned readback area
     size_t host_pinned_bytes = 0;
     void release();
@@ -245,6 +247,9 @@ struct LayerParams {
     // staged form: bytes added to each copy's expected count (the checked
     // build's forced-timeout test; 0 otherwise)
     u32 stage_extra_tx = 0;
+    // single-job launches: the order in which teams take chunks (heavy chunks
+    // first), or null for index order
+    const u32 *order = nullptr;
 };
 
 // One decision in flight: its query, its device workspace and its progress

@@ -144,8 +144,8 @@ __device__ __forceinline__ void layer_team(const LayerParams &p, u64 team, u64 *
     static_assert(!STAGED || (T == 32 && TAB && !PACKED), "the staged form takes warp teams of one job");
     const int tt = threadIdx.x % T;
     const u32 team_mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << (((threadIdx.x & 31) / T) * T));
-    const u64 chunk = team / p.lane_groups;
-    if (chunk >= p.n_chunks) return;
+    if (team / p.lane_groups >= p.n_chunks) return;
+    const u64 chunk = p.order ? p.order[team / p.lane_groups] : team / p.lane_groups;
     const u32 lane0 = (u32)(team % p.lane_groups) * (LPT * T) + LPT * tt;
     if (!TM_IN(lane0 + LPT - 1, p.L, p.status)) return;
     const u64 Lw = p.L;

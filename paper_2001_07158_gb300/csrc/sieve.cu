@@ -282,6 +282,37 @@ __global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in,
 }
 
 // ---------------------------------------------------------------------------
+// Chunk order of single-job layer launches: a chunk is heavy when its arc
+// range, extended to whole in-segments as the layer team extends it, holds
+// more than twice the chunk size (a long in-segment starts in it).  Teams take
+// heavy chunks first, so that a long segment never starts last and keeps one
+// team busy after the others have run out of work.
+// ---------------------------------------------------------------------------
+__global__ void k_chunk_heavy(u64 mf, u64 n_chunks, u32 chunk, const u32 *dst, const u32 *seg_hi, u32 *flag)
+{
+    const u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n_chunks) return;
+    if (c == n_chunks) { flag[c] = 0; return; }
+    const u64 b0 = c * chunk, b1 = min(b0 + chunk, mf);
+    u64 begin = b0, stop = b1;
+    if (b0 > 0 && dst[b0] == dst[b0 - 1]) begin = seg_hi[dst[b0]];
+    if (b1 < mf && dst[b1] == dst[b1 - 1]) stop = seg_hi[dst[b1]];
+    flag[c] = (stop > begin && stop - begin > 2ull * chunk) ? 1u : 0u;
+}
+
+// off[] holds the exclusive offsets of the heavy flags (n_chunks + 1 entries,
+// off[n_chunks] = number of heavy chunks): heavy chunks first, then the others,
+// each group in index order.
+__global__ void k_chunk_order(u64 n_chunks, const u32 *off, u32 *order)
+{
+    const u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chunks) return;
+    const u32 o = off[c];
+    const bool heavy = off[c + 1] != o;
+    order[heavy ? o : off[n_chunks] + (u32)(c - o)] = (u32)c;
+}
+
+// ---------------------------------------------------------------------------
 // Coefficients (Lemma 6.5, eq. motif:1)
 // ---------------------------------------------------------------------------
 // W_d^A = sum_{j in A} w_{d,j} for slots d < k and lanes of the batch.
@@ -644,6 +675,7 @@ Status job_prep(Job &j)
     TM_CUDA(cudaMemcpyAsync(w.slot_count.p, sc.data(), g.num_colors * 4, cudaMemcpyHostToDevice, st));
     u32 *d_cnt = w.counters.as<u32>();
 
+    w.order_chunk = 0;  // the chunk order belongs to the previous query's arcs
     // filter arcs (Sec. 8.1 (i): colours outside M, masked vertices, window)
     cudaEvent_t pa = nullptr;
     TM_TRY(j.prof->begin(st, &pa));
@@ -807,6 +839,7 @@ LayerParams job_layer_params(const Job &j)
     lp.rec = w.rec.as<uint4>();
     lp.n_vert = j.g->n;
     lp.n_cp = j.ncp;
+    lp.order = (w.order_chunk == j.chunk && w.order_chunk != 0) ? w.order.as<u32>() : nullptr;
     u32 *status = nullptr;
     if (status_word(&status).ok()) lp.status = status;
     return lp;
@@ -974,9 +1007,34 @@ static void count_layer(Profiler *prof, const Job &j, u32 lane_groups)
     }
 }
 
-// One job's layer launch in its own (tuned or pinned) shape.
-static Status launch_one(cudaStream_t st, const Job &j, Profiler *prof)
+// The heavy-first chunk order of a job's layer launches at its current chunk
+// size, built once per (query, chunk size) for launches of at least
+// ORDER_MIN_CHUNKS chunks (3 small launches on the job's stream).
+static const u64 ORDER_MIN_CHUNKS = 1024;
+
+static Status ensure_order(Job &j)
 {
+    Workspace &w = *j.ws;
+    if (j.n_chunks < ORDER_MIN_CHUNKS || w.order_chunk == j.chunk) return Status();
+    const u64 nc = j.n_chunks;
+    TM_TRY(w.order.reserve((2 * nc + 1) * 4));
+    u32 *flag = w.order.as<u32>() + nc;  // nc + 1 flags, then offsets
+    k_chunk_heavy<<<grid_for(nc + 1, 256), 256, 0, j.st>>>(j.mf, nc, j.chunk, w.f_dst.as<u32>(), w.seg_hi.as<u32>(),
+                                                          flag);
+    TM_CUDA(cudaGetLastError());
+    TM_TRY(exclusive_scan_on(j.st, w.block_sums, flag, nc + 1, w.counters.as<u32>() + 13,
+                             (u64 *)&j.prof->stats.launches));
+    k_chunk_order<<<grid_for(nc, 256), 256, 0, j.st>>>(nc, flag, w.order.as<u32>());
+    TM_CUDA(cudaGetLastError());
+    j.prof->stats.launches += 2;
+    w.order_chunk = j.chunk;
+    return Status();
+}
+
+// One job's layer launch in its own (tuned or pinned) shape.
+static Status launch_one(cudaStream_t st, Job &j, Profiler *prof)
+{
+    TM_TRY(ensure_order(j));
     cudaEvent_t la = nullptr;
     TM_TRY(prof->begin(st, &la));
     TM_TRY(launch_layer_class(st, j.L, j.variant, job_layer_params(j), nullptr, nullptr, 0,
@@ -999,8 +1057,8 @@ Status launch_layers(cudaStream_t st, const std::vector<Job *> &jobs, DevBuf &de
     const u32 classes[6] = {4, 8, 16, 32, 64, 128};
     size_t off = 0;
     for (u32 Lc : classes) {
-        std::vector<const Job *> cls;
-        for (const Job *j : jobs)
+        std::vector<Job *> cls;
+        for (Job *j : jobs)
             if (j->L == Lc) cls.push_back(j);
         if (cls.empty()) continue;
         if (cls.size() == 1) {
@@ -1147,6 +1205,7 @@ static Status tune_layer(Job &j)
             j.chunk = c.chunk;
             j.variant = c.variant;
             set_team_shape(j);
+            TM_TRY(ensure_order(j));
             TM_TRY(launch_layer_class(j.st, j.L, j.variant, job_layer_params(j), nullptr, nullptr, 0,
                                       j.n_chunks * j.lane_groups));
             TM_CUDA(cudaGetLastError());
