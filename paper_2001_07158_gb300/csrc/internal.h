@@ -265,6 +265,7 @@ struct Job {
     Profiler *prof = nullptr;
     // sizes known after prep
     u64 mf = 0, ncp = 0, n_act = 0;
+    u32 max_seg = 0;      // longest in-segment among the kept arcs
     u32 L = 0, T = 0, lane_groups = 0, chunk = 128;
     u32 variant = 0;      // layer kernel shape (see the autotuner)
     u64 n_chunks = 0;

@@ -32,7 +32,7 @@ __global__ void k_segments(u64 mf, const u32 *f_dst, u32 *seg_lo, u32 *seg_hi, u
 __global__ void k_pos(u64 mf, const u32 *f_src, const u32 *f_time, const u32 *seg_lo, const u32 *seg_hi, u32 *pos,
                       u32 *mark, u32 n);
 __global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in, u32 *cp_out, const u32 *f_src,
-                              const u32 *f_dst, uint4 *rec);
+                              const u32 *f_dst, uint4 *rec, const u32 *seg_hi, u32 *max_seg);
 
 namespace {
 
@@ -305,7 +305,7 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
             TM_TRY(exclusive_scan_on(st, B.block_sums, B.mark.as<u32>(), mf + 1, d_cnt + 1, launches));
             k_checkpoints<<<blocks_of(mf, 256), 256, 0, st>>>(mf, B.pos.as<u32>(), B.mark.as<u32>(),
                                                               B.cp_in.as<u32>(), B.cp_out.as<u32>(), nullptr, nullptr,
-                                                              nullptr);
+                                                              nullptr, nullptr, nullptr);
             TM_CUDA(cudaGetLastError());
             *launches += 4;
             TM_CUDA(cudaMemcpyAsync(h_cnt + 1, d_cnt + 1, 4, cudaMemcpyDeviceToHost, st));

@@ -265,12 +265,14 @@ __global__ void k_pos(u64 mf, const u32 *f_src, const u32 *f_time, const u32 *se
 }
 
 // mark[] holds exclusive checkpoint numbers (length mf+1).  With rec (the
-// staged layer form), also each arc's record {dst, cp_in, cp_out, src}.
+// staged layer form), also each arc's record {dst, cp_in, cp_out, src}; with
+// max_seg, the longest in-segment (from its first arc and seg_hi).
 __global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in, u32 *cp_out, const u32 *f_src,
-                              const u32 *f_dst, uint4 *rec)
+                              const u32 *f_dst, uint4 *rec, const u32 *seg_hi, u32 *max_seg)
 {
     u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= mf) return;
+    if (max_seg && (e == 0 || f_dst[e - 1] != f_dst[e])) atomicMax(max_seg, seg_hi[f_dst[e]] - (u32)e);
     u32 p = pos[e];
     if (p != NONE && !TM_IN(p, mf, &g_status_word)) return;
     const u32 ci = (p == NONE) ? NONE : ck[p];
@@ -713,6 +715,7 @@ Status job_prep(Job &j)
         TM_CUDA(cudaMemsetAsync(w.seg_lo.p, 0, (u64)n * 4, st));
         TM_CUDA(cudaMemsetAsync(w.seg_hi.p, 0, (u64)n * 4, st));
         TM_CUDA(cudaMemsetAsync(w.mark.p, 0, (mf + 1) * 4, st));
+        TM_CUDA(cudaMemsetAsync(d_cnt + 14, 0, 4, st));
         k_segments<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_dst.as<u32>(), w.seg_lo.as<u32>(), w.seg_hi.as<u32>(),
                                                       n);
         k_pos<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.f_src.as<u32>(), w.f_time.as<u32>(), w.seg_lo.as<u32>(),
@@ -722,14 +725,19 @@ Status job_prep(Job &j)
         TM_TRY(exclusive_scan_on(st, w.block_sums, w.mark.as<u32>(), mf + 1, d_cnt + 1, launches));
         k_checkpoints<<<grid_for(mf, 256), 256, 0, st>>>(mf, w.pos.as<u32>(), w.mark.as<u32>(), w.cp_in.as<u32>(),
                                                          w.cp_out.as<u32>(), w.f_src.as<u32>(), w.f_dst.as<u32>(),
-                                                         w.rec.as<uint4>());
+                                                         w.rec.as<uint4>(), w.seg_hi.as<u32>(), d_cnt + 14);
         *launches += 1;
         TM_CUDA(cudaGetLastError());
         TM_CUDA(cudaMemcpyAsync(h_cnt + 1, d_cnt + 1, 4, cudaMemcpyDeviceToHost, st));
+        TM_CUDA(cudaMemcpyAsync(h_cnt + 14, d_cnt + 14, 4, cudaMemcpyDeviceToHost, st));
     }
     TM_TRY(j.prof->end(st, pa, FAM_PREP));
     TM_CUDA(cudaStreamSynchronize(st));
-    if (j.mf > 0) j.ncp = h_cnt[1];
+    j.max_seg = 0;
+    if (j.mf > 0) {
+        j.ncp = h_cnt[1];
+        j.max_seg = h_cnt[14];
+    }
 
     const u64 npts = q.p_end - q.p_begin;
     j.vals.assign(npts, 0);
@@ -1009,13 +1017,16 @@ static void count_layer(Profiler *prof, const Job &j, u32 lane_groups)
 
 // The heavy-first chunk order of a job's layer launches at its current chunk
 // size, built once per (query, chunk size) for launches of at least
-// ORDER_MIN_CHUNKS chunks (3 small launches on the job's stream).
+// ORDER_MIN_CHUNKS chunks whose longest in-segment exceeds twice the chunk
+// (3 small launches on the job's stream); other launches keep index order.
 static const u64 ORDER_MIN_CHUNKS = 1024;
 
 static Status ensure_order(Job &j)
 {
     Workspace &w = *j.ws;
-    if (j.n_chunks < ORDER_MIN_CHUNKS || w.order_chunk == j.chunk) return Status();
+    // no segment longer than twice the chunk: every chunk is light, and index
+    // order is the order
+    if (j.n_chunks < ORDER_MIN_CHUNKS || j.max_seg <= 2ull * j.chunk || w.order_chunk == j.chunk) return Status();
     const u64 nc = j.n_chunks;
     TM_TRY(w.order.reserve((2 * nc + 1) * 4));
     u32 *flag = w.order.as<u32>() + nc;  // nc + 1 flags, then offsets
