@@ -105,7 +105,7 @@ def probe_rates(tm, iters=2048, repeats=3):
 # layer-kernel sources it was taken on (source_sha() below, first 16 hex):
 # a timed-decision layer of the default workload, full size, one-pass dram
 # counters
-LAYER_TRAFFIC = {"source_sha": "52733b1dac2c775b", "bytes_per_launch": 1124556544 + 399504640}
+LAYER_TRAFFIC = {"source_sha": "af99cd24d0c67306", "bytes_per_launch": 1124856320 + 399602688}
 
 
 def parse_args(argv=None):
