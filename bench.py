@@ -114,7 +114,7 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--legs", default="large10,large5,transit,batch,serving,cpu",
                    help="extra workloads measured after the headline at N = 1 (comma list of large10, large5, "
                         "transit, batch, serving, cpu; empty for none)")
@@ -327,10 +327,12 @@ def roofline_of(stats, total_ms, costs, rates, traffic):
             "layer_share_of_step": stats["layer_ms"] / total_ms if total_ms else None}
 
 
-def e2e_decision(tm, stream, g, q, seed, steps, preprocess=False):
+def e2e_decision(tm, stream, g, q, seed, steps, preprocess=False, warmup=1):
     """End to end through the C ABI with host buffers: upload and build the
     graph from pinned host arrays, decide, read the result back, release;
-    mean seconds per step."""
+    (mean seconds per step, per-step seconds).  `warmup` untimed steps first,
+    as for the device-timed value (the first graph created beside the resident
+    one grows the memory pool once)."""
     import numpy as np
     import torch
 
@@ -343,7 +345,7 @@ def e2e_decision(tm, stream, g, q, seed, steps, preprocess=False):
     cpin = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
     cpin.numpy().view(np.uint32)[:] = g.color
     times = []
-    for i in range(steps):
+    for i in range(-warmup if steps > 0 else 0, steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G2 = tm.tmotif_create_graph(g.n, pin["src"].numpy().view(np.uint32), pin["dst"].numpy().view(np.uint32),
@@ -351,8 +353,9 @@ def e2e_decision(tm, stream, g, q, seed, steps, preprocess=False):
                                     g.num_colors, stream=stream)
         tm.tmotif_decide(G2, q.k, q.multiset, seed=seed + 5000 + i, preprocess=preprocess)
         G2.close()
-        times.append(time.perf_counter() - t0)
-    return statistics.mean(times) if times else float("nan")
+        if i >= 0:
+            times.append(time.perf_counter() - t0)
+    return (statistics.mean(times) if times else float("nan")), times
 
 
 def large_leg(tm, stream, dev, costs, rates, steps, warmup, name="large10"):
@@ -363,14 +366,15 @@ def large_leg(tm, stream, dev, costs, rates, steps, warmup, name="large10"):
     G = tm.tmotif_create_graph(g.n, g.src, g.dst, g.time, g.color, g.num_colors, stream=stream)
     total_ms, found, stats, clocks = measure_decision(tm, stream, dev, G, q, steps, warmup, q.seed)
     G.close()
-    e2e_s = e2e_decision(tm, stream, g, q, q.seed, 1)
+    e2e_s, e2e_steps = e2e_decision(tm, stream, g, q, q.seed, 1)
     work = g.m * q.k * (1 << q.k)
     ms = total_ms / steps
     return {"workload": WORKLOADS[name], "n": g.n, "m": g.m, "k": int(q.k), "steps": steps, "warmup": warmup,
             "ms_per_step": ms, "value": work / (ms / 1e3), "unit": UNIT, "found_all": all(found),
             "clocks": clocks, "roofline": roofline_of(stats, total_ms, costs, rates, None),
             "e2e": {"ms_per_step": e2e_s * 1e3, "value": work / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": 12 * g.m + 4 * g.n + 4 * q.k, "d2h_bytes_per_step": 8 * (1 << q.k) + 16},
+                    "h2d_bytes_per_step": 12 * g.m + 4 * g.n + 4 * q.k, "d2h_bytes_per_step": 8 * (1 << q.k) + 16,
+                    "steps": len(e2e_steps), "warmup": 1},
             "gpu_launches": int(stats["launches"])}
 
 
@@ -683,13 +687,15 @@ def run_ours(args):
                else None)
     roofline = roofline_of(stats, total_ms, costs, rates, traffic)
 
-    e2e_s = e2e_decision(tm, stream, g, q, seed, args.e2e_steps, args.preprocess)
+    e2e_s, e2e_steps = e2e_decision(tm, stream, g, q, seed, args.e2e_steps, args.preprocess)
     e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
     if world > 1:
         torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
     e2e = {"value": world * work_units / float(e2e_t.item()), "unit": UNIT,
            "h2d_bytes_per_step": 12 * g.m + 4 * g.n + 4 * q.k,
-           "d2h_bytes_per_step": 8 * (1 << q.k) + 16, "ms_per_step": float(e2e_t.item()) * 1e3}
+           "d2h_bytes_per_step": 8 * (1 << q.k) + 16, "ms_per_step": float(e2e_t.item()) * 1e3,
+           "steps": len(e2e_steps), "warmup": 1 if e2e_steps else 0,
+           "steps_ms": [round(x * 1e3, 3) for x in e2e_steps]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
