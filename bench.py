@@ -297,6 +297,18 @@ def measure_decision(tm, stream, dev, G, q, steps, warmup, seed, preprocess=Fals
     return total_ms, found, stats, clocks
 
 
+def phases_of(stats, total_ms, steps):
+    """Device time per step by kernel family (the library's CUDA events on the
+    decision's stream; static = the static sieve's layer launches), and the
+    rest of the step: host turnarounds, launch gaps and the launches outside
+    those families."""
+    if not steps:
+        return None
+    out = {f: stats[f + "_ms"] / steps for f in ("prep", "coef", "layer", "other", "static")}
+    out["unprofiled"] = total_ms / steps - sum(out.values())
+    return {k: round(v, 4) for k, v in out.items()}
+
+
 def roofline_of(stats, total_ms, costs, rates, traffic):
     """Roofline of the dominant kernel (the layer kernel), from the library's
     CUDA events around every layer launch during the timed region: achieved
@@ -372,6 +384,7 @@ def large_leg(tm, stream, dev, costs, rates, steps, warmup, name="large10"):
     return {"workload": WORKLOADS[name], "n": g.n, "m": g.m, "k": int(q.k), "steps": steps, "warmup": warmup,
             "ms_per_step": ms, "value": work / (ms / 1e3), "unit": UNIT, "found_all": all(found),
             "clocks": clocks, "roofline": roofline_of(stats, total_ms, costs, rates, None),
+            "phases_ms": phases_of(stats, total_ms, steps),
             "e2e": {"ms_per_step": e2e_s * 1e3, "value": work / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 12 * g.m + 4 * g.n + 4 * q.k, "d2h_bytes_per_step": 8 * (1 << q.k) + 16,
                     "steps": len(e2e_steps), "warmup": 1},
@@ -706,7 +719,8 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
                        "parallelism": f"replicas x{world} (independent queries)"},
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": int(stats["launches"]), "paper": PAPER,
+            "gpu_launches": int(stats["launches"]), "phases_ms": phases_of(stats, total_ms, args.steps),
+            "paper": PAPER,
             "peak_hbm_bytes": tm.tmotif_memory_stats()["used_high"]}
     G.close()
     legs = legs_of(args) if (world == 1 and args.workload == "mid" and args.scale == 1.0) else set()

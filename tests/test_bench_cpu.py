@@ -191,3 +191,13 @@ def test_failed_leg_is_recorded_not_raised():
     assert line["leg"]["error"].startswith("ValueError") and line["leg"]["where"]
     bench.run_leg(line, "ok", lambda: {"value": 1})
     assert line["ok"] == {"value": 1}
+
+
+def test_phases_split_the_step():
+    import bench
+
+    stats = {"prep_ms": 2.0, "coef_ms": 1.0, "layer_ms": 10.0, "other_ms": 0.5, "static_ms": 0.4}
+    ph = bench.phases_of(stats, 14.0, 2)
+    assert ph == {"prep": 1.0, "coef": 0.5, "layer": 5.0, "other": 0.25, "static": 0.2, "unprofiled": 0.05}
+    assert abs(sum(ph.values()) - 7.0) < 1e-9
+    assert bench.phases_of(stats, 14.0, 0) is None
