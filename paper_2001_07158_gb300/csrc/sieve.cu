@@ -272,7 +272,12 @@ __global__ void k_checkpoints(u64 mf, const u32 *pos, const u32 *ck, u32 *cp_in,
 {
     u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= mf) return;
-    if (max_seg && (e == 0 || f_dst[e - 1] != f_dst[e])) atomicMax(max_seg, seg_hi[f_dst[e]] - (u32)e);
+    if (max_seg) {  // one atomic per warp, on the warp's longest segment
+        const u32 len = (e == 0 || f_dst[e - 1] != f_dst[e]) ? seg_hi[f_dst[e]] - (u32)e : 0u;
+        const unsigned act = __activemask();
+        const u32 wmax = __reduce_max_sync(act, len);
+        if (wmax && (threadIdx.x & 31) == (u32)(__ffs(act) - 1)) atomicMax(max_seg, wmax);
+    }
     u32 p = pos[e];
     if (p != NONE && !TM_IN(p, mf, &g_status_word)) return;
     const u32 ci = (p == NONE) ? NONE : ck[p];
@@ -333,6 +338,7 @@ __global__ void k_wtab(u32 k, u32 L, u64 p0, QueryKeys keys, u64 *wtab)
 // x_u^A = sum_{d in S_c(u)} v_{u,d} W_d^A for the active vertices: one warp
 // per vertex; v_{u,d} is common to all lanes, so the warp builds its nibble
 // table once per slot and each lane's product is 16 table loads.
+// Resident warps take vertices v, v + (all warps), ... of the active list.
 __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L, const u32 *color,
                                               const u32 *slot_begin, const u32 *slot_count, QueryKeys keys,
                                               const u64 *wtab, u64 *x, u32 n, u32 num_colors, u32 k)
@@ -340,26 +346,34 @@ __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L,
     __shared__ __align__(2048) u64 tabs[8][256];  // tables on 2 KB boundaries
     u64 *tab = tabs[threadIdx.x >> 5];
     const int tt = threadIdx.x & 31;
-    const u64 v = (u64)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (v >= n_act) return;  // whole warp leaves together
-    const u32 u = list[v];
-    if (!TM_IN(u, n, &g_status_word)) return;
-    const u32 c = color[u];
-    if (!TM_IN(c, num_colors, &g_status_word)) return;
-    const u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
-    if (!TM_IN(d1, k + 1, &g_status_word)) return;
-    u64 s[4] = {0, 0, 0, 0};  // lanes tt, tt + 32, tt + 64, tt + 96 (L <= 128)
-    for (u32 d = d0; d < d1; d++) {
-        __syncwarp();
-        gf_table_build(tab, coef_v(keys, u, d), tt, 32);
-        __syncwarp();
+    const u64 warps = (u64)gridDim.x * 8;
+    for (u64 v = (u64)blockIdx.x * 8 + (threadIdx.x >> 5); v < n_act; v += warps) {  // uniform in the warp
+        const u32 u = list[v];
+        if (!TM_IN(u, n, &g_status_word)) continue;
+        const u32 c = color[u];
+        if (!TM_IN(c, num_colors, &g_status_word)) continue;
+        const u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
+        if (!TM_IN(d1, k + 1, &g_status_word)) continue;
+        u64 s[4] = {0, 0, 0, 0};  // lanes tt, tt + 32, tt + 64, tt + 96 (L <= 128)
+        for (u32 d = d0; d < d1; d++) {
+            __syncwarp();
+            gf_table_build(tab, coef_v(keys, u, d), tt, 32);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if ((u32)tt + 32 * i < L) s[i] ^= gf_table_mul(tab, wtab[(u64)d * L + tt + 32 * i]);
+        }
 #pragma unroll
         for (int i = 0; i < 4; i++)
-            if ((u32)tt + 32 * i < L) s[i] ^= gf_table_mul(tab, wtab[(u64)d * L + tt + 32 * i]);
+            if ((u32)tt + 32 * i < L) x[(u64)u * L + tt + 32 * i] = s[i];
     }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-        if ((u32)tt + 32 * i < L) x[(u64)u * L + tt + 32 * i] = s[i];
+}
+
+// Grid of k_coef: whole blocks of 8 warps, at most COEF_BLOCKS_PER_SM per SM.
+const u64 COEF_BLOCKS_PER_SM = 8;
+unsigned coef_grid(u64 n_act)
+{
+    return (unsigned)std::max<u64>(1, std::min<u64>((n_act + 7) / 8, COEF_BLOCKS_PER_SM * sm_count()));
 }
 
 // ---------------------------------------------------------------------------
@@ -460,16 +474,26 @@ __global__ void __launch_bounds__(256) k_layer_staged(LayerParams one)
             if (ss.pending & (1u << b)) stage_wait(ts, b, (ss.phase >> b) & 1u);
 }
 
-// out[lane] = XOR over chunks of partial[chunk * L + lane]; blockDim.x = L,
-// gridDim.x = chunk slices (each XORs its slice, then one atomic per lane).
-__global__ void k_reduce_partials(const u64 *partial, u64 n_chunks, u32 L, u64 *out)
+// out[lane] ^= XOR over chunks of partial[chunk * L + lane] (L a power of two
+// <= 256).  A block of 256 threads reads 256 / L whole chunk rows per round
+// (thread t: lane t % L of row t / L), rows strided over the grid; the block
+// folds its rows in shared memory and adds one atomic per lane.
+const int REDUCE_THREADS = 256;
+__global__ void __launch_bounds__(REDUCE_THREADS) k_reduce_partials(const u64 *partial, u64 n_chunks, u32 L, u64 *out)
 {
-    const u32 lane = threadIdx.x;
-    const u64 per = (n_chunks + gridDim.x - 1) / gridDim.x;
-    const u64 c0 = blockIdx.x * per, c1 = min(n_chunks, c0 + per);
+    __shared__ u64 red[REDUCE_THREADS];
+    const u32 t = threadIdx.x, rows = REDUCE_THREADS / L;
+    const u64 step = (u64)gridDim.x * rows;
     u64 s = 0;
-    for (u64 c = c0; c < c1; c++) s ^= partial[c * L + lane];
-    if (s) atomicXor(&out[lane], s);
+#pragma unroll 4
+    for (u64 c = (u64)blockIdx.x * rows + t / L; c < n_chunks; c += step) s ^= partial[c * L + t % L];
+    red[t] = s;
+    __syncthreads();
+    for (u32 r = rows / 2; r > 0; r >>= 1) {
+        if (t < r * L) red[t] ^= red[t + r * L];
+        __syncthreads();
+    }
+    if (t < L && red[t]) atomicXor(&out[t], red[t]);
 }
 
 // ---------------------------------------------------------------------------
@@ -654,6 +678,45 @@ size_t job_bytes(const Job &j)
                     ((m + CHUNK_MIN - 1) / CHUNK_MIN) * L * 8 + 4096);
 }
 
+// Lane width of a job: a power of two >= 4, at most LANES_MAX, halved while
+// the lane-proportional buffers (x, two checkpoint buffers of ncp rows, chunk
+// partials) would not fit the device memory left.  Per-point values do not
+// depend on the lane width.
+static Status lane_width(const Job &j, u64 ncp, u32 *out)
+{
+    const Workspace &w = *j.ws;
+    const u64 npts = j.q.p_end - j.q.p_begin;
+    u32 L = 4;
+    while (L < LANES_MAX && L < npts) L <<= 1;
+    size_t room = 0;
+    TM_TRY(device_headroom(&room));
+    room += w.x.bytes + w.C0.bytes + w.C1.bytes + w.partial.bytes;
+    const u64 per_lane = ((u64)j.g->n + 2 * std::max<u64>(ncp, 1) + (j.mf + CHUNK_MIN - 1) / CHUNK_MIN) * 8;
+    while (L > 4 && per_lane * L > room / 10 * 9) L >>= 1;
+    *out = L;
+    return Status();
+}
+
+// Coefficients x_u^A and W_d^A of the lane batch at p0 for repeat r, lane
+// width L, on stream s (2 launches).
+static Status launch_coef(Job &j, cudaStream_t s, u32 L, u64 p0, u32 r)
+{
+    Graph &g = *j.g;
+    Workspace &w = *j.ws;
+    const u32 k = j.q.k;
+    const QueryKeys keys = make_keys(mix64(j.q.seed + (u64)(r + j.rep_offset + 1) * TM_GOLDEN));
+    cudaEvent_t ca = nullptr;
+    TM_TRY(j.prof->begin(s, &ca));
+    k_wtab<<<grid_for((u64)k * L, 128), 128, 0, s>>>(k, L, p0, keys, w.wtab.as<u64>());
+    if (j.n_act)
+        k_coef<<<coef_grid(j.n_act), 256, 0, s>>>((u32)j.n_act, w.act_list.as<u32>(), L, g.d_color,
+                                                  w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
+                                                  w.wtab.as<u64>(), w.x.as<u64>(), g.n, g.num_colors, k);
+    j.prof->stats.launches += 2;
+    TM_CUDA(cudaGetLastError());
+    return j.prof->end(s, ca, FAM_COEF);
+}
+
 Status job_prep(Job &j)
 {
     Graph &g = *j.g;
@@ -678,6 +741,8 @@ Status job_prep(Job &j)
     u32 *d_cnt = w.counters.as<u32>();
 
     w.order_chunk = 0;  // the chunk order belongs to the previous query's arcs
+    j.coef_ready = false;
+    if (w.side_join) TM_CUDA(cudaStreamWaitEvent(st, w.side_join, 0));  // an earlier job's side work
     // filter arcs (Sec. 8.1 (i): colours outside M, masked vertices, window)
     cudaEvent_t pa = nullptr;
     TM_TRY(j.prof->begin(st, &pa));
@@ -698,6 +763,16 @@ Status job_prep(Job &j)
     j.mf = h_cnt[0];
     j.n_act = h_cnt[2];
     j.ncp = 0;
+    // On an early return past the fork, the job's stream still joins the side
+    // stream, so nothing later on it (or a free) overtakes the coefficients.
+    struct JoinSide {
+        cudaStream_t st;
+        cudaEvent_t ev = nullptr;
+        ~JoinSide()
+        {
+            if (ev) cudaStreamWaitEvent(st, ev, 0);
+        }
+    } join{st};
     if (j.mf > 0) {
         const u64 mf = j.mf;
         TM_TRY(w.f_src.reserve(mf * 4));
@@ -710,6 +785,24 @@ Status job_prep(Job &j)
         TM_TRY(w.cp_out.reserve(mf * 4));
         TM_TRY(w.seg_lo.reserve((u64)n * 4));
         TM_TRY(w.seg_hi.reserve((u64)n * 4));
+        {  // repeat 0's first lane batch of coefficients on the side stream, at
+           // the lane width that an upper bound on the checkpoints (every arc)
+           // allows; used if the final width (known after the checkpoints) is
+           // the same
+            u32 L0 = 0;
+            TM_TRY(lane_width(j, mf, &L0));
+            TM_TRY(w.x.reserve((u64)n * L0 * 8));
+            TM_TRY(w.wtab.reserve((u64)q.k * L0 * 8));
+            TM_TRY(w.side_for(st));
+            TM_CUDA(cudaEventRecord(w.side_fork, st));
+            TM_CUDA(cudaStreamWaitEvent(w.side, w.side_fork, 0));
+            TM_TRY(launch_coef(j, w.side, L0, q.p_begin, 0));
+            TM_CUDA(cudaEventRecord(w.side_join, w.side));
+            join.ev = w.side_join;
+            j.coef_ready = true;
+            j.coef_L = L0;
+            j.coef_p0 = q.p_begin;
+        }
         TM_TRY(filter_arcs_compact(st, w, g.d_src, g.d_dst, g.d_time, m, w.f_src.as<u32>(), w.f_dst.as<u32>(),
                                    w.f_time.as<u32>(), launches));
         TM_CUDA(cudaMemsetAsync(w.seg_lo.p, 0, (u64)n * 4, st));
@@ -732,6 +825,10 @@ Status job_prep(Job &j)
         TM_CUDA(cudaMemcpyAsync(h_cnt + 14, d_cnt + 14, 4, cudaMemcpyDeviceToHost, st));
     }
     TM_TRY(j.prof->end(st, pa, FAM_PREP));
+    if (join.ev) {  // x and wtab, before any reuse
+        join.ev = nullptr;
+        TM_CUDA(cudaStreamWaitEvent(st, w.side_join, 0));
+    }
     TM_CUDA(cudaStreamSynchronize(st));
     j.max_seg = 0;
     if (j.mf > 0) {
@@ -748,20 +845,10 @@ Status job_prep(Job &j)
     j.sieve_sum = 0;
     j.done = (j.mf == 0);
     if (j.done) return Status();
-    // lane width: power of two >= 4, at most LANES_MAX, halved while the
-    // lane-proportional buffers (x, two checkpoint buffers, chunk partials)
-    // would not fit the device memory left (per-point values do not depend
-    // on the lane width)
-    u32 L = 4;
-    while (L < LANES_MAX && L < npts) L <<= 1;
-    {
-        size_t room = 0;
-        TM_TRY(device_headroom(&room));
-        room += w.x.bytes + w.C0.bytes + w.C1.bytes + w.partial.bytes;
-        const u64 per_lane = ((u64)n + 2 * std::max<u64>(j.ncp, 1) + (j.mf + CHUNK_MIN - 1) / CHUNK_MIN) * 8;
-        while (L > 4 && per_lane * L > room / 10 * 9) L >>= 1;
-    }
+    u32 L = 0;
+    TM_TRY(lane_width(j, j.ncp, &L));
     j.L = L;
+    if (j.coef_L != L) j.coef_ready = false;
     j.chunk = CHUNK;
     j.variant = 0;
     {  // the launch shape pinned or tuned for this graph and lane width, else
@@ -795,23 +882,16 @@ Status job_prep(Job &j)
 
 Status job_batch_begin(Job &j)
 {
-    Graph &g = *j.g;
     Workspace &w = *j.ws;
     const cudaStream_t st = j.st;
-    const u32 L = j.L, k = j.q.k;
-    const QueryKeys keys = make_keys(mix64(j.q.seed + (u64)(j.r + j.rep_offset + 1) * TM_GOLDEN));
-    j.ky = keys.ky;
-    cudaEvent_t ca = nullptr;
-    TM_TRY(j.prof->begin(st, &ca));
-    k_wtab<<<grid_for((u64)k * L, 128), 128, 0, st>>>(k, L, j.p0, keys, w.wtab.as<u64>());
-    if (j.n_act)
-        k_coef<<<(unsigned)((j.n_act + 7) / 8), 256, 0, st>>>((u32)j.n_act, w.act_list.as<u32>(), L, g.d_color,
-                                                               w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
-                                                               w.wtab.as<u64>(), w.x.as<u64>(), g.n, g.num_colors, k);
-    j.prof->stats.launches += 2;
-    TM_CUDA(cudaGetLastError());
+    const u32 L = j.L;
+    j.ky = make_keys(mix64(j.q.seed + (u64)(j.r + j.rep_offset + 1) * TM_GOLDEN)).ky;
+    // prep's side stream computed this batch's coefficients already (the job's
+    // stream waited for them before prep returned)
+    const bool have = j.coef_ready && j.r == 0 && j.p0 == j.coef_p0 && j.coef_L == L;
+    j.coef_ready = false;
+    if (!have) TM_TRY(launch_coef(j, st, L, j.p0, j.r));
     TM_CUDA(cudaMemsetAsync(w.out.p, 0, L * 8, st));
-    TM_TRY(j.prof->end(st, ca, FAM_COEF));
     j.ell = 2;
     return Status();
 }
@@ -1257,8 +1337,10 @@ static Status tune_layer(Job &j)
 Status job_readout_enqueue(Job &j)
 {
     Workspace &w = *j.ws;
-    const unsigned slices = (unsigned)std::min<u64>(j.n_chunks, 128);
-    k_reduce_partials<<<slices, j.L, 0, j.st>>>(w.partial.as<u64>(), j.n_chunks, j.L, w.out.as<u64>());
+    const u64 rows = REDUCE_THREADS / j.L;
+    const unsigned blocks = (unsigned)std::max<u64>(1, std::min<u64>((j.n_chunks + rows - 1) / rows,
+                                                                     (u64)4 * sm_count()));
+    k_reduce_partials<<<blocks, REDUCE_THREADS, 0, j.st>>>(w.partial.as<u64>(), j.n_chunks, j.L, w.out.as<u64>());
     j.prof->stats.launches++;
     TM_CUDA(cudaGetLastError());
     const u64 slot = j.multi_slot ? j.batch_seq : 0;
