@@ -300,9 +300,7 @@ def measure_decision(tm, stream, dev, G, q, steps, warmup, seed, preprocess=Fals
 def phases_of(stats, total_ms, steps):
     """Device time per step by kernel family (the library's CUDA events;
     static = the static sieve's layer launches), and the rest of the step:
-    host turnarounds, launch gaps and the launches outside those families.
-    The first lane batch's coefficients run on a second stream beside prep's
-    arc pipeline, so coef and prep can overlap and the rest can be negative."""
+    host turnarounds, launch gaps and the launches outside those families."""
     if not steps:
         return None
     out = {f: stats[f + "_ms"] / steps for f in ("prep", "coef", "layer", "other", "static")}

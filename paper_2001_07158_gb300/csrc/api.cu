@@ -162,41 +162,8 @@ void Workspace::set_stream(cudaStream_t s)
     for (DevBuf *b : all) b->stream = s;
 }
 
-Status Workspace::side_for(cudaStream_t main)
-{
-    int dev = 0, prio = 0;
-    TM_CUDA(cudaGetDevice(&dev));
-    TM_CUDA(cudaStreamGetPriority(main, &prio));
-    if (side && side_dev == dev && side_prio == prio) return Status();
-    if (side) {
-        TM_CUDA(cudaStreamSynchronize(side));
-        cudaStreamDestroy(side);
-        side = nullptr;
-    }
-    if (side_dev != dev) {  // events belong to the device they were made on
-        if (side_fork) cudaEventDestroy(side_fork);
-        if (side_join) cudaEventDestroy(side_join);
-        side_fork = side_join = nullptr;
-    }
-    if (!side_fork) TM_CUDA(cudaEventCreateWithFlags(&side_fork, cudaEventDisableTiming));
-    if (!side_join) TM_CUDA(cudaEventCreateWithFlags(&side_join, cudaEventDisableTiming));
-    TM_CUDA(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio));
-    side_dev = dev;
-    side_prio = prio;
-    return Status();
-}
-
 void Workspace::release()
 {
-    if (side) {  // its work may still write the buffers freed below
-        cudaStreamSynchronize(side);
-        cudaStreamDestroy(side);
-        side = nullptr;
-    }
-    if (side_fork) cudaEventDestroy(side_fork);
-    if (side_join) cudaEventDestroy(side_join);
-    side_fork = side_join = nullptr;
-    side_dev = -1;
     DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &kbits, &ftiles, &pos,
                      &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list,
                      &arc_sum, &queue, &rec, &order};

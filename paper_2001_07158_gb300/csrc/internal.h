@@ -135,14 +135,6 @@ struct Workspace {
     u32 order_chunk = 0;                // arcs per chunk the order was built for (0: none)
     void *host_pinned = nullptr;        // small pinned readback area
     size_t host_pinned_bytes = 0;
-    // A second stream for the first lane batch's coefficients, which run
-    // beside the arc pipeline of prep: forked after the coefficient buffers
-    // are reserved on the job's stream, joined before anything else on the
-    // job's stream touches them.
-    cudaStream_t side = nullptr;
-    cudaEvent_t side_fork = nullptr, side_join = nullptr;
-    int side_dev = -1, side_prio = 0;
-    Status side_for(cudaStream_t main);  // the side stream, at main's priority on the current device
     void release();
     size_t bytes() const;
     void set_stream(cudaStream_t s);
@@ -291,11 +283,6 @@ struct Job {
     bool localize = false;    // accumulate arc-localised sums at the last layer
     u32 rep_offset = 0;       // repeat index of the first repeat this job evaluates
     u64 batch_seq = 0;    // batch number across repeats (slot index)
-    // coefficients of repeat 0's lane batch at coef_p0, lane width coef_L,
-    // already computed (by prep, on the workspace's side stream)
-    bool coef_ready = false;
-    u32 coef_L = 0;
-    u64 coef_p0 = 0;
 };
 
 // Job steps.  prep: filter, checkpoints, buffer sizing (synchronises the
@@ -460,7 +447,6 @@ Status static_mask(Graph &g, const QuerySpec &q, const uint8_t *d_alive, uint8_t
 Status build_graph_device(const tmotif_graph_desc *d, Graph *g);
 // Streaming multiprocessors of the current device (cached per device).
 int sm_count();
-unsigned coef_grid(u64 n_act);  // grid of k_coef for n_act active vertices
 
 // Device GF multiply of host arrays (diagnostic).
 Status gf_mul_batch(const u64 *a, const u64 *b, u64 *out, u64 n);

@@ -338,7 +338,6 @@ __global__ void k_wtab(u32 k, u32 L, u64 p0, QueryKeys keys, u64 *wtab)
 // x_u^A = sum_{d in S_c(u)} v_{u,d} W_d^A for the active vertices: one warp
 // per vertex; v_{u,d} is common to all lanes, so the warp builds its nibble
 // table once per slot and each lane's product is 16 table loads.
-// Resident warps take vertices v, v + (all warps), ... of the active list.
 __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L, const u32 *color,
                                               const u32 *slot_begin, const u32 *slot_count, QueryKeys keys,
                                               const u64 *wtab, u64 *x, u32 n, u32 num_colors, u32 k)
@@ -346,34 +345,26 @@ __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L,
     __shared__ __align__(2048) u64 tabs[8][256];  // tables on 2 KB boundaries
     u64 *tab = tabs[threadIdx.x >> 5];
     const int tt = threadIdx.x & 31;
-    const u64 warps = (u64)gridDim.x * 8;
-    for (u64 v = (u64)blockIdx.x * 8 + (threadIdx.x >> 5); v < n_act; v += warps) {  // uniform in the warp
-        const u32 u = list[v];
-        if (!TM_IN(u, n, &g_status_word)) continue;
-        const u32 c = color[u];
-        if (!TM_IN(c, num_colors, &g_status_word)) continue;
-        const u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
-        if (!TM_IN(d1, k + 1, &g_status_word)) continue;
-        u64 s[4] = {0, 0, 0, 0};  // lanes tt, tt + 32, tt + 64, tt + 96 (L <= 128)
-        for (u32 d = d0; d < d1; d++) {
-            __syncwarp();
-            gf_table_build(tab, coef_v(keys, u, d), tt, 32);
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-                if ((u32)tt + 32 * i < L) s[i] ^= gf_table_mul(tab, wtab[(u64)d * L + tt + 32 * i]);
-        }
+    const u64 v = (u64)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (v >= n_act) return;  // whole warp leaves together
+    const u32 u = list[v];
+    if (!TM_IN(u, n, &g_status_word)) return;
+    const u32 c = color[u];
+    if (!TM_IN(c, num_colors, &g_status_word)) return;
+    const u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
+    if (!TM_IN(d1, k + 1, &g_status_word)) return;
+    u64 s[4] = {0, 0, 0, 0};  // lanes tt, tt + 32, tt + 64, tt + 96 (L <= 128)
+    for (u32 d = d0; d < d1; d++) {
+        __syncwarp();
+        gf_table_build(tab, coef_v(keys, u, d), tt, 32);
+        __syncwarp();
 #pragma unroll
         for (int i = 0; i < 4; i++)
-            if ((u32)tt + 32 * i < L) x[(u64)u * L + tt + 32 * i] = s[i];
+            if ((u32)tt + 32 * i < L) s[i] ^= gf_table_mul(tab, wtab[(u64)d * L + tt + 32 * i]);
     }
-}
-
-// Grid of k_coef: whole blocks of 8 warps, at most COEF_BLOCKS_PER_SM per SM.
-const u64 COEF_BLOCKS_PER_SM = 8;
-unsigned coef_grid(u64 n_act)
-{
-    return (unsigned)std::max<u64>(1, std::min<u64>((n_act + 7) / 8, COEF_BLOCKS_PER_SM * sm_count()));
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        if ((u32)tt + 32 * i < L) x[(u64)u * L + tt + 32 * i] = s[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -709,7 +700,7 @@ static Status launch_coef(Job &j, cudaStream_t s, u32 L, u64 p0, u32 r)
     TM_TRY(j.prof->begin(s, &ca));
     k_wtab<<<grid_for((u64)k * L, 128), 128, 0, s>>>(k, L, p0, keys, w.wtab.as<u64>());
     if (j.n_act)
-        k_coef<<<coef_grid(j.n_act), 256, 0, s>>>((u32)j.n_act, w.act_list.as<u32>(), L, g.d_color,
+        k_coef<<<(unsigned)((j.n_act + 7) / 8), 256, 0, s>>>((u32)j.n_act, w.act_list.as<u32>(), L, g.d_color,
                                                   w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
                                                   w.wtab.as<u64>(), w.x.as<u64>(), g.n, g.num_colors, k);
     j.prof->stats.launches += 2;
@@ -741,8 +732,6 @@ Status job_prep(Job &j)
     u32 *d_cnt = w.counters.as<u32>();
 
     w.order_chunk = 0;  // the chunk order belongs to the previous query's arcs
-    j.coef_ready = false;
-    if (w.side_join) TM_CUDA(cudaStreamWaitEvent(st, w.side_join, 0));  // an earlier job's side work
     // filter arcs (Sec. 8.1 (i): colours outside M, masked vertices, window)
     cudaEvent_t pa = nullptr;
     TM_TRY(j.prof->begin(st, &pa));
@@ -763,16 +752,6 @@ Status job_prep(Job &j)
     j.mf = h_cnt[0];
     j.n_act = h_cnt[2];
     j.ncp = 0;
-    // On an early return past the fork, the job's stream still joins the side
-    // stream, so nothing later on it (or a free) overtakes the coefficients.
-    struct JoinSide {
-        cudaStream_t st;
-        cudaEvent_t ev = nullptr;
-        ~JoinSide()
-        {
-            if (ev) cudaStreamWaitEvent(st, ev, 0);
-        }
-    } join{st};
     if (j.mf > 0) {
         const u64 mf = j.mf;
         TM_TRY(w.f_src.reserve(mf * 4));
@@ -785,24 +764,6 @@ Status job_prep(Job &j)
         TM_TRY(w.cp_out.reserve(mf * 4));
         TM_TRY(w.seg_lo.reserve((u64)n * 4));
         TM_TRY(w.seg_hi.reserve((u64)n * 4));
-        {  // repeat 0's first lane batch of coefficients on the side stream, at
-           // the lane width that an upper bound on the checkpoints (every arc)
-           // allows; used if the final width (known after the checkpoints) is
-           // the same
-            u32 L0 = 0;
-            TM_TRY(lane_width(j, mf, &L0));
-            TM_TRY(w.x.reserve((u64)n * L0 * 8));
-            TM_TRY(w.wtab.reserve((u64)q.k * L0 * 8));
-            TM_TRY(w.side_for(st));
-            TM_CUDA(cudaEventRecord(w.side_fork, st));
-            TM_CUDA(cudaStreamWaitEvent(w.side, w.side_fork, 0));
-            TM_TRY(launch_coef(j, w.side, L0, q.p_begin, 0));
-            TM_CUDA(cudaEventRecord(w.side_join, w.side));
-            join.ev = w.side_join;
-            j.coef_ready = true;
-            j.coef_L = L0;
-            j.coef_p0 = q.p_begin;
-        }
         TM_TRY(filter_arcs_compact(st, w, g.d_src, g.d_dst, g.d_time, m, w.f_src.as<u32>(), w.f_dst.as<u32>(),
                                    w.f_time.as<u32>(), launches));
         TM_CUDA(cudaMemsetAsync(w.seg_lo.p, 0, (u64)n * 4, st));
@@ -825,10 +786,6 @@ Status job_prep(Job &j)
         TM_CUDA(cudaMemcpyAsync(h_cnt + 14, d_cnt + 14, 4, cudaMemcpyDeviceToHost, st));
     }
     TM_TRY(j.prof->end(st, pa, FAM_PREP));
-    if (join.ev) {  // x and wtab, before any reuse
-        join.ev = nullptr;
-        TM_CUDA(cudaStreamWaitEvent(st, w.side_join, 0));
-    }
     TM_CUDA(cudaStreamSynchronize(st));
     j.max_seg = 0;
     if (j.mf > 0) {
@@ -848,7 +805,6 @@ Status job_prep(Job &j)
     u32 L = 0;
     TM_TRY(lane_width(j, j.ncp, &L));
     j.L = L;
-    if (j.coef_L != L) j.coef_ready = false;
     j.chunk = CHUNK;
     j.variant = 0;
     {  // the launch shape pinned or tuned for this graph and lane width, else
@@ -886,11 +842,7 @@ Status job_batch_begin(Job &j)
     const cudaStream_t st = j.st;
     const u32 L = j.L;
     j.ky = make_keys(mix64(j.q.seed + (u64)(j.r + j.rep_offset + 1) * TM_GOLDEN)).ky;
-    // prep's side stream computed this batch's coefficients already (the job's
-    // stream waited for them before prep returned)
-    const bool have = j.coef_ready && j.r == 0 && j.p0 == j.coef_p0 && j.coef_L == L;
-    j.coef_ready = false;
-    if (!have) TM_TRY(launch_coef(j, st, L, j.p0, j.r));
+    TM_TRY(launch_coef(j, st, L, j.p0, j.r));
     TM_CUDA(cudaMemsetAsync(w.out.p, 0, L * 8, st));
     j.ell = 2;
     return Status();

@@ -376,7 +376,7 @@ Status static_sieve(Graph &g, const QuerySpec &q, const uint8_t *d_alive, u64 *d
     };
     for (u64 p0 = 0; p0 < npts; p0 += L) {
         k_wtab<<<grid_of((u64)k * L, 128), 128, 0, st>>>(k, L, p0, keys, w.wtab.as<u64>());
-        k_coef<<<coef_grid(n_act), 256, 0, st>>>((u32)n_act, w.act_list.as<u32>(), L, g.d_color,
+        k_coef<<<(unsigned)((n_act + 7) / 8), 256, 0, st>>>((u32)n_act, w.act_list.as<u32>(), L, g.d_color,
                                                              w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
                                                              w.wtab.as<u64>(), w.x.as<u64>(), g.n, g.num_colors, k);
         TM_CUDA(cudaMemsetAsync(arr, 0, row * 8 * 2 * (k - 1), st));
