@@ -60,7 +60,7 @@ static Status pool_for_current_device(cudaMemPool_t *out)
 Status dev_alloc(void **p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
-    cudaMemPool_t pool;
+    cudaMemPool_t pool = nullptr;
     TM_TRY(pool_for_current_device(&pool));
     cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 256), pool, s);
     if (e == cudaErrorMemoryAllocation) {
@@ -81,7 +81,7 @@ Status dev_alloc(void **p, size_t bytes, cudaStream_t s)
 Status device_headroom(size_t *bytes)
 {
     *bytes = 0;
-    cudaMemPool_t pool;
+    cudaMemPool_t pool = nullptr;
     TM_TRY(pool_for_current_device(&pool));
     size_t free_b = 0, total_b = 0;
     TM_CUDA(cudaMemGetInfo(&free_b, &total_b));
@@ -103,7 +103,7 @@ bool layer_shape_valid(u32 L, u32 chunk, u32 variant)
 
 Status memory_stats(u64 *used, u64 *used_high, u64 *reserved, bool reset)
 {
-    cudaMemPool_t pool;
+    cudaMemPool_t pool = nullptr;
     TM_TRY(pool_for_current_device(&pool));
     unsigned long long u = 0, h = 0, r = 0;
     TM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
@@ -377,12 +377,15 @@ namespace {
 // With TMOTIF_PREPROCESS_STATIC: the static sieve's kept vertices and the
 // graph of the arcs among them (same vertex ids; Sec. 8.1 (ii) rebuilds the
 // temporal graph on those vertices).  Otherwise the graph itself.
+void delete_subgraph(Graph *x)
+{
+    release_graph_arrays(x);
+    delete x;
+}
+
 struct Prepared {
     Graph *g = nullptr;
-    std::unique_ptr<Graph, void (*)(Graph *)> sub{nullptr, [](Graph *x) {
-                                                      release_graph_arrays(x);
-                                                      delete x;
-                                                  }};
+    std::unique_ptr<Graph, void (*)(Graph *)> sub{nullptr, delete_subgraph};
     double ms = 0;
 };
 

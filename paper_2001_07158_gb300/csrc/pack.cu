@@ -324,8 +324,7 @@ Status run_pack(Graph *const *graphs, const QuerySpec *specs, size_t first, size
             TM_CUDA(cudaGetLastError());
             *launches += 2;
             // layers 2..kmax: each segment follows its own query's k
-            LayerParams lp;
-            std::memset(&lp, 0, sizeof(lp));
+            LayerParams lp{};  // every member zero or null
             lp.src = o_src.as<u32>();
             lp.dst = o_dst.as<u32>();
             lp.time = o_time.as<u32>();
