@@ -259,7 +259,8 @@ void release_graph_arrays(Graph *g)
     dev_free(g->d_dst, g->stream);
     dev_free(g->d_time, g->stream);
     dev_free(g->d_color, g->stream);
-    g->d_src = g->d_dst = g->d_time = g->d_color = nullptr;
+    dev_free(g->d_in_off, g->stream);
+    g->d_src = g->d_dst = g->d_time = g->d_color = g->d_in_off = nullptr;
     dev_free(g->s_in, g->stream);
     dev_free(g->s_out, g->stream);
     g->s_in = g->s_out = nullptr;

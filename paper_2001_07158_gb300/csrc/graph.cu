@@ -408,19 +408,20 @@ Status build_graph_device(const tmotif_graph_desc *d, Graph *g)
         g->pair_hist.assign((size_t)nc * nc, 0);
         TM_CUDA(cudaMemcpyAsync(g->pair_hist.data(), hist.p, (u64)nc * nc * 8, cudaMemcpyDeviceToHost, st));
     }
+    g->n = n;
+    g->m = mk;
+    TM_TRY(build_in_off(*g, st, tiles, d_small + 8));
     TM_CUDA(cudaStreamSynchronize(st));
     tiles.release();
 
-    g->n = n;
     g->m_input = m;
-    g->m = mk;
     g->self_loops = loops;
     g->duplicates = (m - loops) * (und ? 2 : 1) - mk;
     g->num_colors = d->num_colors;
     g->max_time = tmax;
     g->stream = st;
     g->h_color = std::make_shared<std::vector<u32>>(d->color, d->color + n);
-    g->resident_bytes = 3 * mb + (u64)std::max<u32>(n, 1) * 4;
+    g->resident_bytes += 3 * mb + (u64)std::max<u32>(n, 1) * 4;
     return Status();
 }
 

@@ -161,6 +161,7 @@ struct Graph {
     // resident arcs sorted by (dst, time, src)
     u32 *d_src = nullptr, *d_dst = nullptr, *d_time = nullptr;
     u32 *d_color = nullptr;
+    u32 *d_in_off = nullptr;  // n + 1: first arc of each destination's in-segment (null: m >= 2^32 - 1)
     std::shared_ptr<std::vector<u32>> h_color;  // host copy for extraction bookkeeping
     std::vector<u64> pair_hist;         // arcs per (colour(src), colour(dst)), if few colours
     Workspace ws;
@@ -349,9 +350,15 @@ Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_
 // Arc filter (Sec. 8.1 (i)) in two passes: _count leaves the keep mask and
 // tile offsets in the workspace and the kept count in d_total (device u32);
 // after the caller reads the count and sizes the outputs, _compact writes the
-// kept arcs in arc order.
-Status filter_arcs_count(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time, u64 m,
-                         const uint8_t *vflag, const ArcFilter &f, u32 *d_total, u64 *launches);
+// kept arcs in arc order.  in_off: the graph's in-segment offsets (n + 1
+// entries), or null.
+Status filter_arcs_count(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time,
+                         const u32 *in_off, u32 n, u64 m, const uint8_t *vflag, const ArcFilter &f, u32 *d_total,
+                         u64 *launches);
+// The graph's in-segment offsets d_in_off (n + 1 u32; first arc of each
+// destination, arcs sorted by destination), built on st; left null when the
+// arc count does not fit 32 bits.  tiles: scan scratch; d_total: a device u32.
+Status build_in_off(Graph &g, cudaStream_t st, DevBuf &tiles, u32 *d_total);
 Status filter_arcs_compact(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time, u64 m,
                            u32 *o_src, u32 *o_dst, u32 *o_time, u64 *launches);
 

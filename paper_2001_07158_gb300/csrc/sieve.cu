@@ -66,9 +66,14 @@ __global__ void k_active_list(u32 n, const u32 *act, u32 *list)
 //     32j..32j+31) and the tile's kept count;
 //   after an exclusive scan of the tile counts, k_filter_compact writes the
 //     kept arcs, in arc order, from the mask alone.
-// The destination's flag is tested first: arcs are sorted by destination,
-// so those reads are nearly sequential, and the scattered source flag and the
-// time are read only for arcs that pass the tests before them.
+// The destination's flag is tested first.  Arcs are sorted by destination,
+// so a tile spans a run of destinations: with the graph's in-segment offsets
+// (in_off) the tile reads the flags and offsets of those vertices and marks
+// the arcs of flagged ones in shared memory, without reading the arcs'
+// destinations; a tile spanning more vertices than it has arcs (or a graph
+// without offsets) reads each arc's destination instead.  The scattered
+// source flag and the time are read only for arcs that pass the tests before
+// them.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -78,24 +83,60 @@ const int FILTER_TILE = FILTER_THREADS * FILTER_ROUNDS;        // 4096 arcs
 const int FILTER_WORDS = FILTER_TILE / 32;                     // 128 mask words
 
 __global__ void __launch_bounds__(FILTER_THREADS)
-k_filter_count(u64 m, const u32 *src, const u32 *dst, const u32 *time, const uint8_t *vflag, ArcFilter f, u32 *bits,
-               u32 *tile_count)
+k_filter_count(u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32 *in_off, u32 n,
+               const uint8_t *vflag, ArcFilter f, u32 *bits, u32 *tile_count)
 {
     __shared__ u32 warp_count[FILTER_THREADS / 32];
+    __shared__ u32 dmask[FILTER_WORDS];  // bit i: arc base + i has a flagged destination
+    __shared__ u32 vrange[2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u64 base = (u64)blockIdx.x * FILTER_TILE;
+    const u64 end = min(base + (u64)FILTER_TILE, m);
     const bool timed = f.t_min != 0 || f.t_max != 0 || f.n_times != 0;
+    if (threadIdx.x < FILTER_WORDS) dmask[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        vrange[0] = end > base ? dst[base] : 0u;
+        vrange[1] = end > base ? dst[end - 1] : 0u;
+    }
+    __syncthreads();
+    const u32 v0 = vrange[0], v1 = vrange[1];
+    // uniform in the block
+    const bool by_vertex = in_off && end > base && v1 >= v0 && v1 < n && (u64)(v1 - v0) < (u64)FILTER_TILE;
+    if (by_vertex) {
+        for (u64 v = (u64)v0 + threadIdx.x; v <= v1; v += FILTER_THREADS) {
+            if (!vflag[v]) continue;
+            // the vertex's arcs inside the tile, as tile positions [lo, hi)
+            const u64 a = in_off[v], b = in_off[v + 1];
+            const u32 lo = (u32)(max(a, base) - base), hi = (u32)(min(b, end) - base);
+            for (u32 p = lo; p < hi;) {
+                const u32 word = p >> 5, q = min(hi, (word + 1) << 5);
+                const u32 width = q - p;  // 1..32 bits from bit p & 31
+                const u32 bitsw = width == 32 ? 0xffffffffu : (((1u << width) - 1u) << (p & 31));
+                atomicOr(&dmask[word], bitsw);
+                p = q;
+            }
+        }
+        __syncthreads();
+    }
     u32 d[FILTER_ROUNDS];
     bool k[FILTER_ROUNDS];
+    if (by_vertex) {
 #pragma unroll
-    for (int i = 0; i < FILTER_ROUNDS; i++) {
-        const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
-        d[i] = e < m ? dst[e] : 0u;
-    }
+        for (int i = 0; i < FILTER_ROUNDS; i++) {
+            const u32 p = (u32)i * FILTER_THREADS + threadIdx.x;
+            k[i] = base + p < m && ((dmask[p >> 5] >> (p & 31)) & 1u);
+        }
+    } else {
 #pragma unroll
-    for (int i = 0; i < FILTER_ROUNDS; i++) {
-        const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
-        k[i] = e < m && vflag[d[i]];
+        for (int i = 0; i < FILTER_ROUNDS; i++) {
+            const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
+            d[i] = e < m ? dst[e] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < FILTER_ROUNDS; i++) {
+            const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
+            k[i] = e < m && vflag[d[i]];
+        }
     }
 #pragma unroll
     for (int i = 0; i < FILTER_ROUNDS; i++) {
@@ -188,14 +229,15 @@ k_filter_compact(const u32 *__restrict__ src, const u32 *__restrict__ dst, const
 
 // First pass of the arc filter: the keep mask in w.kbits, the tile offsets in
 // w.ftiles and the kept count to d_total (device u32).
-Status filter_arcs_count(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time, u64 m,
-                         const uint8_t *vflag, const ArcFilter &f, u32 *d_total, u64 *launches)
+Status filter_arcs_count(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time,
+                         const u32 *in_off, u32 n, u64 m, const uint8_t *vflag, const ArcFilter &f, u32 *d_total,
+                         u64 *launches)
 {
     const u64 ntiles = std::max<u64>(1, (m + FILTER_TILE - 1) / FILTER_TILE);
     TM_TRY(w.kbits.reserve(ntiles * FILTER_WORDS * 4));
     TM_TRY(w.ftiles.reserve(ntiles * 4));
-    k_filter_count<<<(unsigned)ntiles, FILTER_THREADS, 0, st>>>(m, src, dst, time, vflag, f, w.kbits.as<u32>(),
-                                                                w.ftiles.as<u32>());
+    k_filter_count<<<(unsigned)ntiles, FILTER_THREADS, 0, st>>>(m, src, dst, time, in_off, n, vflag, f,
+                                                                w.kbits.as<u32>(), w.ftiles.as<u32>());
     if (launches) *launches += 1;
     TM_CUDA(cudaGetLastError());
     return exclusive_scan_on(st, w.block_sums, w.ftiles.as<u32>(), ntiles, d_total, launches);
@@ -211,6 +253,32 @@ Status filter_arcs_compact(cudaStream_t st, Workspace &w, const u32 *src, const 
         src, dst, time, w.kbits.as<u32>(), w.ftiles.as<u32>(), (u32)ntiles, o_src, o_dst, o_time);
     if (launches) *launches += 1;
     TM_CUDA(cudaGetLastError());
+    return Status();
+}
+
+// len[d] += (end - start) of d's in-segment: the segment's first arc subtracts
+// its index and its last arc adds its index + 1 (two atomics per segment).
+__global__ void k_in_len(u64 m, const u32 *dst, u32 n, u32 *len)
+{
+    const u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    const u32 d = dst[e];
+    if (!TM_IN(d, n, &g_status_word)) return;
+    if (e == 0 || dst[e - 1] != d) atomicSub(&len[d], (u32)e);
+    if (e + 1 == m || dst[e + 1] != d) atomicAdd(&len[d], (u32)(e + 1));
+}
+
+Status build_in_off(Graph &g, cudaStream_t st, DevBuf &tiles, u32 *d_total)
+{
+    g.d_in_off = nullptr;
+    if (g.m >= 0xFFFFFFFFull) return Status();  // u32 offsets: the filter reads destinations instead
+    const u64 bytes = ((u64)g.n + 1) * 4;
+    TM_TRY(dev_alloc((void **)&g.d_in_off, bytes, st));
+    TM_CUDA(cudaMemsetAsync(g.d_in_off, 0, bytes, st));
+    if (g.m) k_in_len<<<(unsigned)((g.m + 255) / 256), 256, 0, st>>>(g.m, g.d_dst, g.n, g.d_in_off);
+    TM_CUDA(cudaGetLastError());
+    TM_TRY(exclusive_scan_on(st, tiles, g.d_in_off, (u64)g.n + 1, d_total, nullptr));
+    g.resident_bytes += bytes;
     return Status();
 }
 
@@ -742,7 +810,7 @@ Status job_prep(Job &j)
                                                        w.vflag.as<uint8_t>(), w.act.as<u32>());
     *launches += 1;
     TM_CUDA(cudaGetLastError());
-    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, m, w.vflag.as<uint8_t>(), q.filter(), d_cnt + 0,
+    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, g.d_in_off, g.n, m, w.vflag.as<uint8_t>(), q.filter(), d_cnt + 0,
                              launches));
     TM_TRY(exclusive_scan_on(st, w.block_sums, w.act.as<u32>(), (u64)n + 1, d_cnt + 2, launches));
     k_active_list<<<grid_for(n, 256), 256, 0, st>>>(n, w.act.as<u32>(), w.act_list.as<u32>());
@@ -1424,7 +1492,7 @@ Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, cons
     prof.stats.launches += 1;
     TM_CUDA(cudaGetLastError());
     u32 *d_cnt = w.counters.as<u32>();
-    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, m, w.vflag.as<uint8_t>(), f, d_cnt,
+    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, g.d_in_off, g.n, m, w.vflag.as<uint8_t>(), f, d_cnt,
                              (u64 *)&prof.stats.launches));
     u32 mf = 0;
     TM_CUDA(cudaMemcpyAsync(&mf, d_cnt, 4, cudaMemcpyDeviceToHost, st));
@@ -1453,7 +1521,7 @@ Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_
     k_vflag_mask<<<grid_for(g.n, 256), 256, 0, st>>>(g.n, d_alive, w.vflag.as<uint8_t>());
     TM_CUDA(cudaGetLastError());
     u32 *d_cnt = w.counters.as<u32>();
-    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, m, w.vflag.as<uint8_t>(), ArcFilter(), d_cnt,
+    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, g.d_in_off, g.n, m, w.vflag.as<uint8_t>(), ArcFilter(), d_cnt,
                              nullptr));
     u32 mk = 0;
     TM_CUDA(cudaMemcpyAsync(&mk, d_cnt, 4, cudaMemcpyDeviceToHost, st));
@@ -1475,7 +1543,7 @@ Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_
     TM_CUDA(cudaMemcpyAsync(sub->d_color, g.d_color, (u64)g.n * 4, cudaMemcpyDeviceToDevice, st));
     TM_CUDA(cudaGetLastError());
     sub->resident_bytes = 3 * mb + (u64)g.n * 4;
-    return Status();
+    return build_in_off(*sub, st, w.block_sums, d_cnt + 15);
 }
 
 __global__ void k_first_nonzero(const u64 *sums, u64 mf, u32 *best)

@@ -320,6 +320,35 @@ def test_arc_filter_over_ragged_tiles(tm):
         G.close()
 
 
+def test_arc_filter_by_vertex_and_by_arc_tiles(tm):
+    # a tile spanning at most 4096 destinations flags its arcs from the
+    # destinations' flags and in-segment offsets; a tile spanning more reads
+    # each arc's destination.  One graph with both kinds of tile, an
+    # in-segment spanning several tiles, empty vertices between segments and
+    # arcs into the last vertex must give the oracle's sums and paths, also on
+    # the subgraphs of preprocessing and extraction
+    rng = np.random.default_rng(77)
+    n = 60000
+    dst = np.concatenate([np.full(9000, 50), rng.integers(0, 100, 5000), rng.integers(100, n, 6000),
+                          np.full(40, n - 1)]).astype(np.uint32)
+    src = rng.integers(0, n, len(dst)).astype(np.uint32)
+    time = rng.integers(1, 61, len(dst)).astype(np.uint32)
+    color = rng.integers(0, 5, n).astype(np.uint32)
+    g = synth.Graph(n, src, dst, time, color, 5, False, "filter-tiles")
+    G = gpu_graph(tm, g)
+    for k, ms, kw in ((4, [0, 1, 2, 3], {}), (5, [0, 0, 1, 2, 4], {"t_min": 10, "t_max": 50}),
+                      (3, [1, 3, 3], {"end": 50})):
+        assert_same(*both(tm, G, g, k, ms, **kw))
+        f, v, t = tm.tmotif_extract(G, k, ms, method="halving", **kw)
+        fo, vo, to, _ = oracle.extract(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, **kw)
+        assert f == fo and np.array_equal(v, vo) and np.array_equal(t, to)
+    d = tm.tmotif_decide(G, 4, [0, 1, 2, 3], seed=9, preprocess=True)
+    fo, so, po, _ = oracle.decide_preprocessed(g.n, g.src, g.dst, g.time, g.color, g.num_colors, 4, [0, 1, 2, 3],
+                                              seed=9)
+    assert_same(d, (fo, so, po))
+    G.close()
+
+
 # ---------------------------------------------------------------------------
 # Extraction (Sec. 6.9): same deterministic procedure -> the same path
 # ---------------------------------------------------------------------------
