@@ -350,11 +350,12 @@ Status make_subgraph(const Graph &g, Workspace &w, cudaStream_t st, const uint8_
 // Arc filter (Sec. 8.1 (i)) in two passes: _count leaves the keep mask and
 // tile offsets in the workspace and the kept count in d_total (device u32);
 // after the caller reads the count and sizes the outputs, _compact writes the
-// kept arcs in arc order.  in_off: the graph's in-segment offsets (n + 1
-// entries), or null.
+// kept arcs in arc order.  With in_off (the graph's in-segment offsets, n + 1
+// entries) and vlist (the flagged vertices ascending, their count at device
+// d_nlist) the first pass goes by vertex, else by tiles of arcs.
 Status filter_arcs_count(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time,
                          const u32 *in_off, u32 n, u64 m, const uint8_t *vflag, const ArcFilter &f, u32 *d_total,
-                         u64 *launches);
+                         u64 *launches, const u32 *vlist = nullptr, const u32 *d_nlist = nullptr);
 // The graph's in-segment offsets d_in_off (n + 1 u32; first arc of each
 // destination, arcs sorted by destination), built on st; left null when the
 // arc count does not fit 32 bits.  tiles: scan scratch; d_total: a device u32.

@@ -66,14 +66,13 @@ __global__ void k_active_list(u32 n, const u32 *act, u32 *list)
 //     32j..32j+31) and the tile's kept count;
 //   after an exclusive scan of the tile counts, k_filter_compact writes the
 //     kept arcs, in arc order, from the mask alone.
-// The destination's flag is tested first.  Arcs are sorted by destination,
-// so a tile spans a run of destinations: with the graph's in-segment offsets
-// (in_off) the tile reads the flags and offsets of those vertices and marks
-// the arcs of flagged ones in shared memory, without reading the arcs'
-// destinations; a tile spanning more vertices than it has arcs (or a graph
-// without offsets) reads each arc's destination instead.  The scattered
-// source flag and the time are read only for arcs that pass the tests before
-// them.
+// The destination's flag is tested first: arcs are sorted by destination,
+// so those reads are nearly sequential, and the scattered source flag and the
+// time are read only for arcs that pass the tests before them.
+// Where few arcs have a flagged destination, the first pass goes by vertex
+// instead (k_filter_count_v): one warp per flagged destination walks its
+// in-segment (the graph's in-segment offsets) and writes the same mask bits
+// and tile counts, so the arcs of unflagged destinations are never read.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -82,61 +81,39 @@ const int FILTER_ROUNDS = 16;                                  // arcs per threa
 const int FILTER_TILE = FILTER_THREADS * FILTER_ROUNDS;        // 4096 arcs
 const int FILTER_WORDS = FILTER_TILE / 32;                     // 128 mask words
 
+// Time window and EC tuple of the filter (true for an untimed filter).
+__device__ __forceinline__ bool filter_time_ok(const ArcFilter &f, u32 t)
+{
+    bool in = t >= f.t_min && (f.t_max == 0 || t <= f.t_max);
+    if (in && f.n_times) {
+        // constant indices keep the tuple in the parameter space
+        bool hit = false;
+#pragma unroll
+        for (int r = 0; r < TMOTIF_KMAX; r++) hit |= (r < (int)f.n_times) && f.times[r] == t;
+        in = hit;
+    }
+    return in;
+}
+
 __global__ void __launch_bounds__(FILTER_THREADS)
-k_filter_count(u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32 *in_off, u32 n,
-               const uint8_t *vflag, ArcFilter f, u32 *bits, u32 *tile_count)
+k_filter_count(u64 m, const u32 *src, const u32 *dst, const u32 *time, const uint8_t *vflag, ArcFilter f, u32 *bits,
+               u32 *tile_count)
 {
     __shared__ u32 warp_count[FILTER_THREADS / 32];
-    __shared__ u32 dmask[FILTER_WORDS];  // bit i: arc base + i has a flagged destination
-    __shared__ u32 vrange[2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u64 base = (u64)blockIdx.x * FILTER_TILE;
-    const u64 end = min(base + (u64)FILTER_TILE, m);
     const bool timed = f.t_min != 0 || f.t_max != 0 || f.n_times != 0;
-    if (threadIdx.x < FILTER_WORDS) dmask[threadIdx.x] = 0;
-    if (threadIdx.x == 0) {
-        vrange[0] = end > base ? dst[base] : 0u;
-        vrange[1] = end > base ? dst[end - 1] : 0u;
-    }
-    __syncthreads();
-    const u32 v0 = vrange[0], v1 = vrange[1];
-    // uniform in the block
-    const bool by_vertex = in_off && end > base && v1 >= v0 && v1 < n && (u64)(v1 - v0) < (u64)FILTER_TILE;
-    if (by_vertex) {
-        for (u64 v = (u64)v0 + threadIdx.x; v <= v1; v += FILTER_THREADS) {
-            if (!vflag[v]) continue;
-            // the vertex's arcs inside the tile, as tile positions [lo, hi)
-            const u64 a = in_off[v], b = in_off[v + 1];
-            const u32 lo = (u32)(max(a, base) - base), hi = (u32)(min(b, end) - base);
-            for (u32 p = lo; p < hi;) {
-                const u32 word = p >> 5, q = min(hi, (word + 1) << 5);
-                const u32 width = q - p;  // 1..32 bits from bit p & 31
-                const u32 bitsw = width == 32 ? 0xffffffffu : (((1u << width) - 1u) << (p & 31));
-                atomicOr(&dmask[word], bitsw);
-                p = q;
-            }
-        }
-        __syncthreads();
-    }
     u32 d[FILTER_ROUNDS];
     bool k[FILTER_ROUNDS];
-    if (by_vertex) {
 #pragma unroll
-        for (int i = 0; i < FILTER_ROUNDS; i++) {
-            const u32 p = (u32)i * FILTER_THREADS + threadIdx.x;
-            k[i] = base + p < m && ((dmask[p >> 5] >> (p & 31)) & 1u);
-        }
-    } else {
+    for (int i = 0; i < FILTER_ROUNDS; i++) {
+        const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
+        d[i] = e < m ? dst[e] : 0u;
+    }
 #pragma unroll
-        for (int i = 0; i < FILTER_ROUNDS; i++) {
-            const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
-            d[i] = e < m ? dst[e] : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < FILTER_ROUNDS; i++) {
-            const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
-            k[i] = e < m && vflag[d[i]];
-        }
+    for (int i = 0; i < FILTER_ROUNDS; i++) {
+        const u64 e = base + (u64)i * FILTER_THREADS + threadIdx.x;
+        k[i] = e < m && vflag[d[i]];
     }
 #pragma unroll
     for (int i = 0; i < FILTER_ROUNDS; i++) {
@@ -150,16 +127,7 @@ k_filter_count(u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32
 #pragma unroll
         for (int i = 0; i < FILTER_ROUNDS; i++) {
             if (!k[i]) continue;
-            const u32 t = time[base + (u64)i * FILTER_THREADS + threadIdx.x];
-            bool in = t >= f.t_min && (f.t_max == 0 || t <= f.t_max);
-            if (in && f.n_times) {
-                // constant indices keep the tuple in the parameter space
-                bool hit = false;
-#pragma unroll
-                for (int r = 0; r < TMOTIF_KMAX; r++) hit |= (r < (int)f.n_times) && f.times[r] == t;
-                in = hit;
-            }
-            k[i] = in;
+            k[i] = filter_time_ok(f, time[base + (u64)i * FILTER_THREADS + threadIdx.x]);
         }
     }
     u32 count = 0;
@@ -175,6 +143,51 @@ k_filter_count(u64 m, const u32 *src, const u32 *dst, const u32 *time, const u32
         u32 t = 0;
         for (int i = 0; i < FILTER_THREADS / 32; i++) t += warp_count[i];
         tile_count[blockIdx.x] = t;
+    }
+}
+
+// First pass by vertex: resident warps take the flagged destinations v of
+// list[0, *n_list) (ascending) and walk each in-segment [in_off[v],
+// in_off[v + 1]) in rounds of 32 arcs, testing the source's flag and the time.
+// A round's kept bits land in at most two mask words, ORed in (a word can
+// hold the arcs of two destinations), and its count goes to the tiles of
+// those words.  The mask and the tile counts are zero before the launch.
+__global__ void __launch_bounds__(FILTER_THREADS)
+k_filter_count_v(const u32 *list, const u32 *n_list, const u32 *in_off, const u32 *src, const u32 *time,
+                 const uint8_t *vflag, ArcFilter f, u32 n, u64 m, u32 *bits, u32 *tile_count)
+{
+    const int lane = threadIdx.x & 31;
+    const bool timed = f.t_min != 0 || f.t_max != 0 || f.n_times != 0;
+    const u64 nl = *n_list;
+    const u64 warps = (u64)gridDim.x * (FILTER_THREADS / 32);
+    for (u64 i = (u64)blockIdx.x * (FILTER_THREADS / 32) + (threadIdx.x >> 5); i < nl; i += warps) {
+        const u32 v = list[i];  // uniform in the warp
+        if (!TM_IN(v, n, &g_status_word)) continue;
+        const u64 lo = in_off[v], hi = in_off[v + 1];
+        if (!TM_IN(hi, m + 1, &g_status_word) || !TM_IN(lo, hi + 1, &g_status_word)) continue;
+        for (u64 b = lo; b < hi; b += 32) {
+            const u64 e = b + lane;
+            bool ok = false;
+            if (e < hi) {
+                const u32 a = src[e];
+                ok = TM_IN(a, n, &g_status_word) && vflag[a];
+                if (ok && timed) ok = filter_time_ok(f, time[e]);
+            }
+            const u32 mask = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0 && mask) {
+                const u64 w0 = b >> 5;
+                const u32 sh = (u32)(b & 31);
+                const u32 lo_bits = mask << sh, hi_bits = sh ? mask >> (32 - sh) : 0u;
+                if (lo_bits) {
+                    atomicOr(&bits[w0], lo_bits);
+                    atomicAdd(&tile_count[w0 / FILTER_WORDS], (u32)__popc(lo_bits));
+                }
+                if (hi_bits) {
+                    atomicOr(&bits[w0 + 1], hi_bits);
+                    atomicAdd(&tile_count[(w0 + 1) / FILTER_WORDS], (u32)__popc(hi_bits));
+                }
+            }
+        }
     }
 }
 
@@ -228,16 +241,26 @@ k_filter_compact(const u32 *__restrict__ src, const u32 *__restrict__ dst, const
 }  // namespace
 
 // First pass of the arc filter: the keep mask in w.kbits, the tile offsets in
-// w.ftiles and the kept count to d_total (device u32).
+// w.ftiles and the kept count to d_total (device u32).  With a vertex list
+// (the flagged destinations, ascending, their count at d_nlist) and in_off,
+// by vertex; otherwise by tiles of arcs.
 Status filter_arcs_count(cudaStream_t st, Workspace &w, const u32 *src, const u32 *dst, const u32 *time,
                          const u32 *in_off, u32 n, u64 m, const uint8_t *vflag, const ArcFilter &f, u32 *d_total,
-                         u64 *launches)
+                         u64 *launches, const u32 *vlist, const u32 *d_nlist)
 {
     const u64 ntiles = std::max<u64>(1, (m + FILTER_TILE - 1) / FILTER_TILE);
     TM_TRY(w.kbits.reserve(ntiles * FILTER_WORDS * 4));
     TM_TRY(w.ftiles.reserve(ntiles * 4));
-    k_filter_count<<<(unsigned)ntiles, FILTER_THREADS, 0, st>>>(m, src, dst, time, in_off, n, vflag, f,
-                                                                w.kbits.as<u32>(), w.ftiles.as<u32>());
+    if (vlist && d_nlist && in_off) {
+        TM_CUDA(cudaMemsetAsync(w.kbits.p, 0, ntiles * FILTER_WORDS * 4, st));
+        TM_CUDA(cudaMemsetAsync(w.ftiles.p, 0, ntiles * 4, st));
+        const u64 blocks = std::max<u64>(1, std::min<u64>((n + 7) / 8, (u64)8 * sm_count()));
+        k_filter_count_v<<<(unsigned)blocks, FILTER_THREADS, 0, st>>>(vlist, d_nlist, in_off, src, time, vflag, f, n,
+                                                                      m, w.kbits.as<u32>(), w.ftiles.as<u32>());
+    } else {
+        k_filter_count<<<(unsigned)ntiles, FILTER_THREADS, 0, st>>>(m, src, dst, time, vflag, f, w.kbits.as<u32>(),
+                                                                    w.ftiles.as<u32>());
+    }
     if (launches) *launches += 1;
     TM_CUDA(cudaGetLastError());
     return exclusive_scan_on(st, w.block_sums, w.ftiles.as<u32>(), ntiles, d_total, launches);
@@ -776,6 +799,20 @@ static Status launch_coef(Job &j, cudaStream_t s, u32 L, u64 p0, u32 r)
     return j.prof->end(s, ca, FAM_COEF);
 }
 
+// Arcs whose destination's colour is in the multiset (before masks and the
+// time window), from the graph's colour-pair counts; m where there are none.
+static u64 flagged_dst_arcs(const Graph &g, const QuerySpec &q)
+{
+    if (g.pair_hist.empty()) return g.m;
+    std::vector<bool> in(g.num_colors, false);
+    for (u32 c : q.multiset) in[c] = true;
+    u64 s = 0;
+    for (u32 a = 0; a < g.num_colors; a++)
+        for (u32 b = 0; b < g.num_colors; b++)
+            if (in[b]) s += g.pair_hist[(size_t)a * g.num_colors + b];
+    return s;
+}
+
 Status job_prep(Job &j)
 {
     Graph &g = *j.g;
@@ -810,11 +847,14 @@ Status job_prep(Job &j)
                                                        w.vflag.as<uint8_t>(), w.act.as<u32>());
     *launches += 1;
     TM_CUDA(cudaGetLastError());
-    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, g.d_in_off, g.n, m, w.vflag.as<uint8_t>(), q.filter(), d_cnt + 0,
-                             launches));
     TM_TRY(exclusive_scan_on(st, w.block_sums, w.act.as<u32>(), (u64)n + 1, d_cnt + 2, launches));
     k_active_list<<<grid_for(n, 256), 256, 0, st>>>(n, w.act.as<u32>(), w.act_list.as<u32>());
     *launches += 1;
+    // the filter by flagged destination (the active list) where such arcs are
+    // a small share of all
+    const bool by_vertex = g.d_in_off && flagged_dst_arcs(g, q) * 10 < (u64)m * 3;
+    TM_TRY(filter_arcs_count(st, w, g.d_src, g.d_dst, g.d_time, g.d_in_off, g.n, m, w.vflag.as<uint8_t>(), q.filter(),
+                             d_cnt + 0, launches, by_vertex ? w.act_list.as<u32>() : nullptr, d_cnt + 2));
     TM_CUDA(cudaMemcpyAsync(h_cnt, d_cnt, 12, cudaMemcpyDeviceToHost, st));
     TM_CUDA(cudaStreamSynchronize(st));
     j.mf = h_cnt[0];

@@ -320,31 +320,41 @@ def test_arc_filter_over_ragged_tiles(tm):
         G.close()
 
 
-def test_arc_filter_by_vertex_and_by_arc_tiles(tm):
-    # a tile spanning at most 4096 destinations flags its arcs from the
-    # destinations' flags and in-segment offsets; a tile spanning more reads
-    # each arc's destination.  One graph with both kinds of tile, an
-    # in-segment spanning several tiles, empty vertices between segments and
-    # arcs into the last vertex must give the oracle's sums and paths, also on
-    # the subgraphs of preprocessing and extraction
+def test_arc_filter_by_vertex_and_by_tiles(tm):
+    # the filter's first pass goes by flagged destination (one warp walks each
+    # in-segment) when such arcs are under 30 % of all (from the graph's
+    # colour-pair counts), else by tiles of arcs.  One graph, queries on both
+    # sides of that switch, with an in-segment spanning several tiles, empty
+    # vertices between segments, arcs into the last vertex, a window, an EC
+    # tuple, and the subgraphs of extraction and preprocessing: the oracle's
+    # sums and paths
     rng = np.random.default_rng(77)
-    n = 60000
+    n, nc = 60000, 12
     dst = np.concatenate([np.full(9000, 50), rng.integers(0, 100, 5000), rng.integers(100, n, 6000),
                           np.full(40, n - 1)]).astype(np.uint32)
     src = rng.integers(0, n, len(dst)).astype(np.uint32)
     time = rng.integers(1, 61, len(dst)).astype(np.uint32)
-    color = rng.integers(0, 5, n).astype(np.uint32)
-    g = synth.Graph(n, src, dst, time, color, 5, False, "filter-tiles")
+    color = rng.integers(0, nc, n).astype(np.uint32)
+    g = synth.Graph(n, src, dst, time, color, nc, False, "filter-passes")
+    hub = int(color[50])
+    others = [c for c in range(nc) if c != hub]
+
+    def share(ms):
+        return np.isin(color[dst], ms).mean()
+
+    few = [others[0], others[1], others[1]]              # hub's colour out: few flagged destinations
+    many = [hub, others[0], others[2], others[3]]        # hub's colour in: most arcs
+    assert share(few) < 0.2 and share(many) > 0.4
     G = gpu_graph(tm, g)
-    for k, ms, kw in ((4, [0, 1, 2, 3], {}), (5, [0, 0, 1, 2, 4], {"t_min": 10, "t_max": 50}),
-                      (3, [1, 3, 3], {"end": 50})):
+    for k, ms, kw in ((3, few, {}), (4, many, {}), (3, few, {"t_min": 10, "t_max": 50}),
+                      (3, many[:3], {"t_max": 40, "end": 50}), (3, [others[4], others[4], others[5]], {"start": n - 1})):
         assert_same(*both(tm, G, g, k, ms, **kw))
         f, v, t = tm.tmotif_extract(G, k, ms, method="halving", **kw)
         fo, vo, to, _ = oracle.extract(g.n, g.src, g.dst, g.time, g.color, g.num_colors, k, ms, **kw)
         assert f == fo and np.array_equal(v, vo) and np.array_equal(t, to)
-    d = tm.tmotif_decide(G, 4, [0, 1, 2, 3], seed=9, preprocess=True)
-    fo, so, po, _ = oracle.decide_preprocessed(g.n, g.src, g.dst, g.time, g.color, g.num_colors, 4, [0, 1, 2, 3],
-                                              seed=9)
+    assert_same(*_ec_both(tm, G, g, 3, few, [4, 20, 33]))
+    d = tm.tmotif_decide(G, 3, few, seed=9, preprocess=True)
+    fo, so, po, _ = oracle.decide_preprocessed(g.n, g.src, g.dst, g.time, g.color, g.num_colors, 3, few, seed=9)
     assert_same(d, (fo, so, po))
     G.close()
 
