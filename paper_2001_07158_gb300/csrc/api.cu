@@ -158,7 +158,7 @@ void Workspace::set_stream(cudaStream_t s)
 {
     DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &kbits, &ftiles, &pos,
                      &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list,
-                     &arc_sum, &queue, &rec, &order};
+                     &arc_sum, &queue, &rec, &order, &slist, &gcount};
     for (DevBuf *b : all) b->stream = s;
 }
 
@@ -166,7 +166,7 @@ void Workspace::release()
 {
     DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &kbits, &ftiles, &pos,
                      &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list,
-                     &arc_sum, &queue, &rec, &order};
+                     &arc_sum, &queue, &rec, &order, &slist, &gcount};
     for (DevBuf *b : all) b->release();
     if (host_pinned) cudaFreeHost(host_pinned);
     host_pinned = nullptr;
@@ -177,7 +177,7 @@ size_t Workspace::bytes() const
 {
     const DevBuf *all[] = {&vflag, &slot_begin, &slot_count, &seg_lo, &seg_hi, &f_src, &f_dst, &f_time, &kbits, &ftiles, &pos,
                            &mark, &cp_in, &cp_out, &block_sums, &counters, &x, &C0, &C1, &out, &wtab, &alive, &partial, &act, &act_list,
-                           &arc_sum, &queue, &rec, &order};
+                           &arc_sum, &queue, &rec, &order, &slist, &gcount};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->bytes;
     return s;

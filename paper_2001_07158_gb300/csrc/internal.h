@@ -132,6 +132,8 @@ struct Workspace {
     DevBuf queue;                       // u64 team counter of the layer launches
     DevBuf rec;                         // m_f x 16 B: {dst, cp_in, cp_out, src} of the staged layer form
     DevBuf order;                       // n_chunks + 1 u32: heavy-first chunk order, then flags and offsets
+    DevBuf slist;                       // n_act u32: the active vertices grouped by colour
+    DevBuf gcount;                      // 2 k u32: per-colour counts and cursors of that grouping
     u32 order_chunk = 0;                // arcs per chunk the order was built for (0: none)
     void *host_pinned = nullptr;        // small pinned readback area
     size_t host_pinned_bytes = 0;
@@ -284,6 +286,7 @@ struct Job {
     bool localize = false;    // accumulate arc-localised sums at the last layer
     u32 rep_offset = 0;       // repeat index of the first repeat this job evaluates
     u64 batch_seq = 0;    // batch number across repeats (slot index)
+    bool slist_ready = false;  // the workspace's slist holds this query's active vertices by colour
 };
 
 // Job steps.  prep: filter, checkpoints, buffer sizing (synchronises the

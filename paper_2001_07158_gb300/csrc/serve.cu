@@ -49,7 +49,7 @@ size_t job_estimate(const Graph &g, const QuerySpec &q)
     const u64 mf = kept_arc_bound(g, q), n = g.n, m = g.m;
     u64 L = 4;
     while (L < 128 && L < q.p_end - q.p_begin) L <<= 1;
-    return (size_t)(n * 9 + (m + 1) * 4 + mf * 32 + n * L * 8 + 2 * mf * L * 8 + ((mf + 127) / 128) * L * 8 +
+    return (size_t)(n * 13 + (m + 1) * 4 + mf * 32 + n * L * 8 + 2 * mf * L * 8 + ((mf + 127) / 128) * L * 8 +
                     (u64)q.k * L * 8 + 4096 + (m / 4096 + 1) * 4);
 }
 

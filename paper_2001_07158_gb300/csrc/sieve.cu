@@ -458,6 +458,99 @@ __global__ void __launch_bounds__(256) k_coef(u32 n_act, const u32 *list, u32 L,
         if ((u32)tt + 32 * i < L) x[(u64)u * L + tt + 32 * i] = s[i];
 }
 
+// Coefficients by multiplier table (large lists): x_u^A = sum_d v_{u,d} W_d^A
+// read the other way round.  W_d^A is common to every vertex of slot d, so a
+// block holds the nibble tables of W_d^A for all k slots and a group of LG
+// lanes (k * LG tables of 2 KB, built once per block) and each thread takes a
+// vertex: per slot of its colour one v_{u,d}, then LG lane products of 16
+// table loads.  The vertices come grouped by colour (slist), so the threads
+// of a warp read the same table at each step.
+
+// Grouping the active vertices by colour: gcnt[slot_begin[c]] counts colour c
+// (k counters; one atomic per colour per warp), then every vertex takes a
+// place in its colour's range of slist.
+__global__ void k_group_count(u32 n_act, const u32 *list, const u32 *color, const u32 *slot_begin, u32 *gcnt)
+{
+    const u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_act) return;
+    const u32 g = slot_begin[color[list[v]]];
+    const unsigned act = __activemask();
+    const unsigned same = __match_any_sync(act, g);
+    if ((threadIdx.x & 31) == (u32)(__ffs(same) - 1)) atomicAdd(&gcnt[g], (u32)__popc(same));
+}
+
+// gcnt[0..k): counts, gcnt[k..2k): cursors (zero); slist gets each colour's
+// vertices in the range that the counts' exclusive prefix gives.
+__global__ void k_group_scatter(u32 n_act, const u32 *list, const u32 *color, const u32 *slot_begin, u32 k,
+                                u32 *gcnt, u32 *slist)
+{
+    const u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_act) return;
+    const u32 u = list[v];
+    const u32 g = slot_begin[color[u]];
+    if (!TM_IN(g, k, &g_status_word)) return;
+    u32 base = 0;
+    for (u32 i = 0; i < g; i++) base += gcnt[i];
+    const unsigned act = __activemask();
+    const unsigned same = __match_any_sync(act, g);
+    const int lead = __ffs(same) - 1;
+    u32 first = 0;
+    if ((int)(threadIdx.x & 31) == lead) first = atomicAdd(&gcnt[k + g], (u32)__popc(same));
+    first = __shfl_sync(same, first, lead);
+    const u32 rank = __popc(same & ((1u << (threadIdx.x & 31)) - 1u));
+    slist[base + first + rank] = u;
+}
+
+const int COEF_T_THREADS = 512;
+const u64 COEF_T_SMEM = 192 * 1024;  // tables; plus 2 KB for the alignment
+
+// Lanes per block of k_coef_t: the largest power of two <= L whose k tables
+// per lane fit COEF_T_SMEM, at least 4 (k <= TMOTIF_KMAX).
+static u32 coef_t_lanes(u32 k, u32 L)
+{
+    u32 lg = std::min<u32>(L, 16);
+    while (lg > 4 && (u64)k * lg * 2048 > COEF_T_SMEM) lg >>= 1;
+    return lg;
+}
+
+template <int LG>
+__global__ void __launch_bounds__(COEF_T_THREADS) k_coef_t(u32 n_act, const u32 *slist, u32 L, u32 k,
+                                                           const u32 *color, const u32 *slot_begin,
+                                                           const u32 *slot_count, QueryKeys keys, const u64 *wtab,
+                                                           u64 *x, u32 n, u32 num_colors, u32 groups)
+{
+    extern __shared__ __align__(16) u64 smem[];
+    const u32 sa = (u32)__cvta_generic_to_shared(smem);
+    u64 *tabs = smem + (((2048u - (sa & 2047u)) & 2047u) >> 3);  // 2 KB boundary
+    const u32 group = blockIdx.x % groups, a0 = group * LG;
+    const u32 warp = threadIdx.x >> 5, tt = threadIdx.x & 31, nwarps = COEF_T_THREADS / 32;
+    // table (d, a) at tabs + (d * LG + a) * 256: nibble table of W_d^{a0 + a}
+    for (u32 t = warp; t < k * LG; t += nwarps)
+        gf_table_build(tabs + (u64)t * 256, wtab[(u64)(t / LG) * L + a0 + t % LG], tt, 32);
+    __syncthreads();
+    const u64 step = (u64)(gridDim.x / groups) * COEF_T_THREADS;
+    for (u64 i = (u64)(blockIdx.x / groups) * COEF_T_THREADS + threadIdx.x; i < n_act; i += step) {
+        const u32 u = slist[i];
+        if (!TM_IN(u, n, &g_status_word)) continue;
+        const u32 c = color[u];
+        if (!TM_IN(c, num_colors, &g_status_word)) continue;
+        const u32 d0 = slot_begin[c], d1 = d0 + slot_count[c];
+        if (!TM_IN(d1, k + 1, &g_status_word)) continue;
+        u64 acc[LG];
+#pragma unroll
+        for (int a = 0; a < LG; a++) acc[a] = 0;
+        for (u32 d = d0; d < d1; d++) {
+            const u64 v = coef_v(keys, u, d);
+            const u64 *td = tabs + (u64)d * LG * 256;
+#pragma unroll
+            for (int a = 0; a < LG; a++) acc[a] ^= gf_table_mul(td + a * 256, v);
+        }
+        ulonglong2 *out = (ulonglong2 *)(x + (u64)u * L + a0);
+#pragma unroll
+        for (int a = 0; a < LG; a += 2) out[a / 2] = make_ulonglong2(acc[a], acc[a + 1]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Layer kernel: eq. (gen-polynomial:3), one walk length per job per launch.
 // MULTI = false: the single job in `one` (read from parameter space);
@@ -756,7 +849,7 @@ size_t job_bytes(const Job &j)
 {
     const u64 n = j.g->n, m = j.mf ? j.mf : j.g->m, L = j.L ? j.L : LANES_MAX;
     const u64 ncp = j.mf ? j.ncp : m;
-    return (size_t)(n * (1 + 8) + j.g->m / 8 + 4096 + m * 28 + n * L * 8 + 2 * ncp * L * 8 +
+    return (size_t)(n * (1 + 12) + j.g->m / 8 + 4096 + m * 28 + n * L * 8 + 2 * ncp * L * 8 +
                     ((m + CHUNK_MIN - 1) / CHUNK_MIN) * L * 8 + 4096);
 }
 
@@ -779,8 +872,32 @@ static Status lane_width(const Job &j, u64 ncp, u32 *out)
     return Status();
 }
 
+// Lists with at least this many vertex-lanes take the coefficients by
+// multiplier table (k_coef_t); shorter ones one warp per vertex (k_coef).
+static const u64 COEF_T_MIN_LANES = 1ull << 20;
+
+template <int LG>
+static Status launch_coef_t(cudaStream_t s, u32 blocks, u32 groups, size_t smem, u32 n_act, const u32 *slist, u32 L,
+                            u32 k, const Graph &g, const Workspace &w, const QueryKeys &keys)
+{
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    TM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TMOTIF_ERR_CUDA, "device index");
+    if (!attr_set[dev]) {
+        TM_CUDA(cudaFuncSetAttribute(k_coef_t<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(COEF_T_SMEM + 2048)));
+        attr_set[dev] = true;
+    }
+    k_coef_t<LG><<<blocks, COEF_T_THREADS, smem, s>>>(n_act, slist, L, k, g.d_color, w.slot_begin.as<u32>(),
+                                                       w.slot_count.as<u32>(), keys, w.wtab.as<u64>(),
+                                                       w.x.as<u64>(), g.n, g.num_colors, groups);
+    return Status();
+}
+
 // Coefficients x_u^A and W_d^A of the lane batch at p0 for repeat r, lane
-// width L, on stream s (2 launches).
+// width L, on stream s (2 launches; the first batch of a query by table also
+// groups the active vertices by colour, 2 launches).
 static Status launch_coef(Job &j, cudaStream_t s, u32 L, u64 p0, u32 r)
 {
     Graph &g = *j.g;
@@ -790,11 +907,35 @@ static Status launch_coef(Job &j, cudaStream_t s, u32 L, u64 p0, u32 r)
     cudaEvent_t ca = nullptr;
     TM_TRY(j.prof->begin(s, &ca));
     k_wtab<<<grid_for((u64)k * L, 128), 128, 0, s>>>(k, L, p0, keys, w.wtab.as<u64>());
-    if (j.n_act)
+    j.prof->stats.launches += 1;
+    if (j.n_act && j.n_act * L >= COEF_T_MIN_LANES) {
+        if (!j.slist_ready) {
+            TM_TRY(w.slist.reserve(j.n_act * 4));
+            TM_TRY(w.gcount.reserve(2 * (u64)TMOTIF_KMAX * 4));
+            TM_CUDA(cudaMemsetAsync(w.gcount.p, 0, 2 * (u64)k * 4, s));
+            k_group_count<<<grid_for(j.n_act, 256), 256, 0, s>>>((u32)j.n_act, w.act_list.as<u32>(), g.d_color,
+                                                                  w.slot_begin.as<u32>(), w.gcount.as<u32>());
+            k_group_scatter<<<grid_for(j.n_act, 256), 256, 0, s>>>((u32)j.n_act, w.act_list.as<u32>(), g.d_color,
+                                                                    w.slot_begin.as<u32>(), k, w.gcount.as<u32>(),
+                                                                    w.slist.as<u32>());
+            j.prof->stats.launches += 2;
+            TM_CUDA(cudaGetLastError());
+            j.slist_ready = true;
+        }
+        const u32 lg = coef_t_lanes(k, L), groups = L / lg;
+        const u32 blocks = groups * std::max<u32>(1, (u32)sm_count() / groups);
+        const size_t smem = (size_t)k * lg * 2048 + 2048;
+        const u32 *sl = w.slist.as<u32>();
+        if (lg == 16) TM_TRY(launch_coef_t<16>(s, blocks, groups, smem, (u32)j.n_act, sl, L, k, g, w, keys));
+        else if (lg == 8) TM_TRY(launch_coef_t<8>(s, blocks, groups, smem, (u32)j.n_act, sl, L, k, g, w, keys));
+        else TM_TRY(launch_coef_t<4>(s, blocks, groups, smem, (u32)j.n_act, sl, L, k, g, w, keys));
+        j.prof->stats.launches += 1;
+    } else if (j.n_act) {
         k_coef<<<(unsigned)((j.n_act + 7) / 8), 256, 0, s>>>((u32)j.n_act, w.act_list.as<u32>(), L, g.d_color,
-                                                  w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
-                                                  w.wtab.as<u64>(), w.x.as<u64>(), g.n, g.num_colors, k);
-    j.prof->stats.launches += 2;
+                                                              w.slot_begin.as<u32>(), w.slot_count.as<u32>(), keys,
+                                                              w.wtab.as<u64>(), w.x.as<u64>(), g.n, g.num_colors, k);
+        j.prof->stats.launches += 1;
+    }
     TM_CUDA(cudaGetLastError());
     return j.prof->end(s, ca, FAM_COEF);
 }
@@ -837,6 +978,7 @@ Status job_prep(Job &j)
     u32 *d_cnt = w.counters.as<u32>();
 
     w.order_chunk = 0;  // the chunk order belongs to the previous query's arcs
+    j.slist_ready = false;  // the active vertices grouped by colour, for this query
     // filter arcs (Sec. 8.1 (i): colours outside M, masked vertices, window)
     cudaEvent_t pa = nullptr;
     TM_TRY(j.prof->begin(st, &pa));

@@ -359,6 +359,29 @@ def test_arc_filter_by_vertex_and_by_tiles(tm):
     G.close()
 
 
+def test_coefficients_by_multiplier_table(tm):
+    # lists of at least 2^20 vertex-lanes take x_u^A by multiplier table:
+    # tables of W_d^A for 16, 8 or 4 lanes per block (k <= 6, 7..12, 13..20),
+    # the active vertices grouped by colour, repeated colours (two slots);
+    # every per-point sum equals the oracle's; an extraction through such
+    # lists returns a valid path
+    g = synth.uniform_graph(100000, 300000, 50, 4, seed=91)
+    G = gpu_graph(tm, g)
+    for k, ms, kw in ((4, [0, 1, 2, 3], {}), (5, [0, 1, 1, 2, 3], {}),
+                      (7, [0, 0, 1, 1, 2, 3, 3], {"point_begin": 0, "point_end": 64}),
+                      (13, [0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 0], {"point_begin": 4000, "point_end": 4064})):
+        assert_same(*both(tm, G, g, k, ms, **kw))
+    ms = [0, 1, 1, 2, 3]
+    f, v, t = tm.tmotif_extract(G, 5, ms, method="halving")
+    assert f
+    arcs = set(zip(g.src.tolist(), g.dst.tolist(), g.time.tolist()))
+    assert len(set(v.tolist())) == 5 and sorted(g.color[v].tolist()) == sorted(ms)
+    for r in range(4):
+        assert (int(v[r]), int(v[r + 1]), int(t[r])) in arcs
+        assert r == 0 or t[r] > t[r - 1]
+    G.close()
+
+
 # ---------------------------------------------------------------------------
 # Extraction (Sec. 6.9): same deterministic procedure -> the same path
 # ---------------------------------------------------------------------------
