@@ -872,9 +872,12 @@ static Status lane_width(const Job &j, u64 ncp, u32 *out)
     return Status();
 }
 
-// Lists with at least this many vertex-lanes take the coefficients by
-// multiplier table (k_coef_t); shorter ones one warp per vertex (k_coef).
+// Lists of at least COEF_T_MIN_LANES vertex-lanes at lane widths up to
+// COEF_T_MAX_L take the coefficients by multiplier table (k_coef_t); the
+// others one warp per vertex (k_coef), whose per-vertex table is then shared
+// by 64 or 128 lanes and which was faster there.
 static const u64 COEF_T_MIN_LANES = 1ull << 20;
+static const u32 COEF_T_MAX_L = 32;
 
 template <int LG>
 static Status launch_coef_t(cudaStream_t s, u32 blocks, u32 groups, size_t smem, u32 n_act, const u32 *slist, u32 L,
@@ -908,7 +911,7 @@ static Status launch_coef(Job &j, cudaStream_t s, u32 L, u64 p0, u32 r)
     TM_TRY(j.prof->begin(s, &ca));
     k_wtab<<<grid_for((u64)k * L, 128), 128, 0, s>>>(k, L, p0, keys, w.wtab.as<u64>());
     j.prof->stats.launches += 1;
-    if (j.n_act && j.n_act * L >= COEF_T_MIN_LANES) {
+    if (j.n_act && L <= COEF_T_MAX_L && j.n_act * L >= COEF_T_MIN_LANES) {
         if (!j.slist_ready) {
             TM_TRY(w.slist.reserve(j.n_act * 4));
             TM_TRY(w.gcount.reserve(2 * (u64)TMOTIF_KMAX * 4));

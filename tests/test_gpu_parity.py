@@ -360,16 +360,18 @@ def test_arc_filter_by_vertex_and_by_tiles(tm):
 
 
 def test_coefficients_by_multiplier_table(tm):
-    # lists of at least 2^20 vertex-lanes take x_u^A by multiplier table:
-    # tables of W_d^A for 16, 8 or 4 lanes per block (k <= 6, 7..12, 13..20),
-    # the active vertices grouped by colour, repeated colours (two slots);
-    # every per-point sum equals the oracle's; an extraction through such
-    # lists returns a valid path
+    # lists of at least 2^20 vertex-lanes at up to 32 lanes take x_u^A by
+    # multiplier table: tables of W_d^A for 16, 8 or 4 lanes per block
+    # (k <= 6, 7..12, 13..20), the active vertices grouped by colour, repeated
+    # colours (two slots); every per-point sum equals the oracle's (and the
+    # 64-lane case, one warp per vertex, too); an extraction through such lists
+    # returns a valid path
     g = synth.uniform_graph(100000, 300000, 50, 4, seed=91)
     G = gpu_graph(tm, g)
     for k, ms, kw in ((4, [0, 1, 2, 3], {}), (5, [0, 1, 1, 2, 3], {}),
-                      (7, [0, 0, 1, 1, 2, 3, 3], {"point_begin": 0, "point_end": 64}),
-                      (13, [0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 0], {"point_begin": 4000, "point_end": 4064})):
+                      (7, [0, 0, 1, 1, 2, 3, 3], {"point_begin": 0, "point_end": 32}),
+                      (13, [0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 0], {"point_begin": 4000, "point_end": 4032}),
+                      (7, [0, 0, 1, 1, 2, 3, 3], {"point_begin": 64, "point_end": 128})):
         assert_same(*both(tm, G, g, k, ms, **kw))
     ms = [0, 1, 1, 2, 3]
     f, v, t = tm.tmotif_extract(G, 5, ms, method="halving")
