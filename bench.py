@@ -423,7 +423,8 @@ def transit_leg(tm, stream, dev, costs, rates, steps, warmup):
         total_ms, found, stats, clocks = measure_decision(tm, stream, dev, G, q, steps, warmup, q.seed, pre)
         ms = total_ms / steps
         leg = {"ms_per_step": ms, "value": work / (ms / 1e3), "unit": UNIT, "found_all": all(found),
-               "clocks": clocks, "roofline": roofline_of(stats, total_ms, costs, rates, None)}
+               "clocks": clocks, "roofline": roofline_of(stats, total_ms, costs, rates, None),
+               "phases_ms": phases_of(stats, total_ms, steps)}
         if pre:
             sr = static_roofline(stats, costs, rates)
             if sr:
