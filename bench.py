@@ -105,7 +105,7 @@ def probe_rates(tm, iters=2048, repeats=3):
 # layer-kernel sources it was taken on (source_sha() below, first 16 hex):
 # a timed-decision layer of the default workload, full size, one-pass dram
 # counters
-LAYER_TRAFFIC = {"source_sha": "d2bf8c5d9b655d2c", "bytes_per_launch": 1125068032 + 399579392}
+LAYER_TRAFFIC = {"source_sha": "b84d4058b4a9445d", "bytes_per_launch": 1124364288 + 399417856}
 
 
 def parse_args(argv=None):
