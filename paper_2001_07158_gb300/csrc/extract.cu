@@ -17,12 +17,27 @@
 #include <algorithm>
 #include <map>
 #include <numeric>
+#include <mutex>
 #include <vector>
 
 #include "gf64.cuh"
 #include "internal.h"
 
 namespace tmo {
+
+Status ensure_host_colors(Graph &g)
+{
+    static std::mutex mu;  // the server's lanes and submitting threads share graphs
+    std::lock_guard<std::mutex> lock(mu);
+    if (g.h_color) return Status();
+    auto c = std::make_shared<std::vector<u32>>(g.n);
+    if (g.n) {
+        TM_CUDA(cudaMemcpyAsync(c->data(), g.d_color, (u64)g.n * 4, cudaMemcpyDeviceToHost, g.stream));
+        TM_CUDA(cudaStreamSynchronize(g.stream));
+    }
+    g.h_color = std::move(c);
+    return Status();
+}
 
 void ExtractState::init(const Graph &g, const QuerySpec &q)
 {
@@ -213,6 +228,7 @@ Status extract_path(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, int *f
     *found = 0;
     *probes = 0;
     ExtractState ex;
+    TM_TRY(ensure_host_colors(g));
     ex.init(g, q);
     TM_TRY(g.ws.alive.reserve(std::max<u32>(g.n, 1)));
     QuerySpec pq;
@@ -328,6 +344,7 @@ Status extract_localized(Graph &g, const QuerySpec &q, u32 *verts, u32 *times, i
 {
     *found = 0;
     LocalizedExtract ex;
+    TM_TRY(ensure_host_colors(g));
     ex.init(g, q);
     QuerySpec sub;
     u32 rep = 0;

@@ -420,7 +420,6 @@ Status build_graph_device(const tmotif_graph_desc *d, Graph *g)
     g->num_colors = d->num_colors;
     g->max_time = tmax;
     g->stream = st;
-    g->h_color = std::make_shared<std::vector<u32>>(d->color, d->color + n);
     g->resident_bytes += 3 * mb + (u64)std::max<u32>(n, 1) * 4;
     return Status();
 }

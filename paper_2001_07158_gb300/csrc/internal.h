@@ -164,7 +164,7 @@ struct Graph {
     u32 *d_src = nullptr, *d_dst = nullptr, *d_time = nullptr;
     u32 *d_color = nullptr;
     u32 *d_in_off = nullptr;  // n + 1: first arc of each destination's in-segment (null: m >= 2^32 - 1)
-    std::shared_ptr<std::vector<u32>> h_color;  // host copy for extraction bookkeeping
+    std::shared_ptr<std::vector<u32>> h_color;  // host copy for extraction bookkeeping (ensure_host_colors)
     std::vector<u64> pair_hist;         // arcs per (colour(src), colour(dst)), if few colours
     Workspace ws;
     Profiler prof;
@@ -346,6 +346,9 @@ Status gather_arcs(Graph &g, Workspace &w, cudaStream_t st, Profiler &prof, cons
 
 // Device arrays of a graph (arcs, colours, workspace, profiler events).
 void release_graph_arrays(Graph *g);
+// g.h_color, copied from the device on the graph's stream at first use (the
+// extraction entry points call it before their bookkeeping reads colours).
+Status ensure_host_colors(Graph &g);
 // The arcs of g whose endpoints both have alive[u] != 0 (device mask), as a
 // new resident graph with the same vertex ids (extraction's shrinking
 // subgraph).  Uses workspace w on stream st.

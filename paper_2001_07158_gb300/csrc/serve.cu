@@ -795,6 +795,10 @@ extern "C" int tmotif_submit(tmotif_server_t s, tmotif_graph_t g, const tmotif_q
         r->is_extract = is_extract != 0;
         r->halving = (r->q.flags & TMOTIF_EXTRACT_HALVING) != 0;
         r->large = request_work(*g, r->q, r->is_extract) > LARGE_WORK;
+        if (r->is_extract) {
+            Status hc = ensure_host_colors(*g);
+            if (!hc.ok()) return hc.code;
+        }
         if (r->is_extract && r->halving) r->ex.init(*g, r->q);
         if (r->is_extract && !r->halving) r->lex.init(*g, r->q);
         r->t_submit = Clock::now();
